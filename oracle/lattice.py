@@ -1,0 +1,164 @@
+"""D3Q19 BGK liquid solver, FP64 (test infrastructure only; see package docstring).
+
+Fields are numpy arrays indexed ``[q, z, y, x]`` for populations and
+``[z, y, x]`` for scalars; vectors carry a leading component axis
+``[3, z, y, x]`` ordered (x, y, z).  Lattice units: dx = dt_l = e = 1.
+
+Direction numbering follows the paper's grouping (Eq. 7): the six axis
+directions first, then the twelve edge diagonals, the rest velocity last.
+"""
+import numpy as np
+
+# --- Eq. 7: discrete velocities c_j (e = 1).  j = 0..5 axis, 6..17 edges, 18 rest.
+C = np.array(
+    [
+        (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
+        (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0),
+        (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1),
+        (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1),
+        (0, 0, 0),
+    ],
+    dtype=np.int64,
+)
+Q = 19
+
+# --- Eq. 8: weights w_j.
+W = np.array([1.0 / 18.0] * 6 + [1.0 / 36.0] * 12 + [1.0 / 3.0], dtype=np.float64)
+
+# Opposite direction of each c_j (the direction with velocity -c_j).
+OPP = np.array([int(np.flatnonzero((C == -C[j]).all(axis=1))[0]) for j in range(Q)])
+
+# Wall bit for each face, in the order (-x, +x, -y, +y, -z, +z).
+WALL_XM, WALL_XP, WALL_YM, WALL_YP, WALL_ZM, WALL_ZP = (1 << k for k in range(6))
+ALL_WALLS = 0x3F
+
+
+def viscosity(omega):
+    """Eq. 9 with dx = dt_l = 1: nu = (2 tau - 1)/6, tau = 1/omega."""
+    tau = 1.0 / omega
+    return (2.0 * tau - 1.0) / 6.0
+
+
+def equilibrium(rho, u):
+    """Eq. 6 (e = 1): f_j^eq = w_j rho [1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u].
+
+    rho: [...]; u: [3, ...]  ->  [Q, ...].
+    """
+    rho = np.asarray(rho, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    usq = (u * u).sum(axis=0)
+    feq = np.empty((Q,) + rho.shape, dtype=np.float64)
+    for j in range(Q):
+        cu = C[j, 0] * u[0] + C[j, 1] * u[1] + C[j, 2] * u[2]
+        feq[j] = W[j] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq)
+    return feq
+
+
+def density(f):
+    """Eq. 10: rho = sum_j f_j."""
+    return f.sum(axis=0)
+
+
+def momentum(f):
+    """Eq. 10: rho u = sum_j c_j f_j  -> [3, ...]."""
+    m = np.zeros((3,) + f.shape[1:], dtype=np.float64)
+    for j in range(Q):
+        for d in range(3):
+            if C[j, d] != 0:
+                m[d] += C[j, d] * f[j]
+    return m
+
+
+def velocity(f, force=None):
+    """Macroscopic velocity.
+
+    With ``force=None`` this is the bare moment of Eq. 10, u = sum c f / rho
+    (the quantity Algorithm 1 step 3 interpolates to the bubble).  With a force
+    field it is the first-forcing velocity of Eq. 13,
+    u = (sum c f + F dt_l / 2) / rho.  The sum in Eq. 13 is printed over
+    j = 1..9, a D2Q9 leftover; it runs over all 19 directions here.
+    """
+    m = momentum(f)
+    if force is not None:
+        m = m + 0.5 * force
+    return m / density(f)
+
+
+def guo_term(u, force, omega):
+    """Eq. 12: F_j = (1 - 1/(2 tau)) w_j [3 (c_j - u) + 9 (c_j . u) c_j] . F."""
+    pref = 1.0 - 0.5 * omega
+    out = np.empty((Q,) + u.shape[1:], dtype=np.float64)
+    for j in range(Q):
+        cu = C[j, 0] * u[0] + C[j, 1] * u[1] + C[j, 2] * u[2]
+        acc = np.zeros(u.shape[1:], dtype=np.float64)
+        for d in range(3):
+            acc += (3.0 * (C[j, d] - u[d]) + 9.0 * cu * C[j, d]) * force[d]
+        out[j] = pref * W[j] * acc
+    return out
+
+
+def collide(f, omega, force=None):
+    """One local forced BGK update, Eq. 13 -> 14 -> 15 (dt_l = 1).
+
+    First forcing (Eq. 13) gives rho and the velocity u; the collision (Eq. 14)
+    relaxes towards f^eq(rho, u) of Eq. 6 with rate 1/tau = omega; the second
+    forcing (Eq. 15) adds the Guo term of Eq. 12 built from the same u.
+    Returns the post-collision populations f''.
+    """
+    rho = density(f)
+    u = velocity(f, force)
+    feq = equilibrium(rho, u)
+    fpost = f - omega * (f - feq)
+    if force is not None:
+        fpost = fpost + guo_term(u, force, omega)
+    return fpost
+
+
+def stream(fpost, walls):
+    """Eq. 16, f_j(x + c_j, t + 1) = f''_j(x, t), with walls on the box faces.
+
+    ``walls`` has one bit per face (-x, +x, -y, +y, -z, +z).  A clear bit makes
+    that axis periodic (both faces of an axis must agree).  A set bit is a
+    stationary no-slip wall half-way between the boundary node and the next
+    (outside) node (Sec. 3.3, read as plain half-way bounce-back): a population
+    whose link x -> x + c_j crosses a wall returns to x as the opposite
+    population, f_{opp(j)}(x, t + 1) = f''_j(x, t).
+    """
+    _check_walls(walls)
+    nz, ny, nx = fpost.shape[1:]
+    shape = (nx, ny, nz)
+    wall_axis = [bool(walls & (1 << (2 * d))) for d in range(3)]
+    out = np.empty_like(fpost)
+    # Coordinates of every node, per axis, broadcast to the field shape.
+    coord = [np.arange(shape[0])[None, None, :], np.arange(shape[1])[None, :, None],
+             np.arange(shape[2])[:, None, None]]
+    for j in range(Q):
+        moved = fpost[j]
+        for d in range(3):
+            if C[j, d] != 0:
+                moved = np.roll(moved, C[j, d], axis=2 - d)
+        out[j] = moved
+    # Half-way bounce-back: a node x receives population j from x - c_j.  If
+    # that link crosses a wall, the value is instead f''_{opp(j)}(x).
+    for j in range(Q):
+        crosses = np.zeros(fpost.shape[1:], dtype=bool)
+        for d in range(3):
+            if C[j, d] == 0 or not wall_axis[d]:
+                continue
+            src = coord[d] - C[j, d]
+            crosses = crosses | np.broadcast_to((src < 0) | (src >= shape[d]), crosses.shape)
+        out[j][crosses] = fpost[OPP[j]][crosses]
+    return out
+
+
+def _check_walls(walls):
+    for d in range(3):
+        lo = bool(walls & (1 << (2 * d)))
+        hi = bool(walls & (1 << (2 * d + 1)))
+        if lo != hi:
+            raise ValueError("both faces of an axis must be walls, or both periodic")
+
+
+def lb_step(f, omega, walls, force=None):
+    """Collide (Eq. 13-15) then stream (Eq. 16) once."""
+    return stream(collide(f, omega, force), walls)

@@ -1,0 +1,116 @@
+"""Pins for the oracle's coupling maps (Sec. 3.2, Eq. 18-21) and binning (Algorithm 1 step 2)."""
+import numpy as np
+import pytest
+
+from oracle import binning, lattice as lat, mapping
+
+
+@pytest.mark.parametrize("n", [0.75, 1.5, 3.0, 4.5])
+def test_mapping_function_criteria(n):
+    # The four criteria listed before Eq. 18: smooth (continuous first
+    # derivative, zero at the window edge), maximum at the bubble, zero at the
+    # boundary of a finite window, unit integral.
+    nodes, wts = np.polynomial.legendre.leggauss(8)
+    integral = (mapping.kernel_z(n * nodes, n) * wts).sum() * n
+    assert abs(integral - 1.0) < 1e-14
+    assert mapping.kernel_z(n, n) == pytest.approx(0.0, abs=1e-15)
+    assert mapping.kernel_z(-n, n) == pytest.approx(0.0, abs=1e-15)
+    assert mapping.kernel_z(n * 1.0001, n) == 0.0
+    h = 1e-6 * n
+    for edge in (-n, n):
+        inside = edge - np.sign(edge) * h
+        slope = (mapping.kernel_z(edge, n) - mapping.kernel_z(inside, n)) / h
+        assert abs(slope) < 1e-5 / n ** 2
+    r = np.linspace(-n, n, 2001)
+    assert np.argmax(mapping.kernel_z(r, n)) == 1000
+    assert mapping.kernel_z(0.0, n) == pytest.approx(15.0 / (16.0 * n))
+
+
+def test_cell_integral_matches_quadrature():
+    # Eq. 19 one factor: G(b) - G(a) equals Gauss-Legendre quadrature of Z over
+    # [a, b] clipped to the window (a quartic is integrated exactly with 3+ points).
+    rng = np.random.default_rng(7)
+    nodes, wts = np.polynomial.legendre.leggauss(5)
+    for _ in range(200):
+        n = rng.uniform(0.5, 5.0)
+        a = rng.uniform(-1.5 * n, 1.2 * n)
+        b = a + rng.uniform(0.0, 2.0)
+        lo, hi = max(a, -n), min(b, n)
+        quad = 0.0
+        if hi > lo:
+            xs = 0.5 * (hi - lo) * nodes + 0.5 * (hi + lo)
+            quad = 0.5 * (hi - lo) * (mapping.kernel_z(xs, n) * wts).sum()
+        exact = mapping.kernel_g(b, n) - mapping.kernel_g(a, n)
+        assert abs(exact - quad) < 1e-14
+
+
+@pytest.mark.parametrize("walls", [0, lat.ALL_WALLS])
+def test_weights_partition_of_unity(walls):
+    # Sum over nodes of int_{Omega_j} Z is one, also for a window cut by a wall
+    # (renormalised) or wrapping a periodic face.
+    rng = np.random.default_rng(8)
+    dims = (12, 10, 14)
+    for _ in range(20):
+        d = rng.uniform(0.8, 2.5)
+        n = 1.5 * d
+        xb = [rng.uniform(0.0, L) for L in dims]
+        w = mapping.node_weights(xb, n, dims, walls)
+        assert abs(w.sum() - 1.0) < 1e-13
+        assert (w >= 0.0).all()
+
+
+def test_unclipped_weights_need_no_renormalisation():
+    # Away from walls the raw tensor-product cell integrals already sum to one.
+    dims = (16, 16, 16)
+    per = [False, False, False]
+    xb = (7.3, 8.1, 8.9)
+    n = 3.0
+    w = [mapping.axis_weights(xb[a], n, dims[a], per[a]) for a in range(3)]
+    assert abs(w[0].sum() * w[1].sum() * w[2].sum() - 1.0) < 1e-14
+
+
+def test_spreading_equal_and_opposite():
+    # Eq. 21: the spread field carries exactly the bubbles' total reaction.
+    rng = np.random.default_rng(9)
+    dims = (10, 9, 12)
+    psis = [1e-5 * rng.standard_normal(3) for _ in range(4)]
+    xbs = [[rng.uniform(0.5, L - 0.5) for L in dims] for _ in range(4)]
+    ns = [1.5 * rng.uniform(1.0, 2.0) for _ in range(4)]
+    phi = mapping.spread(psis, xbs, ns, dims, lat.ALL_WALLS)
+    assert np.allclose(phi.sum(axis=(1, 2, 3)), np.sum(psis, axis=0), rtol=1e-13, atol=0)
+
+
+def test_interpolation_of_constant_field():
+    # Eq. 20 reproduces a uniform field exactly (follows from the partition of unity).
+    dims = (8, 8, 10)
+    sigma = np.empty((3,) + dims[::-1])
+    sigma[0], sigma[1], sigma[2] = 1.5e-4, -2e-5, 3e-4
+    out = mapping.interpolate(sigma, (0.9, 4.4, 9.6), 2.25, lat.ALL_WALLS)
+    assert np.allclose(out, [1.5e-4, -2e-5, 3e-4], rtol=1e-13, atol=0)
+
+
+def test_window_support_by_hand():
+    # Bubble at x = 16.3 with d = 2 (n = 3): the window (13.3, 19.3) overlaps
+    # cells 13..19; at x = 1.0 it is cut by the wall to cells 0..3; on a
+    # periodic axis of length 8 it wraps to 6, 7, 0, 1, 2, 3.
+    assert binning.support_cells(16.3, 3.0, 64, False) == list(range(13, 20))
+    assert binning.support_cells(1.0, 3.0, 64, False) == [0, 1, 2, 3]
+    assert binning.support_cells(1.0, 3.0, 8, True) == [6, 7, 0, 1, 2, 3]
+    # Integer window ends: (14, 20) overlaps cells 14..19 exactly.
+    assert binning.support_cells(17.0, 3.0, 64, False) == list(range(14, 20))
+    assert binning.containing_cell((16.3, 16.7, 8.2), (32, 32, 64)) == (8 * 32 + 16) * 32 + 16
+
+
+def test_tile_lists_by_hand():
+    # 64 x 8 x 8 box, tiles 32 x 4 x 4.  Bubble 0 at (31.5, 1.5, 6.5), n = 1.5:
+    # x cells 30..32 -> x tiles 0, 1; y cells 0..2 -> tile 0; z cells 5..7 -> tile 1.
+    # Bubble 1 (inactive) is ignored; bubble 2 at (5, 5, 1), n = 0.75: x 4..5,
+    # y 4..5, z 0..1 -> tile (0, 1, 0).
+    dims, tile = (64, 8, 8), (32, 4, 4)
+    xs = [(31.5, 1.5, 6.5), (10.0, 2.0, 2.0), (5.0, 5.0, 1.0)]
+    ns = [1.5, 1.5, 0.75]
+    off, items = binning.tile_lists(xs, ns, [True, False, True], dims, lat.ALL_WALLS, tile)
+    # tiles per axis (2, 2, 2): id = (tz * 2 + ty) * 2 + tx
+    expect = {4: [0], 5: [0], 2: [2]}
+    for t in range(8):
+        assert items[off[t]:off[t + 1]] == expect.get(t, [])
