@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled D3Q19 LBGK-LPT step (arXiv:1710.07073) on GB300.
+
+Metric: coupled-step MLUPS (million lattice-site updates per second) and the
+fraction of the HBM roofline reached by the fused collide-stream kernel.
+
+A step is one pass of the whole hot path: bubble update with forward coupling,
+binning, and the fused collide-stream sweep with backward coupling.  The
+default workload is the large single column: 256x256x512 sites, omega 1.6,
+half-way bounce-back on all six walls, one bubble of diameter 2 released at
+rest at (128, 128, 64), FP32 populations.  The 2.55 GB population state is far
+larger than L2, so no flush is needed between steps.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded crop of the same
+workload instead.  Under torchrun each rank runs an independent replica of the
+column on its own GPU (the method is not sharded), and rank 0 prints one JSON
+line with the whole-job throughput.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled D3Q19 step MLUPS & % HBM roofline, FP32 vs FP16-store at <=1% u_t error"
+FALLBACK_HBM_GBS = 6800.0
+STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
+STORAGE_SCALE = {"f32": 1.0, "f16": 256.0, "bf16": 1.0}
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
+KERNEL_SOURCES = ("paper_1710_07073_gb300/csrc/lbm_collide.cu",
+                  "paper_1710_07073_gb300/csrc/lbm_device.cuh",
+                  "paper_1710_07073_gb300/csrc/lbm_internal.cuh")
+
+
+def workload(name):
+    from paper_1710_07073_gb300 import workloads as wl
+    if name == "single_large":
+        dims = wl.SINGLE_LARGE
+        pos, vel, diam = wl.single_bubble(dims)
+        return dict(name="single bubble column 256x256x512", dims=dims, omega=1.6,
+                    pos=pos, vel=vel, diam=diam, g=1e-5)
+    if name == "swarm":
+        dims = wl.SWARM_FULL
+        pos, vel, diam = wl.swarm(dims, 100_000, seed=1234)
+        return dict(name="dispersed swarm 384x384x768, 100000 bubbles", dims=dims, omega=1.7,
+                    pos=pos, vel=vel, diam=diam, g=1e-5)
+    raise SystemExit("unknown workload %s" % name)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profile_traffic(storage, dims):
+    """DRAM bytes per collide-stream launch from the committed ncu summary, if it
+    was taken on the current kernel source for this storage and lattice."""
+    try:
+        with open(PROFILE_SUMMARY) as fh:
+            prof = json.load(fh)
+    except Exception:
+        return None
+    entry = prof.get("%s_%dx%dx%d" % (storage, *dims))
+    if not entry or entry.get("kernel_hash") != kernel_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self):
+        self.marks.append(time.perf_counter())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        t0, t1 = (self.marks + [0, 0])[:2] if len(self.marks) >= 2 else (0, float("inf"))
+        rows = [l for (t, l) in self.lines if t0 <= t <= t1] or [l for (_, l) in self.lines[-5:]]
+        window = "timed region" if any(t0 <= t <= t1 for (t, _) in self.lines) else "around timed region"
+        mhz, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for row in rows:
+            parts = [p.strip() for p in row.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz), "window": window}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_mlups(wl, sample_sites, steps, warmup=0):
+    """Time the FP64 oracle on a crop of the workload centred on its bubbles.
+
+    The crop is a wall-bounded box of about ``sample_sites`` sites holding the
+    bubbles that fit inside it; returns (MLUPS, seconds, description)."""
+    from oracle.step import OracleSim
+    from oracle import bubble as obub
+    dims = wl["dims"]
+    cz = int(min(dims[2], max(16, min(64, sample_sites // 256))))
+    cxy = int(max(16, min(dims[0], int((sample_sites / cz) ** 0.5) // 8 * 8)))
+    crop = (min(cxy, dims[0]), min(cxy, dims[1]), cz)
+    centre = np.median(wl["pos"], axis=0)
+    lo = np.array([min(max(int(centre[a] - crop[a] / 2), 0), dims[a] - crop[a]) for a in range(3)],
+                  dtype=np.float64)
+    rel = wl["pos"] - lo
+    r = 0.5 * wl["diam"][:, None]
+    sel = ((rel >= r) & (rel <= np.array(crop) - r)).all(axis=1)
+    sim = OracleSim(crop, wl["omega"], 0x3F, obub.BubbleParams(wl["omega"], g=wl["g"]))
+    sim.set_bubbles(rel[sel], wl["vel"][sel], wl["diam"][sel])
+    for _ in range(warmup):
+        sim.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step()
+    dt = time.perf_counter() - t0
+    sites = crop[0] * crop[1] * crop[2]
+    desc = "%dx%dx%d crop of the workload at %s with %d bubble(s), %d step(s)" % (
+        crop[0], crop[1], crop[2], lo.astype(int).tolist(), int(sel.sum()), steps)
+    return sites * steps / dt / 1e6, dt, desc
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    # Keep the whole run within about two minutes at ~1 MLUPS.
+    sample = int(max(16384, min(1 << 20, 1.0e8 / max(1, args.steps + args.warmup))))
+    t_start = time.perf_counter()
+    value, dt, desc = oracle_mlups(wl, sample, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / max(1, args.steps), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "dims": list(wl["dims"]), "omega": wl["omega"],
+                   "sample": desc},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": round(time.perf_counter() - t_start, 2),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, wl):
+    import torch
+    from paper_1710_07073_gb300 import lbm
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU; the CPU oracle is only timed with --impl reference")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lbm.lib()   # fails loudly if the CUDA library is missing
+
+    storage = args.storage
+    dims = wl["dims"]
+    S = int(np.prod(dims))
+    stream = torch.cuda.Stream()
+    params = lbm.lbm_default_params()
+    params.g = wl["g"]
+
+    with torch.cuda.stream(stream):
+        col = lbm.Column(dims, wl["omega"], lbm.LBM_WALL_ALL, STORAGES[storage],
+                         STORAGE_SCALE[storage], params=params, torch_plumbing=True)
+        ctx = col.ctx
+        lbm.lbm_set_bubbles(ctx, wl["pos"].reshape(-1), wl["vel"].reshape(-1), wl["diam"])
+        lbm.lbm_step(ctx, args.warmup)
+
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3 if sampler.proc else 0.0)
+        lbm.lbm_set_kernel_timing(ctx, True)
+        launches0 = lbm.lbm_launch_count(ctx)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler.mark()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lbm.lbm_step(ctx, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sampler.mark()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = lbm.lbm_launch_count(ctx) - launches0
+        k_ms, k_n = lbm.lbm_get_kernel_time(ctx)
+        lbm.lbm_set_kernel_timing(ctx, False)
+        time.sleep(0.2 if sampler.proc else 0.0)
+        clocks = sampler.stop()
+
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * S * args.steps / (ms * 1e-3) / 1e6
+
+        # End to end through the public API with host buffers: upload the
+        # initial fields and bubbles from pinned memory, step, read the bubbles
+        # back after every step, download the final fields.
+        nb = wl["diam"].size
+        rho_h = torch.ones(S, dtype=torch.float64).pin_memory().numpy()
+        u_h = torch.zeros(3 * S, dtype=torch.float64).pin_memory().numpy()
+        rho_o = torch.empty(S, dtype=torch.float64).pin_memory().numpy()
+        u_o = torch.empty(3 * S, dtype=torch.float64).pin_memory().numpy()
+        pos_h = torch.from_numpy(wl["pos"].reshape(-1).copy()).pin_memory().numpy()
+        vel_h = torch.from_numpy(wl["vel"].reshape(-1).copy()).pin_memory().numpy()
+        d_h = torch.from_numpy(wl["diam"].copy()).pin_memory().numpy()
+        lbm.lbm_set_fields(ctx, rho_h, u_h)          # warm the allocator's staging blocks
+        lbm.lbm_get_fields(ctx, out_rho=rho_o, out_u=u_o)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lbm.lbm_set_fields(ctx, rho_h, u_h)
+        lbm.lbm_set_bubbles(ctx, pos_h, vel_h, d_h)
+        for _ in range(args.steps):
+            lbm.lbm_step(ctx, 1)
+            lbm.lbm_get_bubbles(ctx)
+        lbm.lbm_get_fields(ctx, out_rho=rho_o, out_u=u_o)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_value = world * S * args.steps / e2e_s / 1e6
+        h2d = (4 * 8 * S + 7 * 8 * nb) / args.steps
+        d2h = (4 * 8 * S) / args.steps + (12 * 8 + 4) * nb
+        col.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    bytes_per_site = 2 * 19 * (4 if storage == "f32" else 2)
+    avg_kernel_s = (k_ms / max(1, k_n)) * 1e-3
+    achieved = bytes_per_site * S / avg_kernel_s / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = profile_traffic(storage, dims)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt, desc = oracle_mlups(wl, 1 << 20, 8, warmup=1)
+        cpu = {"value": round(v, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": desc + " (%.1f s, numpy float64, single thread)" % dt}
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "dims": list(dims), "omega": wl["omega"],
+                   "bubbles": int(wl["diam"].size), "storage": storage,
+                   "walls": "bounce-back on all six faces",
+                   "l2": "inputs larger than L2 (%.2f GB populations), no flush" % (
+                       2 * 19 * S * (4 if storage == "f32" else 2) / 1e9 / 2),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": "k_collide_stream<%s>" % storage,
+                     "algorithmic_bytes_per_launch": bytes_per_site * S,
+                     "avg_launch_ms": round(avg_kernel_s * 1e3, 5), "launches": k_n,
+                     "peak_kind": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d, 1),
+                "d2h_bytes_per_step": round(d2h, 1)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
+    ap.add_argument("--workload", choices=("single_large", "swarm"), default="single_large")
+    ap.add_argument("--storage", choices=tuple(STORAGES), default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dims", default=None,
+                    help="override the lattice (nx,ny,nz) for profiling a smaller case")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = workload(args.workload)
+    if args.dims:
+        from paper_1710_07073_gb300 import workloads as wlm
+        dims = tuple(int(v) for v in args.dims.split(","))
+        if wl["diam"].size == 1:
+            pos, vel, diam = wlm.single_bubble(dims, float(wl["diam"][0]))
+        else:
+            pos, vel, diam = wlm.swarm(dims, wl["diam"].size, seed=1234)
+        wl.update(dims=dims, pos=pos, vel=vel, diam=diam,
+                  name="%s resized to %dx%dx%d" % (wl["name"], *dims))
+    if args.impl == "reference":
+        return run_reference(args, wl)
+    return run_gpu(args, wl)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * lbm.h -- C ABI of the GB300 LBGK-LPT bubble-column library (liblbm.so).
+ *
+ * The library advances one liquid column, discretised with the D3Q19 BGK
+ * lattice Boltzmann model, two-way coupled to Lagrangian point bubbles, as
+ * stated in arXiv:1710.07073:
+ *   - liquid: BGK collision with Guo forcing and streaming (Sec. 2.2,
+ *     Eq. 5-16), half-way bounce-back on wall faces (Sec. 3.3);
+ *   - bubbles: Newton's law with buoyancy, drag and added mass
+ *     (Sec. 2.1, Eq. 1-4, Table 1), sub-stepped as in Table 2;
+ *   - coupling: clipped fourth-order polynomial mapping (Sec. 3.2,
+ *     Eq. 18-21) for interpolation to the bubbles and spreading back;
+ *   - order of operations: Algorithm 1.
+ *
+ * Units are lattice units: dx = dt_l = 1, lattice speed e = 1.  Gravity acts
+ * along -z.  Every array crossing this ABI is a HOST array owned by the
+ * caller; the library copies in and out.  The library owns all device memory
+ * (allocated with cudaMalloc, or with the caller's allocator when one is set
+ * with lbm_set_allocator before the first device use).
+ *
+ * Layouts.  Site (i, j, k), 0 <= i < nx etc., has linear index
+ * s = (k * ny + j) * nx + i (x fastest).  Scalar fields are double[S],
+ * S = nx*ny*nz.  Vector fields are structure-of-arrays double[3*S]
+ * (all x components, then y, then z).  Per-bubble vectors are
+ * interleaved double[3*n] (x0, y0, z0, x1, ...).  Populations are
+ * double[19*S], direction-major, in the order returned by lbm_velocity_set.
+ *
+ * Errors.  Every int-returning call returns LBM_OK (0) or a negative
+ * LBM_ERR_* code; the context keeps a message readable with
+ * lbm_last_error.  LBM_ERR_UNSTABLE is sticky: once the liquid solver has
+ * flagged a non-finite value or |u| >= 0.3 (beyond the low-Mach range of
+ * Eq. 6) every later lbm_step returns it until the state is reset with
+ * lbm_set_fields or lbm_set_populations.
+ *
+ * Threads.  A context may be used from one host thread at a time.  All work
+ * is enqueued on the context's CUDA stream (lbm_set_stream); calls that
+ * return host data synchronise that stream.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define LBM_OK            0
+#define LBM_ERR_ARG      -1   /* invalid argument; nothing was changed        */
+#define LBM_ERR_ALLOC    -2   /* device allocation failed                     */
+#define LBM_ERR_UNSTABLE -3   /* liquid solver produced NaN/Inf or |u|>=0.3  */
+#define LBM_ERR_TIMEOUT  -4   /* reserved: a bounded device wait ran out      */
+#define LBM_ERR_CUDA     -5   /* a CUDA runtime call failed                   */
+#define LBM_ERR_STATE    -6   /* call not valid in the current state          */
+
+/* ---- walls: one bit per box face; a set bit is a half-way bounce-back
+ * no-slip wall (Sec. 3.3), a clear bit makes the axis periodic.  Both faces
+ * of an axis must agree. ---------------------------------------------------- */
+#define LBM_WALL_XM  0x01
+#define LBM_WALL_XP  0x02
+#define LBM_WALL_YM  0x04
+#define LBM_WALL_YP  0x08
+#define LBM_WALL_ZM  0x10
+#define LBM_WALL_ZP  0x20
+#define LBM_WALL_ALL 0x3F
+
+/* ---- population storage precision (collision arithmetic is always FP32).
+ * Populations are stored shifted by their rest-state value w_j * rho_l:
+ *   F32 : f_j - w_j rho_l
+ *   F16 / BF16 : (f_j - w_j rho_l) * scale / w_j, rounded to nearest even. */
+#define LBM_STORE_F32  0
+#define LBM_STORE_F16  1
+#define LBM_STORE_BF16 2
+
+/* Largest bubble diameter accepted (lattice units); the mapping window
+ * n = width_factor * d must fit the library's fixed tile bookkeeping. */
+#define LBM_MAX_DIAMETER 6.0
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Closure and coupling parameters, lattice units (Table 1, Table 2, Eq. 3). */
+typedef struct lbm_params {
+    double g;             /* gravity magnitude, acting along -z            */
+    double rho_l;         /* liquid density; also the storage shift rho_0   */
+    double rho_ratio;     /* rho_b / rho_l                                  */
+    double sigma;         /* surface tension (enters Eo, Eq. 3)             */
+    double c_added_mass;  /* C_A of the virtual-mass force (Table 1: 0.5)   */
+    double drag_scale;    /* multiplies F_D (1.0 = Table 1)                 */
+    double sn_coeff;      /* a in 24/Re (1 + a Re^b) (0.15)                 */
+    double sn_exp;        /* b in 24/Re (1 + a Re^b) (0.687)                */
+    double width_factor;  /* mapping half-width n = width_factor * d_b (1.5)*/
+    int    substeps;      /* bubble sub-steps per liquid step (Table 2: 10) */
+    int    two_way;       /* 1: spread the reaction onto the liquid (Eq. 21)*/
+} lbm_params;
+
+typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
+typedef void  (*lbm_free_fn)(void* ptr, size_t bytes, void* user);
+
+/* Fill *p with the defaults: g=1e-5, rho_l=1, rho_ratio=1e-3,
+ * sigma=5.84e-6, C_A=0.5, drag_scale=1, sn_coeff=0.15, sn_exp=0.687,
+ * width_factor=1.5, substeps=10, two_way=1. */
+void lbm_default_params(lbm_params* p);
+
+/* Velocity set and weights in the library's direction order (Eq. 7-8):
+ * c[3*j + a] is component a of c_j, w[j] its weight.  Either may be NULL. */
+void lbm_velocity_set(int* c57, double* w19);
+
+/* Create a context for an nx*ny*nz column with relaxation frequency omega
+ * (Eq. 9: nu = (1/omega - 1/2)/3; omega must lie in (0, 2)) and the given
+ * wall bits, FP32 storage.  The liquid starts at f = f^eq(rho_l, 0)
+ * (Algorithm 1 initialisation).  Device memory is allocated on first use.
+ * Returns LBM_ERR_ARG for non-positive sizes, S >= 2^31 sites, omega out of
+ * range or mismatched wall bits. */
+int lbm_create(int nx, int ny, int nz, double omega, unsigned walls, lbm_ctx** out);
+
+/* As lbm_create with a storage precision (LBM_STORE_*) and, for the 16-bit
+ * formats, the scale applied after dividing by w_j (ignored for F32). */
+int lbm_create_storage(int nx, int ny, int nz, double omega, unsigned walls,
+                       int storage, double scale, lbm_ctx** out);
+
+/* Free the context and all device memory it owns.  NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*) for all work. */
+int lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Route device allocations through alloc/free (e.g. a framework's caching
+ * allocator).  Must come before the first call that touches the device. */
+int lbm_set_allocator(lbm_ctx* ctx, lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user);
+
+int lbm_set_params(lbm_ctx* ctx, const lbm_params* p);
+int lbm_get_params(const lbm_ctx* ctx, lbm_params* p);
+
+/* Set the liquid to f = f^eq(rho, u) (Eq. 6; Algorithm 1 initialisation).
+ * rho: double[S] or NULL for rho_l everywhere; u3: double[3*S] SoA or NULL
+ * for rest.  Clears the sticky instability flag. */
+int lbm_set_fields(lbm_ctx* ctx, const double* rho, const double* u3);
+
+/* Set the pre-collision populations f_j(x, t) directly (double[19*S] in
+ * lbm_velocity_set order).  Clears the sticky instability flag. */
+int lbm_set_populations(lbm_ctx* ctx, const double* f);
+
+/* Read the pre-collision populations f_j(x, t) (double[19*S]). */
+int lbm_get_populations(lbm_ctx* ctx, double* f);
+
+/* Replace all bubbles.  pos3/vel3: double[3*n] interleaved; diam: double[n].
+ * Each centre must lie inside the box, 0 < d <= LBM_MAX_DIAMETER, and on a
+ * periodic axis the window must not wrap onto itself (2n + 2 <= L).  All
+ * bubbles start active with no liquid-velocity history (D_t u_l = 0 on
+ * their first step).  n = 0 removes all bubbles. */
+int lbm_set_bubbles(lbm_ctx* ctx, int n, const double* pos3, const double* vel3,
+                    const double* diam);
+
+/* Advance nsteps coupled steps (Algorithm 1 loop body), each:
+ *   1. per active bubble: interpolate the bare Eq. 10 liquid velocity of the
+ *      current populations to the centre (Eq. 19-20, window renormalised
+ *      over in-box nodes), run `substeps` explicit Newton updates (Eq. 4)
+ *      with m_eff = m_b + C_A rho_l V_b, form psi_b = -mean F_D;
+ *   2. bin the bubbles' windows to lattice tiles (Algorithm 1 step 2);
+ *   3. one fused collide-stream sweep: each node gathers its force Phi from
+ *      the bubbles binned to its tile (Eq. 21, fixed order, no atomics),
+ *      applies Eq. 13, 6, 14, 12, 15 and streams (Eq. 16) with bounce-back;
+ *   4. a bubble whose centre reached nz - r_b under a +z wall is deactivated
+ *      (Algorithm 1, stop at the top) after spreading this step.
+ * Returns after the work has completed, with LBM_ERR_UNSTABLE if flagged. */
+int lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Liquid density and bare Eq. 10 velocity u = sum c f / rho of the current
+ * pre-collision populations.  Either pointer may be NULL. */
+int lbm_get_fields(lbm_ctx* ctx, double* rho, double* u3);
+
+/* Copy out up to `cap` bubbles.  Any output pointer may be NULL.
+ * pos3, vel3: state after the last step; ul3: liquid velocity interpolated at
+ * the start of the last step; psi3: reaction spread in the last step;
+ * active: 1 while the bubble is coupled.  *n receives the bubble count. */
+int lbm_get_bubbles(lbm_ctx* ctx, int cap, int* n, double* pos3, double* vel3,
+                    double* ul3, double* psi3, int* active);
+
+/* FP64 totals over the box: out4 = {sum rho, sum rho u_x, sum rho u_y,
+ * sum rho u_z} of the current pre-collision populations (Eq. 10). */
+int lbm_get_totals(lbm_ctx* ctx, double* out4);
+
+/* Binning of the last step (Algorithm 1 step 2), for inspection.
+ * cell: int[n] linear id of the cell holding each bubble after its update
+ * (-1 when inactive); tile3: the tile shape (tx, ty, tz); *ntiles: tile
+ * count; offsets: int[ntiles+1]; items: int[cap_items] bubble ids, per tile in
+ * ascending order; *nitems: number of ids.  Any pointer may be NULL. */
+int lbm_get_bins(lbm_ctx* ctx, int* cell, int* tile3, int* ntiles, int* offsets,
+                 int* items, int cap_items, int* nitems);
+
+/* Number of lattice sites and bytes of population storage per site and step
+ * (read + write of all 19 populations). */
+long long lbm_sites(const lbm_ctx* ctx);
+int lbm_bytes_per_site(const lbm_ctx* ctx);
+
+/* Per-launch timing of the fused collide-stream kernel: when on, each launch
+ * is bracketed by CUDA events on the context stream; lbm_get_kernel_time
+ * returns the summed milliseconds and the launch count since timing was
+ * switched on (synchronises the stream). */
+int lbm_set_kernel_timing(lbm_ctx* ctx, int on);
+int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
+
+/* Number of kernels this context has launched since it was created. */
+long long lbm_launch_count(const lbm_ctx* ctx);
+
+/* Wait for all work enqueued by this context. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Message of the last error on this context ("" if none); never NULL. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Static name of a status code. */
+const char* lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

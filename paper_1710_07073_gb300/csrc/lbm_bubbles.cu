@@ -1,0 +1,617 @@
+// Bubble side of the coupled step and the field utilities.
+//
+//  k_bubbles      one warp per bubble: forward coupling (Eq. 19-20) of the bare
+//                 Eq. 10 liquid velocity, Table 1 forces, sub-stepped Newton
+//                 update (Eq. 4, Table 2), reaction psi_b = -mean F_D
+//                 (Algorithm 1 step 6) and the spreading record for the sweep.
+//  binning        bubble windows to lattice tiles (Algorithm 1 step 2):
+//                 integer counting sort, then each tile's list in bubble order.
+//  field kernels  initialisation to f^eq (Eq. 6), population I/O, Eq. 10
+//                 moments and FP64 totals.
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Bubble update
+// ---------------------------------------------------------------------------
+
+// Window normalisation along one axis: the integral of the mapping over the
+// in-box part of [-n, n] (without 15/16); the full 16/15 on a periodic axis.
+__device__ __forceinline__ double axis_norm(double xa, double n, int L, bool periodic) {
+    if (periodic) return cell_poly_d(-1.0, 1.0);
+    return cell_poly_d(-xa / n, ((double)L - xa) / n);
+}
+
+__device__ __forceinline__ void make_record(const double* xb, double n, const Geo& g,
+                                            const double* psi, BubbleRec& r) {
+    int anc[3];
+    float fr[3];
+    double norm = 1.0;
+    const int L[3] = {g.nx, g.ny, g.nz};
+    for (int a = 0; a < 3; ++a) {
+        double fl = floor(xb[a]);
+        anc[a] = (int)fl;
+        fr[a] = (float)(xb[a] - fl);
+        norm *= axis_norm(xb[a], n, L[a], !(g.walls & (1u << (2 * a))));
+    }
+    r.ax = anc[0];
+    r.ay = anc[1];
+    r.az = anc[2];
+    r.pad = 0;
+    r.fx = fr[0];
+    r.fy = fr[1];
+    r.fz = fr[2];
+    r.inv_n = (float)(1.0 / n);
+    r.h = (float)(0.5 / n);
+    r.px = (float)(psi[0] / norm);
+    r.py = (float)(psi[1] / norm);
+    r.pz = (float)(psi[2] / norm);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(128)
+k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, BubbleDev B,
+          BubbleConst bc, int* __restrict__ flag) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= B.nb) return;
+    if (!B.active[b]) {
+        if (lane == 0) {
+            B.spread[b] = 0;
+            B.cell[b] = -1;
+        }
+        return;
+    }
+    const int L[3] = {g.nx, g.ny, g.nz};
+    double xb[3] = {B.x[3 * b], B.x[3 * b + 1], B.x[3 * b + 2]};
+    const double n = B.n[b];
+    if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) {
+        // A non-finite centre can only come from an unstable liquid: stop
+        // coupling this bubble and report the instability.
+        if (lane == 0) {
+            B.active[b] = 0;
+            B.spread[b] = 0;
+            B.cell[b] = -1;
+            atomicOr(flag, 2);
+        }
+        return;
+    }
+
+    // Window cells per axis (Algorithm 1 step 2): cells overlapping (x - n, x + n).
+    int lo[3], cnt[3], anc[3];
+    float fr[3];
+    double norm = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const bool periodic = !(g.walls & (1u << (2 * a)));
+        int l = (int)floor(xb[a] - n);
+        int h = (int)ceil(xb[a] + n) - 1;
+        if (!periodic) {
+            l = max(l, 0);
+            h = min(h, L[a] - 1);
+        }
+        lo[a] = l;
+        cnt[a] = min(max(h - l + 1, 0), 2 * (int)MAX_HALF_WIDTH + 2);
+        double fl = floor(xb[a]);
+        anc[a] = (int)fl;
+        fr[a] = (float)(xb[a] - fl);
+        norm *= axis_norm(xb[a], n, L[a], periodic);
+    }
+    const float inv_n = (float)(1.0 / n), hh = (float)(0.5 / n);
+
+    // Forward coupling (Eq. 20): lanes stride over the window's nodes.
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+    const int M = cnt[0] * cnt[1] * cnt[2];
+    for (int m = lane; m < M; m += 32) {
+        const int ix = m % cnt[0];
+        const int rest = m / cnt[0];
+        const int iy = rest % cnt[1];
+        const int iz = rest / cnt[1];
+        const int i = lo[0] + ix, j = lo[1] + iy, k = lo[2] + iz;
+        const float w = cell_poly(((float)(i - anc[0]) + 0.5f - fr[0]) * inv_n, hh) *
+                        cell_poly(((float)(j - anc[1]) + 0.5f - fr[1]) * inv_n, hh) *
+                        cell_poly(((float)(k - anc[2]) + 0.5f - fr[2]) * inv_n, hh);
+        const int iw = (i % g.nx + g.nx) % g.nx;
+        const int jw = (j % g.ny + g.ny) % g.ny;
+        const int kw = (k % g.nz + g.nz) % g.nz;
+        float gv[Q];
+        gather<ST>(f, g, cp, iw, jw, kw, gv);
+        float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            drho += gv[q];
+            if (cx(q) != 0) jx += (float)cx(q) * gv[q];
+            if (cy(q) != 0) jy += (float)cy(q) * gv[q];
+            if (cz(q) != 0) jz += (float)cz(q) * gv[q];
+        }
+        const float inv_rho = 1.0f / (cp.rho0 + drho);
+        ax = fmaf(w, jx * inv_rho, ax);
+        ay = fmaf(w, jy * inv_rho, ay);
+        az = fmaf(w, jz * inv_rho, az);
+    }
+    double sx = ax, sy = ay, sz = az;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane != 0) return;
+
+    const double ul[3] = {sx / norm, sy / norm, sz / norm};
+    double dul[3] = {0.0, 0.0, 0.0};
+    if (B.has_prev[b]) {
+        for (int a = 0; a < 3; ++a) dul[a] = (ul[a] - B.ulprev[3 * b + a]) / bc.dt_l;
+    }
+
+    // Table 1 forces and the Newton update of Eq. 4 with the added mass on
+    // the left (m_eff), sub-stepped with dt_b (Table 2).
+    const double d = B.d[b];
+    const double r = 0.5 * d;
+    const double vol = M_PI * d * d * d / 6.0;
+    const double meff = (bc.rho_b + bc.c_am * bc.rho_l) * vol;
+    const double fb = (bc.rho_l - bc.rho_b) * vol * bc.g;
+    const double eo = (bc.rho_l - bc.rho_b) * bc.g * d * d / bc.sigma;
+    const double eo_term = 8.0 / 3.0 * eo / (eo + 4.0);
+    const double drag_pref = 0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale;
+    const double visc_a0 = 24.0 * bc.nu / d, visc_b = 48.0 * bc.nu / d;
+    const double fvm[3] = {bc.c_am * bc.rho_l * vol * dul[0], bc.c_am * bc.rho_l * vol * dul[1],
+                           bc.c_am * bc.rho_l * vol * dul[2]};
+    double u[3] = {B.u[3 * b], B.u[3 * b + 1], B.u[3 * b + 2]};
+    double fd_sum[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < bc.substeps; ++k) {
+        const double v0 = u[0] - ul[0], v1 = u[1] - ul[1], v2 = u[2] - ul[2];
+        const double speed = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+        const double re = speed * d / bc.nu;
+        const double visc_a = visc_a0 * (1.0 + bc.sn_coeff * pow(re, bc.sn_exp));
+        const double cdv = fmax(fmin(visc_a, visc_b), eo_term * speed);   // C_D |v|
+        const double fd[3] = {-drag_pref * cdv * v0, -drag_pref * cdv * v1,
+                              -drag_pref * cdv * v2};
+        const double fz_buoy[3] = {0.0, 0.0, fb};
+        for (int a = 0; a < 3; ++a) {
+            fd_sum[a] += fd[a];
+            u[a] = u[a] + (fz_buoy[a] + fd[a] + fvm[a]) / meff * bc.dt_b;
+            xb[a] = xb[a] + u[a] * bc.dt_b;
+            if (g.walls & (1u << (2 * a))) {
+                if (xb[a] < r) {
+                    xb[a] = r;
+                    u[a] = fmax(u[a], 0.0);
+                }
+                if (xb[a] > (double)L[a] - r) {
+                    xb[a] = (double)L[a] - r;
+                    u[a] = fmin(u[a], 0.0);
+                }
+            } else {
+                xb[a] = __dsub_rn(xb[a], __dmul_rn((double)L[a], floor(xb[a] / (double)L[a])));
+            }
+        }
+    }
+    double psi[3];
+    for (int a = 0; a < 3; ++a) {
+        psi[a] = -fd_sum[a] / (double)bc.substeps;
+        B.x[3 * b + a] = xb[a];
+        B.u[3 * b + a] = u[a];
+        B.ul[3 * b + a] = ul[a];
+        B.ulprev[3 * b + a] = ul[a];
+        B.psi[3 * b + a] = psi[a];
+    }
+    B.has_prev[b] = 1;
+    if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]) && isfinite(u[0]) &&
+          isfinite(u[1]) && isfinite(u[2]) && isfinite(psi[0]) && isfinite(psi[1]) &&
+          isfinite(psi[2]))) {
+        B.active[b] = 0;
+        B.spread[b] = 0;
+        B.cell[b] = -1;
+        atomicOr(flag, 2);
+        return;
+    }
+    B.spread[b] = 1;
+    int ci[3];
+    for (int a = 0; a < 3; ++a) ci[a] = min(max((int)floor(xb[a]), 0), L[a] - 1);
+    B.cell[b] = (ci[2] * g.ny + ci[1]) * g.nx + ci[0];
+    make_record(xb, n, g, psi, B.rec[b]);
+    // Algorithm 1: the bubble stops once it reaches the top of the liquid.
+    if ((g.walls & 0x20) && xb[2] >= (double)g.nz - r) B.active[b] = 0;
+}
+
+cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                           const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    const int threads = 128;
+    const int blocks = (b.nb * 32 + threads - 1) / threads;
+    switch (storage) {
+        case 0: k_bubbles<0><<<blocks, threads, 0, st>>>((const float*)f, g, cp, b, bc, flag); break;
+        case 1: k_bubbles<1><<<blocks, threads, 0, st>>>((const __half*)f, g, cp, b, bc, flag); break;
+        default:
+            k_bubbles<2><<<blocks, threads, 0, st>>>((const __nv_bfloat16*)f, g, cp, b, bc, flag);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Binning (Algorithm 1 step 2): bubble windows -> tiles, deterministic lists
+// ---------------------------------------------------------------------------
+
+// Tiles of one axis holding at least one window cell, ascending.
+__device__ int axis_tiles(double xa, double n, int L, bool periodic, int T,
+                          int out[MAX_AXIS_TILES]) {
+    int lo = (int)floor(xa - n);
+    int hi = (int)ceil(xa + n) - 1;
+    int cnt = 0;
+    if (!periodic) {
+        lo = max(lo, 0);
+        hi = min(hi, L - 1);
+        for (int t = lo / T; t <= hi / T && cnt < MAX_AXIS_TILES; ++t) out[cnt++] = t;
+        return cnt;
+    }
+    for (int c = lo; c <= hi; ++c) {
+        const int t = ((c % L + L) % L) / T;
+        bool seen = false;
+        for (int q = 0; q < cnt; ++q) seen |= (out[q] == t);
+        if (!seen && cnt < MAX_AXIS_TILES) out[cnt++] = t;
+    }
+    for (int i = 1; i < cnt; ++i) {   // insertion sort, at most a few entries
+        int v = out[i], k = i - 1;
+        while (k >= 0 && out[k] > v) {
+            out[k + 1] = out[k];
+            --k;
+        }
+        out[k + 1] = v;
+    }
+    return cnt;
+}
+
+template <bool FILL>
+__global__ void k_bin(Geo g, BubbleDev B, Bins bins) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nb || !B.spread[b]) return;
+    const int L[3] = {g.nx, g.ny, g.nz};
+    const int T[3] = {TX, TY, TZ};
+    int tl[3][MAX_AXIS_TILES];
+    int nt[3];
+    const double n = B.n[b];
+    for (int a = 0; a < 3; ++a)
+        nt[a] = axis_tiles(B.x[3 * b + a], n, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
+    for (int iz = 0; iz < nt[2]; ++iz)
+        for (int iy = 0; iy < nt[1]; ++iy)
+            for (int ix = 0; ix < nt[0]; ++ix) {
+                const int t = (tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix];
+                const int pos = atomicAdd(&bins.cnt[t], 1);
+                if (FILL) {
+                    const int at = bins.off[t] + pos;
+                    if (at < bins.cap) bins.items[at] = b;
+                    else atomicOr(bins.overflow, 1);
+                }
+            }
+}
+
+// Sort each tile's list by bubble id so the gather order is fixed.
+__global__ void k_bin_sort(Bins bins) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= bins.T) return;
+    const int beg = bins.off[t], end = min(bins.off[t + 1], bins.cap);
+    for (int i = beg + 1; i < end; ++i) {
+        const int v = bins.items[i];
+        int k = i - 1;
+        while (k >= beg && bins.items[k] > v) {
+            bins.items[k + 1] = bins.items[k];
+            --k;
+        }
+        bins.items[k + 1] = v;
+    }
+}
+
+// Exclusive scan of counts into offsets (3 passes, 1024 counts per block).
+constexpr int SCAN_BLOCK = 256, SCAN_ITEMS = 4, SCAN_CHUNK = SCAN_BLOCK * SCAN_ITEMS;
+
+int scan_blocks(int T) { return (T + SCAN_CHUNK - 1) / SCAN_CHUNK; }
+
+__device__ int block_exclusive_scan(int v, int* warp_sums, int& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sums[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+        int si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += t;
+        }
+        if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = si - s;
+        if (lane == (int)(blockDim.x >> 5) - 1) warp_sums[32] = si;
+    }
+    __syncthreads();
+    const int res = warp_sums[wid] + incl - v;
+    total = warp_sums[32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_local(const int* cnt, int* off, int T,
+                                                            int* block_sums) {
+    __shared__ int ws[33];
+    const int base = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = (base + k < T) ? cnt[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, ws, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < T) off[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sums(int* block_sums, int nblocks, int* off,
+                                                           int T) {
+    __shared__ int ws[33];
+    int carry = 0;
+    for (int c0 = 0; c0 < nblocks; c0 += SCAN_BLOCK) {
+        const int i = c0 + threadIdx.x;
+        const int v = i < nblocks ? block_sums[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, ws, total);
+        if (i < nblocks) block_sums[i] = ex + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) off[T] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_add(int* off, int T, const int* block_sums) {
+    const int base = blockIdx.x * SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
+    const int add = block_sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < T) off[base + k] += add;
+}
+
+cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(bins.cnt, 0, sizeof(int) * (size_t)bins.T, st);
+    if (e != cudaSuccess) return e;
+    const int tb = 128;
+    const int bb = (b.nb + tb - 1) / tb;
+    if (b.nb > 0) k_bin<false><<<bb, tb, 0, st>>>(g, b, bins);
+    k_scan_local<<<bins.nblocks, SCAN_BLOCK, 0, st>>>(bins.cnt, bins.off, bins.T, bins.block_sums);
+    k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(bins.block_sums, bins.nblocks, bins.off, bins.T);
+    k_scan_add<<<bins.nblocks, SCAN_BLOCK, 0, st>>>(bins.off, bins.T, bins.block_sums);
+    e = cudaMemsetAsync(bins.cnt, 0, sizeof(int) * (size_t)bins.T, st);
+    if (e != cudaSuccess) return e;
+    if (b.nb > 0) k_bin<true><<<bb, tb, 0, st>>>(g, b, bins);
+    k_bin_sort<<<(bins.T + 127) / 128, 128, 0, st>>>(bins);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Field utilities
+// ---------------------------------------------------------------------------
+
+// Eq. 10 moments of the pre-collision populations, FP64.
+template <int ST>
+__global__ void k_fields(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
+                         double* __restrict__ rho, double* __restrict__ u) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.S) return;
+    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    float gv[Q];
+    gather<ST>(f, g, cp, x, y, z, gv);
+    double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        drho += gv[j];
+        jx += cx(j) * (double)gv[j];
+        jy += cy(j) * (double)gv[j];
+        jz += cz(j) * (double)gv[j];
+    }
+    const double r = (double)cp.rho0 + drho;
+    if (rho) rho[s] = r;
+    if (u) {
+        u[s] = jx / r;
+        u[g.S + s] = jy / r;
+        u[2 * g.S + s] = jz / r;
+    }
+}
+
+template <int ST>
+__global__ void k_get_pop(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
+                          double* __restrict__ out) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.S) return;
+    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    float gv[Q];
+    gather<ST>(f, g, cp, x, y, z, gv);
+#pragma unroll
+    for (int j = 0; j < Q; ++j) out[(size_t)j * g.S + s] = wd(j) * (double)cp.rho0 + (double)gv[j];
+}
+
+// Where the stored (post-collision) value of direction j at node y comes
+// from: the population j of node y + c_j, or -- if that link crosses a
+// wall -- the population opp(j) of node y itself (inverse of the pull).
+__device__ __forceinline__ void push_target(const Geo& g, int j, int x, int y, int z, int& dir,
+                                            long long& node) {
+    int tx = x + cx(j), ty = y + cy(j), tz = z + cz(j);
+    bool bounce = false;
+    if (cx(j) != 0 && (tx < 0 || tx >= g.nx)) {
+        if (g.walls & 0x01) bounce = true;
+        else tx = tx < 0 ? tx + g.nx : tx - g.nx;
+    }
+    if (cy(j) != 0 && (ty < 0 || ty >= g.ny)) {
+        if (g.walls & 0x04) bounce = true;
+        else ty = ty < 0 ? ty + g.ny : ty - g.ny;
+    }
+    if (cz(j) != 0 && (tz < 0 || tz >= g.nz)) {
+        if (g.walls & 0x10) bounce = true;
+        else tz = tz < 0 ? tz + g.nz : tz - g.nz;
+    }
+    if (bounce) {
+        dir = opp(j);
+        node = site_index(g, x, y, z);
+    } else {
+        dir = j;
+        node = site_index(g, tx, ty, tz);
+    }
+}
+
+template <int ST>
+__global__ void k_set_pop(const double* __restrict__ fin, typename Store<ST>::T* __restrict__ f,
+                          Geo g, CollideParams cp) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.S) return;
+    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    for (int j = 0; j < Q; ++j) {
+        int dir;
+        long long node;
+        push_target(g, j, x, y, z, dir, node);
+        const double v = fin[(size_t)dir * g.S + node] - wd(dir) * (double)cp.rho0;
+        f[(size_t)j * g.S + s] = Store<ST>::from_double(v, j, cp);
+    }
+}
+
+// f = f^eq(rho, u) of Eq. 6, stored shifted: g^eq_j = w_j [drho + rho (3cu + 4.5cu^2 - 1.5u^2)].
+template <int ST>
+__global__ void k_set_feq(const double* __restrict__ rho, const double* __restrict__ u,
+                          typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.S) return;
+    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    for (int j = 0; j < Q; ++j) {
+        int dir;
+        long long node;
+        push_target(g, j, x, y, z, dir, node);
+        const double r = rho ? rho[node] : (double)cp.rho0;
+        const double ux = u ? u[node] : 0.0, uy = u ? u[g.S + node] : 0.0,
+                     uz = u ? u[2 * g.S + node] : 0.0;
+        const double cu = cx(dir) * ux + cy(dir) * uy + cz(dir) * uz;
+        const double usq = ux * ux + uy * uy + uz * uz;
+        const double v = wd(dir) * ((r - (double)cp.rho0) + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
+        f[(size_t)j * g.S + s] = Store<ST>::from_double(v, j, cp);
+    }
+}
+
+// FP64 totals: per-block partial sums in fixed order, then one block.
+constexpr int TOT_BLOCK = 256;
+
+int totals_partials(const Geo& g) {
+    long long blocks = (g.S + TOT_BLOCK - 1) / TOT_BLOCK;
+    return (int)(blocks < 4096 ? blocks : 4096);
+}
+
+__device__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    return t;
+}
+
+template <int ST>
+__global__ void __launch_bounds__(TOT_BLOCK)
+k_totals(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, double* partials) {
+    __shared__ double sh[32];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < g.S;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny),
+                  z = (int)(s / ((long long)g.nx * g.ny));
+        float gv[Q];
+        gather<ST>(f, g, cp, x, y, z, gv);
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            acc[0] += gv[j];
+            acc[1] += cx(j) * (double)gv[j];
+            acc[2] += cy(j) * (double)gv[j];
+            acc[3] += cz(j) * (double)gv[j];
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        const double t = block_sum(acc[k], sh);
+        if (threadIdx.x == 0) partials[4 * blockIdx.x + k] = t;
+    }
+}
+
+__global__ void k_totals_final(const double* partials, int np, double mass0, double* out4) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < np; ++i)
+        for (int k = 0; k < 4; ++k) t[k] += partials[4 * i + k];
+    out4[0] = mass0 + t[0];
+    out4[1] = t[1];
+    out4[2] = t[2];
+    out4[3] = t[3];
+}
+
+static unsigned site_blocks(const Geo& g) { return (unsigned)((g.S + 255) / 256); }
+
+cudaError_t launch_fields(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                          double* rho, double* u, cudaStream_t st) {
+    switch (storage) {
+        case 0: k_fields<0><<<site_blocks(g), 256, 0, st>>>((const float*)f, g, cp, rho, u); break;
+        case 1: k_fields<1><<<site_blocks(g), 256, 0, st>>>((const __half*)f, g, cp, rho, u); break;
+        default:
+            k_fields<2><<<site_blocks(g), 256, 0, st>>>((const __nv_bfloat16*)f, g, cp, rho, u);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_populations(int storage, const void* f, const Geo& g,
+                                   const CollideParams& cp, double* out, cudaStream_t st) {
+    switch (storage) {
+        case 0: k_get_pop<0><<<site_blocks(g), 256, 0, st>>>((const float*)f, g, cp, out); break;
+        case 1: k_get_pop<1><<<site_blocks(g), 256, 0, st>>>((const __half*)f, g, cp, out); break;
+        default:
+            k_get_pop<2><<<site_blocks(g), 256, 0, st>>>((const __nv_bfloat16*)f, g, cp, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(int storage, const double* fin, void* f, const Geo& g,
+                                   const CollideParams& cp, cudaStream_t st) {
+    switch (storage) {
+        case 0: k_set_pop<0><<<site_blocks(g), 256, 0, st>>>(fin, (float*)f, g, cp); break;
+        case 1: k_set_pop<1><<<site_blocks(g), 256, 0, st>>>(fin, (__half*)f, g, cp); break;
+        default: k_set_pop<2><<<site_blocks(g), 256, 0, st>>>(fin, (__nv_bfloat16*)f, g, cp);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_equilibrium(int storage, const double* rho, const double* u, void* f,
+                                   const Geo& g, const CollideParams& cp, cudaStream_t st) {
+    switch (storage) {
+        case 0: k_set_feq<0><<<site_blocks(g), 256, 0, st>>>(rho, u, (float*)f, g, cp); break;
+        case 1: k_set_feq<1><<<site_blocks(g), 256, 0, st>>>(rho, u, (__half*)f, g, cp); break;
+        default:
+            k_set_feq<2><<<site_blocks(g), 256, 0, st>>>(rho, u, (__nv_bfloat16*)f, g, cp);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                          double* partials, int npartials, double* out4, cudaStream_t st) {
+    switch (storage) {
+        case 0: k_totals<0><<<npartials, TOT_BLOCK, 0, st>>>((const float*)f, g, cp, partials); break;
+        case 1: k_totals<1><<<npartials, TOT_BLOCK, 0, st>>>((const __half*)f, g, cp, partials); break;
+        default:
+            k_totals<2><<<npartials, TOT_BLOCK, 0, st>>>((const __nv_bfloat16*)f, g, cp, partials);
+    }
+    k_totals_final<<<1, 32, 0, st>>>(partials, npartials, (double)g.S * (double)cp.rho0, out4);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,692 @@
+// Host side of the C ABI declared in include/lbm.h: argument checks, device
+// state, and the order of launches of one coupled step (Algorithm 1 of
+// arXiv:1710.07073).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    unsigned walls = 0;
+    double omega = 1.0;
+    int storage = LBM_STORE_F32;
+    double scale = 1.0;
+    lbm_params p{};
+    cudaStream_t stream = nullptr;
+    lbm_alloc_fn af = nullptr;
+    lbm_free_fn ff = nullptr;
+    void* au = nullptr;
+
+    bool dev_ready = false;
+    int device = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    int* flag_d = nullptr;
+    int* flag_h = nullptr;       // pinned
+    bool unstable = false;
+
+    // bubbles
+    BubbleDev bub{};
+    int nb_cap = 0;
+    // bins
+    Bins bins{};
+    bool bins_valid = false;
+
+    // timing of the collide-stream launches
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+
+    long long launches = 0;      // kernels enqueued by this context
+
+    std::vector<std::pair<void*, size_t>> allocs;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(call, what)                                 \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+void* dalloc(lbm_ctx* c, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (c->af) {
+        p = c->af(bytes, c->au);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocs.emplace_back(p, bytes);
+    return p;
+}
+
+void dfree(lbm_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i) {
+        if (c->allocs[i].first == p) {
+            if (c->ff) c->ff(p, c->allocs[i].second, c->au);
+            else cudaFree(p);
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+size_t elem_size(int storage) { return storage == LBM_STORE_F32 ? 4 : 2; }
+
+Geo geo_of(const lbm_ctx* c) {
+    Geo g;
+    g.nx = c->nx;
+    g.ny = c->ny;
+    g.nz = c->nz;
+    g.walls = c->walls;
+    g.S = (long long)c->nx * c->ny * c->nz;
+    g.ntx = (c->nx + TX - 1) / TX;
+    g.nty = (c->ny + TY - 1) / TY;
+    g.ntz = (c->nz + TZ - 1) / TZ;
+    return g;
+}
+
+CollideParams collide_params(const lbm_ctx* c) {
+    CollideParams cp;
+    cp.omega = (float)c->omega;
+    cp.pref = (float)(1.0 - 0.5 * c->omega);
+    cp.rho0 = (float)c->p.rho_l;
+    cp.scale = (float)c->scale;
+    cp.inv_scale = (float)(1.0 / c->scale);
+    return cp;
+}
+
+BubbleConst bubble_const(const lbm_ctx* c) {
+    BubbleConst bc;
+    bc.g = c->p.g;
+    bc.rho_l = c->p.rho_l;
+    bc.rho_b = c->p.rho_ratio * c->p.rho_l;
+    bc.sigma = c->p.sigma;
+    bc.c_am = c->p.c_added_mass;
+    bc.drag_scale = c->p.drag_scale;
+    bc.sn_coeff = c->p.sn_coeff;
+    bc.sn_exp = c->p.sn_exp;
+    bc.nu = (2.0 / c->omega - 1.0) / 6.0;     // Eq. 9
+    bc.dt_l = 1.0;
+    bc.dt_b = 1.0 / c->p.substeps;            // Table 2: dt_b = dt_l / substeps
+    bc.substeps = c->p.substeps;
+    return bc;
+}
+
+int ensure_device(lbm_ctx* c) {
+    if (c->dev_ready) return LBM_OK;
+    LBM_CUDA(cudaGetDevice(&c->device), "cudaGetDevice");
+    const Geo g = geo_of(c);
+    const size_t bytes = (size_t)Q * (size_t)g.S * elem_size(c->storage);
+    for (int k = 0; k < 2; ++k) {
+        c->f[k] = dalloc(c, bytes);
+        if (!c->f[k]) return fail(c, LBM_ERR_ALLOC, "population buffer of %zu bytes", bytes);
+    }
+    c->flag_d = (int*)dalloc(c, sizeof(int));
+    if (!c->flag_d) return fail(c, LBM_ERR_ALLOC, "flag");
+    LBM_CUDA(cudaMallocHost((void**)&c->flag_h, sizeof(int)), "cudaMallocHost");
+    // Rest state f = f^eq(rho_l, 0) has zero shifted value in every format.
+    LBM_CUDA(cudaMemsetAsync(c->f[0], 0, bytes, c->stream), "memset f");
+    LBM_CUDA(cudaMemsetAsync(c->flag_d, 0, sizeof(int), c->stream), "memset flag");
+    c->cur = 0;
+    // Tile bookkeeping.
+    c->bins.T = g.ntx * g.nty * g.ntz;
+    c->bins.nblocks = scan_blocks(c->bins.T);
+    c->bins.cnt = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.T);
+    c->bins.off = (int*)dalloc(c, sizeof(int) * ((size_t)c->bins.T + 1));
+    c->bins.block_sums = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.nblocks);
+    c->bins.overflow = (int*)dalloc(c, sizeof(int));
+    if (!c->bins.cnt || !c->bins.off || !c->bins.block_sums || !c->bins.overflow)
+        return fail(c, LBM_ERR_ALLOC, "tile bins");
+    LBM_CUDA(cudaMemsetAsync(c->bins.overflow, 0, sizeof(int), c->stream), "memset overflow");
+    c->bins.items = nullptr;
+    c->bins.cap = 0;
+    c->dev_ready = true;
+    return LBM_OK;
+}
+
+int check_walls(unsigned walls) {
+    if (walls & ~0x3Fu) return 0;
+    for (int a = 0; a < 3; ++a) {
+        bool lo = walls & (1u << (2 * a)), hi = walls & (1u << (2 * a + 1));
+        if (lo != hi) return 0;
+    }
+    return 1;
+}
+
+// Tiles a window of half-width n can touch along an axis of tile size T.
+int axis_tile_bound(double n, int T) {
+    int cells = (int)std::ceil(2.0 * n) + 1;
+    return (cells + T - 1) / T + 1;
+}
+
+void free_bubbles(lbm_ctx* c) {
+    BubbleDev& b = c->bub;
+    void* ptrs[] = {b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
+                    b.cell, b.rec, c->bins.items};
+    for (void* p : ptrs) dfree(c, p);
+    b = BubbleDev{};
+    c->bins.items = nullptr;
+    c->bins.cap = 0;
+    c->nb_cap = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_params(lbm_params* p) {
+    if (!p) return;
+    p->g = 1e-5;
+    p->rho_l = 1.0;
+    p->rho_ratio = 1e-3;
+    p->sigma = 5.84e-6;
+    p->c_added_mass = 0.5;
+    p->drag_scale = 1.0;
+    p->sn_coeff = 0.15;
+    p->sn_exp = 0.687;
+    p->width_factor = 1.5;
+    p->substeps = 10;
+    p->two_way = 1;
+}
+
+void lbm_velocity_set(int* c57, double* w19) {
+    for (int j = 0; j < Q; ++j) {
+        if (c57) {
+            c57[3 * j] = cx(j);
+            c57[3 * j + 1] = cy(j);
+            c57[3 * j + 2] = cz(j);
+        }
+        if (w19) w19[j] = wd(j);
+    }
+}
+
+int lbm_create_storage(int nx, int ny, int nz, double omega, unsigned walls, int storage,
+                       double scale, lbm_ctx** out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return LBM_ERR_ARG;
+    if ((long long)nx * ny * nz >= (1LL << 31)) return LBM_ERR_ARG;
+    if (!(omega > 0.0 && omega < 2.0)) return LBM_ERR_ARG;
+    if (!check_walls(walls)) return LBM_ERR_ARG;
+    if (storage < LBM_STORE_F32 || storage > LBM_STORE_BF16) return LBM_ERR_ARG;
+    if (storage != LBM_STORE_F32 && !(scale > 0.0 && std::isfinite(scale))) return LBM_ERR_ARG;
+    lbm_ctx* c = new lbm_ctx();
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->walls = walls;
+    c->omega = omega;
+    c->storage = storage;
+    c->scale = storage == LBM_STORE_F32 ? 1.0 : scale;
+    lbm_default_params(&c->p);
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_create(int nx, int ny, int nz, double omega, unsigned walls, lbm_ctx** out) {
+    return lbm_create_storage(nx, ny, nz, omega, walls, LBM_STORE_F32, 1.0, out);
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    if (c->dev_ready) cudaStreamSynchronize(c->stream);
+    for (auto& e : c->events) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    while (!c->allocs.empty()) dfree(c, c->allocs.back().first);
+    if (c->flag_h) cudaFreeHost(c->flag_h);
+    delete c;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* stream) {
+    if (!c) return LBM_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+int lbm_set_allocator(lbm_ctx* c, lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user) {
+    if (!c) return LBM_ERR_ARG;
+    if (c->dev_ready) return fail(c, LBM_ERR_STATE, "allocator must be set before first device use");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(c, LBM_ERR_ARG, "alloc and free must both be set or both be NULL");
+    c->af = alloc;
+    c->ff = free_fn;
+    c->au = user;
+    return LBM_OK;
+}
+
+int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
+    if (!c || !p) return LBM_ERR_ARG;
+    if (!(p->g >= 0.0) || !(p->rho_l > 0.0) || !(p->rho_ratio >= 0.0 && p->rho_ratio < 1.0) ||
+        !(p->sigma > 0.0) || !(p->c_added_mass >= 0.0) || !(p->drag_scale >= 0.0) ||
+        !(p->sn_coeff >= 0.0) || !(p->sn_exp > 0.0) || !(p->width_factor > 0.0) ||
+        p->substeps < 1 || p->substeps > 10000)
+        return fail(c, LBM_ERR_ARG, "parameter out of range");
+    if (p->rho_ratio + p->c_added_mass <= 0.0)
+        return fail(c, LBM_ERR_ARG, "effective bubble mass must be positive");
+    if (c->bub.nb > 0) {
+        std::vector<double> d(c->bub.nb);
+        LBM_CUDA(cudaMemcpy(d.data(), c->bub.d, sizeof(double) * d.size(), cudaMemcpyDeviceToHost),
+                 "read diameters");
+        for (double v : d)
+            if (p->width_factor * v > MAX_HALF_WIDTH)
+                return fail(c, LBM_ERR_ARG, "width_factor too large for the current bubbles");
+        if (p->width_factor != c->p.width_factor)
+            return fail(c, LBM_ERR_STATE, "set width_factor before lbm_set_bubbles");
+    }
+    c->p = *p;
+    return LBM_OK;
+}
+
+int lbm_get_params(const lbm_ctx* c, lbm_params* p) {
+    if (!c || !p) return LBM_ERR_ARG;
+    *p = c->p;
+    return LBM_OK;
+}
+
+int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u3) {
+    if (!c) return LBM_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    const Geo g = geo_of(c);
+    double* rho_d = nullptr;
+    double* u_d = nullptr;
+    if (rho) {
+        rho_d = (double*)dalloc(c, sizeof(double) * (size_t)g.S);
+        if (!rho_d) return fail(c, LBM_ERR_ALLOC, "rho staging");
+        LBM_CUDA(cudaMemcpyAsync(rho_d, rho, sizeof(double) * (size_t)g.S, cudaMemcpyHostToDevice,
+                                 c->stream), "upload rho");
+    }
+    if (u3) {
+        u_d = (double*)dalloc(c, sizeof(double) * 3 * (size_t)g.S);
+        if (!u_d) {
+            dfree(c, rho_d);
+            return fail(c, LBM_ERR_ALLOC, "u staging");
+        }
+        LBM_CUDA(cudaMemcpyAsync(u_d, u3, sizeof(double) * 3 * (size_t)g.S, cudaMemcpyHostToDevice,
+                                 c->stream), "upload u");
+    }
+    cudaError_t e = launch_set_equilibrium(c->storage, rho_d, u_d, c->f[c->cur], g,
+                                           collide_params(c), c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, rho_d);
+    dfree(c, u_d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set equilibrium");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "set equilibrium (sync)");
+    LBM_CUDA(cudaMemsetAsync(c->flag_d, 0, sizeof(int), c->stream), "memset flag");
+    c->unstable = false;
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const double* f) {
+    if (!c || !f) return LBM_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    const Geo g = geo_of(c);
+    const size_t bytes = sizeof(double) * Q * (size_t)g.S;
+    double* fd = (double*)dalloc(c, bytes);
+    if (!fd) return fail(c, LBM_ERR_ALLOC, "population staging");
+    cudaError_t e = cudaMemcpyAsync(fd, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_set_populations(c->storage, fd, c->f[c->cur], g, collide_params(c), c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, fd);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set populations");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "set populations (sync)");
+    LBM_CUDA(cudaMemsetAsync(c->flag_d, 0, sizeof(int), c->stream), "memset flag");
+    c->unstable = false;
+    return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* f) {
+    if (!c || !f) return LBM_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    const Geo g = geo_of(c);
+    const size_t bytes = sizeof(double) * Q * (size_t)g.S;
+    double* fd = (double*)dalloc(c, bytes);
+    if (!fd) return fail(c, LBM_ERR_ALLOC, "population staging");
+    cudaError_t e = launch_get_populations(c->storage, c->f[c->cur], g, collide_params(c), fd,
+                                           c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, fd, bytes, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, fd);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get populations");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "get populations (sync)");
+    return LBM_OK;
+}
+
+int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
+                    const double* diam) {
+    if (!c || n < 0) return LBM_ERR_ARG;
+    if (n > 0 && (!pos3 || !diam)) return fail(c, LBM_ERR_ARG, "pos3 and diam are required");
+    const int L[3] = {c->nx, c->ny, c->nz};
+    for (int b = 0; b < n; ++b) {
+        const double d = diam[b];
+        if (!(d > 0.0 && d <= LBM_MAX_DIAMETER))
+            return fail(c, LBM_ERR_ARG, "bubble %d: diameter %g outside (0, %g]", b, d,
+                        (double)LBM_MAX_DIAMETER);
+        const double hw = c->p.width_factor * d;
+        if (hw > MAX_HALF_WIDTH)
+            return fail(c, LBM_ERR_ARG, "bubble %d: window half-width %g exceeds %g", b, hw,
+                        MAX_HALF_WIDTH);
+        for (int a = 0; a < 3; ++a) {
+            const double x = pos3[3 * b + a];
+            if (!(x >= 0.0 && x < (double)L[a]))
+                return fail(c, LBM_ERR_ARG, "bubble %d: centre outside the box", b);
+            const bool periodic = !(c->walls & (1u << (2 * a)));
+            if (periodic && 2.0 * hw + 2.0 > (double)L[a])
+                return fail(c, LBM_ERR_ARG, "bubble %d: window wraps onto itself on axis %d", b, a);
+            if (!periodic && d >= (double)L[a])
+                return fail(c, LBM_ERR_ARG, "bubble %d: wider than the box on axis %d", b, a);
+            if (vel3 && !std::isfinite(vel3[3 * b + a]))
+                return fail(c, LBM_ERR_ARG, "bubble %d: non-finite velocity", b);
+        }
+    }
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "sync before bubble reset");
+    free_bubbles(c);
+    c->bins_valid = false;
+    if (n == 0) return LBM_OK;
+
+    BubbleDev& B = c->bub;
+    const size_t v3 = sizeof(double) * 3 * (size_t)n, v1 = sizeof(double) * (size_t)n,
+                 i1 = sizeof(int) * (size_t)n;
+    B.x = (double*)dalloc(c, v3);
+    B.u = (double*)dalloc(c, v3);
+    B.d = (double*)dalloc(c, v1);
+    B.n = (double*)dalloc(c, v1);
+    B.ulprev = (double*)dalloc(c, v3);
+    B.ul = (double*)dalloc(c, v3);
+    B.psi = (double*)dalloc(c, v3);
+    B.has_prev = (int*)dalloc(c, i1);
+    B.active = (int*)dalloc(c, i1);
+    B.spread = (int*)dalloc(c, i1);
+    B.cell = (int*)dalloc(c, i1);
+    B.rec = (BubbleRec*)dalloc(c, sizeof(BubbleRec) * (size_t)n);
+    // Upper bound of (tile, bubble) pairs from the largest window.
+    double dmax = 0.0;
+    for (int b = 0; b < n; ++b) dmax = std::fmax(dmax, diam[b]);
+    const double hwmax = c->p.width_factor * dmax;
+    const long long per = (long long)axis_tile_bound(hwmax, TX) * axis_tile_bound(hwmax, TY) *
+                          axis_tile_bound(hwmax, TZ);
+    const long long cap = per * n;
+    if (cap >= (1LL << 31)) {
+        free_bubbles(c);
+        return fail(c, LBM_ERR_ARG, "too many bubbles for the tile lists");
+    }
+    c->bins.cap = (int)cap;
+    c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
+    if (!B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
+        !B.active || !B.spread || !B.cell || !B.rec || !c->bins.items) {
+        free_bubbles(c);
+        return fail(c, LBM_ERR_ALLOC, "bubble state");
+    }
+    B.nb = n;
+    std::vector<double> hn(n), zeros(3 * (size_t)n, 0.0);
+    for (int b = 0; b < n; ++b) hn[b] = c->p.width_factor * diam[b];
+    std::vector<int> ones(n, 1), izero(n, 0), minus(n, -1);
+    cudaStream_t s = c->stream;
+    LBM_CUDA(cudaMemcpyAsync(B.x, pos3, v3, cudaMemcpyHostToDevice, s), "upload pos");
+    LBM_CUDA(cudaMemcpyAsync(B.u, vel3 ? vel3 : zeros.data(), v3, cudaMemcpyHostToDevice, s),
+             "upload vel");
+    LBM_CUDA(cudaMemcpyAsync(B.d, diam, v1, cudaMemcpyHostToDevice, s), "upload diam");
+    LBM_CUDA(cudaMemcpyAsync(B.n, hn.data(), v1, cudaMemcpyHostToDevice, s), "upload n");
+    LBM_CUDA(cudaMemcpyAsync(B.ulprev, zeros.data(), v3, cudaMemcpyHostToDevice, s), "ulprev");
+    LBM_CUDA(cudaMemcpyAsync(B.ul, zeros.data(), v3, cudaMemcpyHostToDevice, s), "ul");
+    LBM_CUDA(cudaMemcpyAsync(B.psi, zeros.data(), v3, cudaMemcpyHostToDevice, s), "psi");
+    LBM_CUDA(cudaMemcpyAsync(B.has_prev, izero.data(), i1, cudaMemcpyHostToDevice, s), "has_prev");
+    LBM_CUDA(cudaMemcpyAsync(B.active, ones.data(), i1, cudaMemcpyHostToDevice, s), "active");
+    LBM_CUDA(cudaMemcpyAsync(B.spread, izero.data(), i1, cudaMemcpyHostToDevice, s), "spread");
+    LBM_CUDA(cudaMemcpyAsync(B.cell, minus.data(), i1, cudaMemcpyHostToDevice, s), "cell");
+    LBM_CUDA(cudaMemsetAsync(B.rec, 0, sizeof(BubbleRec) * (size_t)n, s), "rec");
+    LBM_CUDA(cudaStreamSynchronize(s), "bubble upload");
+    c->nb_cap = n;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c || nsteps < 0) return LBM_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    if (c->unstable) return fail(c, LBM_ERR_UNSTABLE, "liquid solver is unstable (sticky)");
+    const Geo g = geo_of(c);
+    const CollideParams cp = collide_params(c);
+    const BubbleConst bc = bubble_const(c);
+    const bool bubbles = c->bub.nb > 0;
+    const bool two_way = bubbles && c->p.two_way;
+    for (int s = 0; s < nsteps; ++s) {
+        if (bubbles) {
+            LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bc, c->flag_d, c->stream),
+                     "bubble update");
+            LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
+            c->bins_valid = true;
+            c->launches += 1 + BINNING_LAUNCHES;
+        }
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (c->timing) {
+            if (c->events_used == c->events.size()) {
+                cudaEvent_t a, b;
+                LBM_CUDA(cudaEventCreate(&a), "event");
+                LBM_CUDA(cudaEventCreate(&b), "event");
+                c->events.emplace_back(a, b);
+            }
+            e0 = c->events[c->events_used].first;
+            e1 = c->events[c->events_used].second;
+            ++c->events_used;
+            LBM_CUDA(cudaEventRecord(e0, c->stream), "event record");
+        }
+        LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
+                                       two_way ? &c->bins : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
+                                       c->stream),
+                 "collide-stream");
+        if (c->timing) LBM_CUDA(cudaEventRecord(e1, c->stream), "event record");
+        c->launches += 1;
+        c->cur ^= 1;
+    }
+    LBM_CUDA(cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int), cudaMemcpyDeviceToHost,
+                             c->stream), "read flag");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "step");
+    if (*c->flag_h) {
+        c->unstable = true;
+        return fail(c, LBM_ERR_UNSTABLE, "non-finite value or |u| >= 0.3 in the liquid");
+    }
+    if (c->bins_valid) {
+        int ov = 0;
+        LBM_CUDA(cudaMemcpy(&ov, c->bins.overflow, sizeof(int), cudaMemcpyDeviceToHost), "overflow");
+        if (ov) return fail(c, LBM_ERR_STATE, "tile list capacity exceeded");
+    }
+    return LBM_OK;
+}
+
+int lbm_get_fields(lbm_ctx* c, double* rho, double* u3) {
+    if (!c) return LBM_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    if (!rho && !u3) return LBM_OK;
+    const Geo g = geo_of(c);
+    double* rd = rho ? (double*)dalloc(c, sizeof(double) * (size_t)g.S) : nullptr;
+    double* ud = u3 ? (double*)dalloc(c, sizeof(double) * 3 * (size_t)g.S) : nullptr;
+    if ((rho && !rd) || (u3 && !ud)) {
+        dfree(c, rd);
+        dfree(c, ud);
+        return fail(c, LBM_ERR_ALLOC, "field staging");
+    }
+    cudaError_t e = launch_fields(c->storage, c->f[c->cur], g, collide_params(c), rd, ud, c->stream);
+    if (e == cudaSuccess && rho)
+        e = cudaMemcpyAsync(rho, rd, sizeof(double) * (size_t)g.S, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u3)
+        e = cudaMemcpyAsync(u3, ud, sizeof(double) * 3 * (size_t)g.S, cudaMemcpyDeviceToHost,
+                            c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, rd);
+    dfree(c, ud);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get fields");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "get fields (sync)");
+    return LBM_OK;
+}
+
+int lbm_get_bubbles(lbm_ctx* c, int cap, int* n, double* pos3, double* vel3, double* ul3,
+                    double* psi3, int* active) {
+    if (!c || cap < 0) return LBM_ERR_ARG;
+    const int nb = c->bub.nb;
+    if (n) *n = nb;
+    const int k = nb < cap ? nb : cap;
+    if (k == 0) return LBM_OK;
+    cudaStream_t s = c->stream;
+    const size_t v3 = sizeof(double) * 3 * (size_t)k;
+    if (pos3) LBM_CUDA(cudaMemcpyAsync(pos3, c->bub.x, v3, cudaMemcpyDeviceToHost, s), "pos");
+    if (vel3) LBM_CUDA(cudaMemcpyAsync(vel3, c->bub.u, v3, cudaMemcpyDeviceToHost, s), "vel");
+    if (ul3) LBM_CUDA(cudaMemcpyAsync(ul3, c->bub.ul, v3, cudaMemcpyDeviceToHost, s), "ul");
+    if (psi3) LBM_CUDA(cudaMemcpyAsync(psi3, c->bub.psi, v3, cudaMemcpyDeviceToHost, s), "psi");
+    if (active)
+        LBM_CUDA(cudaMemcpyAsync(active, c->bub.active, sizeof(int) * (size_t)k,
+                                 cudaMemcpyDeviceToHost, s), "active");
+    LBM_CUDA(cudaStreamSynchronize(s), "get bubbles");
+    return LBM_OK;
+}
+
+int lbm_get_totals(lbm_ctx* c, double* out4) {
+    if (!c || !out4) return LBM_ERR_ARG;
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    const Geo g = geo_of(c);
+    const int np = totals_partials(g);
+    double* part = (double*)dalloc(c, sizeof(double) * 4 * (size_t)np + sizeof(double) * 4);
+    if (!part) return fail(c, LBM_ERR_ALLOC, "totals scratch");
+    double* out_d = part + 4 * (size_t)np;
+    cudaError_t e = launch_totals(c->storage, c->f[c->cur], g, collide_params(c), part, np, out_d,
+                                  c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out4, out_d, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, part);
+    if (e != cudaSuccess) return cuda_fail(c, e, "totals");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "totals (sync)");
+    return LBM_OK;
+}
+
+int lbm_get_bins(lbm_ctx* c, int* cell, int* tile3, int* ntiles, int* offsets, int* items,
+                 int cap_items, int* nitems) {
+    if (!c || cap_items < 0) return LBM_ERR_ARG;
+    if (tile3) {
+        tile3[0] = TX;
+        tile3[1] = TY;
+        tile3[2] = TZ;
+    }
+    const Geo g = geo_of(c);
+    const int T = g.ntx * g.nty * g.ntz;
+    if (ntiles) *ntiles = T;
+    if (!c->bins_valid) {
+        if (nitems) *nitems = 0;
+        if (offsets) std::memset(offsets, 0, sizeof(int) * ((size_t)T + 1));
+        if (cell)
+            for (int b = 0; b < c->bub.nb; ++b) cell[b] = -1;
+        return LBM_OK;
+    }
+    cudaStream_t s = c->stream;
+    LBM_CUDA(cudaStreamSynchronize(s), "bins sync");
+    int total = 0;
+    LBM_CUDA(cudaMemcpy(&total, c->bins.off + T, sizeof(int), cudaMemcpyDeviceToHost), "bins total");
+    if (nitems) *nitems = total;
+    if (offsets)
+        LBM_CUDA(cudaMemcpy(offsets, c->bins.off, sizeof(int) * ((size_t)T + 1),
+                            cudaMemcpyDeviceToHost), "bins offsets");
+    if (items) {
+        const int k = total < cap_items ? total : cap_items;
+        if (k > 0)
+            LBM_CUDA(cudaMemcpy(items, c->bins.items, sizeof(int) * (size_t)k,
+                                cudaMemcpyDeviceToHost), "bins items");
+    }
+    if (cell && c->bub.nb > 0)
+        LBM_CUDA(cudaMemcpy(cell, c->bub.cell, sizeof(int) * (size_t)c->bub.nb,
+                            cudaMemcpyDeviceToHost), "bins cells");
+    return LBM_OK;
+}
+
+long long lbm_sites(const lbm_ctx* c) { return c ? (long long)c->nx * c->ny * c->nz : 0; }
+
+int lbm_bytes_per_site(const lbm_ctx* c) { return c ? (int)(2 * Q * elem_size(c->storage)) : 0; }
+
+int lbm_set_kernel_timing(lbm_ctx* c, int on) {
+    if (!c) return LBM_ERR_ARG;
+    if (c->dev_ready) LBM_CUDA(cudaStreamSynchronize(c->stream), "timing sync");
+    c->timing = on != 0;
+    c->events_used = 0;
+    return LBM_OK;
+}
+
+int lbm_get_kernel_time(lbm_ctx* c, double* ms, int* launches) {
+    if (!c) return LBM_ERR_ARG;
+    if (c->dev_ready) LBM_CUDA(cudaStreamSynchronize(c->stream), "timing sync");
+    double total = 0.0;
+    for (size_t i = 0; i < c->events_used; ++i) {
+        float t = 0.0f;
+        LBM_CUDA(cudaEventElapsedTime(&t, c->events[i].first, c->events[i].second), "elapsed");
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (int)c->events_used;
+    c->events_used = 0;
+    return LBM_OK;
+}
+
+long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
+
+int lbm_sync(lbm_ctx* c) {
+    if (!c) return LBM_ERR_ARG;
+    if (!c->dev_ready) return LBM_OK;
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "sync");
+    return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+const char* lbm_status_string(int s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_ERR_ARG: return "LBM_ERR_ARG";
+        case LBM_ERR_ALLOC: return "LBM_ERR_ALLOC";
+        case LBM_ERR_UNSTABLE: return "LBM_ERR_UNSTABLE";
+        case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+        case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+        case LBM_ERR_STATE: return "LBM_ERR_STATE";
+        default: return "LBM_UNKNOWN";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+// Internal declarations shared by the CUDA translation units of liblbm.so.
+//
+// D3Q19 direction order used by this library (Eq. 7-8 of arXiv:1710.07073,
+// renumbered with the rest velocity first):
+//   0: (0,0,0)
+//   1,2: (+-1,0,0)   3,4: (0,+-1,0)   5,6: (0,0,+-1)
+//   7: (+1,+1,0) 8: (-1,-1,0) 9: (+1,-1,0) 10: (-1,+1,0)
+//   11: (+1,0,+1) 12: (-1,0,-1) 13: (+1,0,-1) 14: (-1,0,+1)
+//   15: (0,+1,+1) 16: (0,-1,-1) 17: (0,+1,-1) 18: (0,-1,+1)
+// Opposite directions come in consecutive pairs (2k-1, 2k).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+constexpr int Q = 19;
+// Binning tile; the collide-stream CTA covers TX x TY sites of one z-plane, so
+// all threads of a CTA share one tile.
+constexpr int TX = 32, TY = 4, TZ = 4;
+constexpr int MAX_AXIS_TILES = 8;   // per-axis tiles a window may touch (n <= 9)
+constexpr double MAX_HALF_WIDTH = 9.0;
+
+__host__ __device__ __forceinline__ constexpr int cx(int j) {
+    return (j == 1 || j == 7 || j == 9 || j == 11 || j == 13) ? 1
+         : (j == 2 || j == 8 || j == 10 || j == 12 || j == 14) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cy(int j) {
+    return (j == 3 || j == 7 || j == 10 || j == 15 || j == 17) ? 1
+         : (j == 4 || j == 8 || j == 9 || j == 16 || j == 18) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cz(int j) {
+    return (j == 5 || j == 11 || j == 14 || j == 15 || j == 18) ? 1
+         : (j == 6 || j == 12 || j == 13 || j == 16 || j == 17) ? -1 : 0;
+}
+__host__ __device__ __forceinline__ constexpr int opp(int j) {
+    return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1);
+}
+// Eq. 8 weights and their reciprocals.
+__host__ __device__ __forceinline__ constexpr float wf(int j) {
+    return j == 0 ? (1.0f / 3.0f) : (j <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
+}
+__host__ __device__ __forceinline__ constexpr double wd(int j) {
+    return j == 0 ? (1.0 / 3.0) : (j <= 6 ? (1.0 / 18.0) : (1.0 / 36.0));
+}
+__host__ __device__ __forceinline__ constexpr float inv_wf(int j) {
+    return j == 0 ? 3.0f : (j <= 6 ? 18.0f : 36.0f);
+}
+
+struct Geo {
+    int nx, ny, nz;
+    unsigned walls;        // LBM_WALL_* bits
+    long long S;           // sites
+    int ntx, nty, ntz;     // tiles per axis
+};
+
+struct CollideParams {
+    float omega;           // 1/tau
+    float pref;            // 1 - omega/2 (Eq. 12)
+    float rho0;            // storage shift reference density
+    float scale;           // 16-bit storage: stored = g * scale / w_j
+    float inv_scale;
+};
+
+// What the collide-stream sweep needs to spread one bubble (Eq. 21): the
+// integer anchor cell and FP32 offset of the centre, the window in units of
+// the half-width, and psi_b divided by the window normalisation.
+struct __align__(16) BubbleRec {
+    int ax, ay, az, pad;
+    float fx, fy, fz, inv_n;
+    float px, py, pz, h;   // h = 0.5 * inv_n
+};
+
+struct BubbleDev {
+    int nb;
+    double* x;        // [3*nb] interleaved position
+    double* u;        // [3*nb] velocity
+    double* d;        // [nb] diameter
+    double* n;        // [nb] window half-width
+    double* ulprev;   // [3*nb] interpolated liquid velocity of the previous step
+    double* ul;       // [3*nb] interpolated liquid velocity of the last step
+    double* psi;      // [3*nb] reaction of the last step
+    int* has_prev;    // [nb]
+    int* active;      // [nb]
+    int* spread;      // [nb] 1 if the bubble spread in the last step
+    int* cell;        // [nb] containing cell after the last update (-1 inactive)
+    BubbleRec* rec;   // [nb]
+};
+
+struct BubbleConst {
+    double g, rho_l, rho_b, sigma, c_am, drag_scale, sn_coeff, sn_exp, nu, dt_b, dt_l;
+    int substeps;
+};
+
+struct Bins {
+    int T;             // tiles
+    int* cnt;          // [T] counts, then fill cursors
+    int* off;          // [T+1]
+    int* items;        // [cap]
+    int cap;
+    int* block_sums;   // scan scratch [nblocks]
+    int nblocks;
+    int* overflow;     // set to 1 if items would exceed cap
+};
+
+// ---- launchers (defined in the kernel translation units) -------------------
+cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
+                                  const CollideParams& cp, const Bins* bins,
+                                  const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
+cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                           const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st);
+// Kernels launched by one launch_binning call (count, 3-pass scan, fill, sort).
+constexpr int BINNING_LAUNCHES = 6;
+cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st);
+cudaError_t launch_fields(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                          double* rho, double* u, cudaStream_t st);
+cudaError_t launch_get_populations(int storage, const void* f, const Geo& g,
+                                   const CollideParams& cp, double* out, cudaStream_t st);
+cudaError_t launch_set_populations(int storage, const double* fin, void* f, const Geo& g,
+                                   const CollideParams& cp, cudaStream_t st);
+cudaError_t launch_set_equilibrium(int storage, const double* rho, const double* u, void* f,
+                                   const Geo& g, const CollideParams& cp, cudaStream_t st);
+cudaError_t launch_totals(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                          double* partials, int npartials, double* out4, cudaStream_t st);
+int totals_partials(const Geo& g);
+int scan_blocks(int T);
+
+}  // namespace lbm
