@@ -62,11 +62,43 @@ def node_weights(xb, n, dims, walls):
     return w3 / w3.sum()
 
 
+def axis_window(xb, n, length, periodic):
+    """Cells of one axis whose interval overlaps the window (xb - n, xb + n) and
+    their cell integrals of Z (Eq. 19, one factor).  On a periodic axis the cells
+    are wrapped into [0, length); on a wall axis cells outside the box are dropped
+    (the weights of the in-box cells are the only non-zero ones)."""
+    lo = int(np.floor(xb - n))
+    hi = int(np.ceil(xb + n)) - 1
+    cells = np.arange(lo, hi + 1)
+    w = kernel_g(cells + 1.0 - xb, n) - kernel_g(cells - xb, n)
+    if periodic:
+        cells = np.mod(cells, length)
+    else:
+        keep = (cells >= 0) & (cells < length)
+        cells, w = cells[keep], w[keep]
+    return cells, w
+
+
+def window_weights(xb, n, dims, walls):
+    """Eq. 19 weights on the window's nodes, renormalised to sum to one.
+
+    Returns (cz, cy, cx, w3) with w3[k, j, i] the weight of node (cx[i], cy[j], cz[k]).
+    Equal to ``node_weights`` restricted to its non-zero entries.
+    """
+    per = [not bool(walls & (1 << (2 * d))) for d in range(3)]
+    cx, wx = axis_window(xb[0], n, dims[0], per[0])
+    cy, wy = axis_window(xb[1], n, dims[1], per[1])
+    cz, wz = axis_window(xb[2], n, dims[2], per[2])
+    w3 = wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
+    return cz, cy, cx, w3 / w3.sum()
+
+
 def interpolate(sigma, xb, n, walls):
     """Eq. 20: Psi = sum_j sigma(j) int_{Omega_j} Z.  sigma: [C, nz, ny, nx] -> [C]."""
     nz, ny, nx = sigma.shape[1:]
-    w = node_weights(xb, n, (nx, ny, nz), walls)
-    return np.array([(sigma[c] * w).sum() for c in range(sigma.shape[0])])
+    cz, cy, cx, w = window_weights(xb, n, (nx, ny, nz), walls)
+    sub = sigma[:, cz[:, None, None], cy[None, :, None], cx[None, None, :]]
+    return np.array([(sub[c] * w).sum() for c in range(sigma.shape[0])])
 
 
 def spread(psi_list, xb_list, n_list, dims, walls):
@@ -74,7 +106,8 @@ def spread(psi_list, xb_list, n_list, dims, walls):
     nx, ny, nz = dims
     phi = np.zeros((3, nz, ny, nx), dtype=np.float64)
     for psi, xb, n in zip(psi_list, xb_list, n_list):
-        w = node_weights(xb, n, dims, walls)
+        cz, cy, cx, w = window_weights(xb, n, dims, walls)
+        idx = (cz[:, None, None], cy[None, :, None], cx[None, None, :])
         for d in range(3):
-            phi[d] += psi[d] * w
+            phi[d][idx] += psi[d] * w
     return phi

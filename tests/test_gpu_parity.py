@@ -198,7 +198,7 @@ def test_periodic_bubble_crosses_face():
     dims = (16, 16, 24)
     walls = olat.WALL_XM | olat.WALL_XP | olat.WALL_YM | olat.WALL_YP
     p = lbm.lbm_default_params()
-    p.g = 2e-3
+    p.g = 1e-2                         # terminal velocity ~0.02 per step
     col, sim = _coupled_pair(dims, 1.5, walls, [[8.0, 8.0, 23.3]], [[0, 0, 0.02]], [1.5], p)
     lbm.lbm_step(col.ctx, 60)
     sim.run(60)

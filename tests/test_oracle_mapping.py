@@ -59,6 +59,23 @@ def test_weights_partition_of_unity(walls):
         assert (w >= 0.0).all()
 
 
+@pytest.mark.parametrize("walls", [0, lat.ALL_WALLS, lat.WALL_ZM | lat.WALL_ZP])
+def test_window_weights_equal_full_grid_weights(walls):
+    # The window restriction drops only zero weights (Eq. 18 vanishes outside
+    # [-n, n]); periodic windows must not overlap themselves (2n + 2 <= L).
+    rng = np.random.default_rng(10)
+    dims = (14, 12, 16)
+    for _ in range(20):
+        n = 1.5 * rng.uniform(0.7, 2.6)
+        xb = [rng.uniform(0.0, L) for L in dims]
+        full = mapping.node_weights(xb, n, dims, walls)
+        cz, cy, cx, w = mapping.window_weights(xb, n, dims, walls)
+        assert len(set(cx)) == len(cx) and len(set(cy)) == len(cy) and len(set(cz)) == len(cz)
+        sub = full[cz[:, None, None], cy[None, :, None], cx[None, None, :]]
+        assert np.allclose(sub, w, rtol=1e-12, atol=1e-15)
+        assert abs(full.sum() - w.sum()) < 1e-13
+
+
 def test_unclipped_weights_need_no_renormalisation():
     # Away from walls the raw tensor-product cell integrals already sum to one.
     dims = (16, 16, 16)
