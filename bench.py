@@ -36,7 +36,7 @@ METRIC = "coupled D3Q19 step MLUPS & % HBM roofline, FP32 vs FP16-store at <=1% 
 FALLBACK_HBM_GBS = 6800.0
 STORAGES = {"f32": 0, "f16": 1, "bf16": 2}
 STORAGE_SCALE = {"f32": 1.0, "f16": 256.0, "bf16": 1.0}
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "collide_stream_traffic.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "collide_stream_traffic.txt")
 KERNEL_SOURCES = ("paper_1710_07073_gb300/csrc/lbm_collide.cu",
                   "paper_1710_07073_gb300/csrc/lbm_device.cuh",
                   "paper_1710_07073_gb300/csrc/lbm_internal.cuh")
@@ -77,15 +77,16 @@ def measured_peak():
 def profile_traffic(storage, dims):
     """DRAM bytes per collide-stream launch from the committed ncu summary, if it
     was taken on the current kernel source for this storage and lattice."""
+    key = "%s_%dx%dx%d" % (storage, *dims)
     try:
         with open(PROFILE_SUMMARY) as fh:
-            prof = json.load(fh)
-    except Exception:
+            for line in fh:
+                parts = line.split()
+                if len(parts) >= 3 and not line.startswith("#") and parts[0] == key:
+                    return float(parts[2]) if parts[1] == kernel_hash() else None
+    except OSError:
         return None
-    entry = prof.get("%s_%dx%dx%d" % (storage, *dims))
-    if not entry or entry.get("kernel_hash") != kernel_hash():
-        return None
-    return entry.get("dram_bytes_per_launch")
+    return None
 
 
 class ClockSampler:
