@@ -201,6 +201,42 @@ int lbm_bytes_per_site(const lbm_ctx* ctx);
 int lbm_set_kernel_timing(lbm_ctx* ctx, int on);
 int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
 
+/* ---- Binning that allocates nothing -------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory when they need the binning: code running while
+ * a stream is captured into a CUDA graph in global capture mode (cudaMalloc is
+ * an error there), runtimes that hand all device memory to their own pool at
+ * start-up, and tight loops that cannot pay for the device-wide
+ * synchronisation of a cudaMalloc.  It bins bubbles into tiles exactly as
+ * lbm_step does (the result equals lbm_get_bins for the same centres) but
+ * keeps its scratch -- LBM_NOALLOC_MAX_TILES tile counters plus the scan's
+ * block sums, about 1 MiB -- in a fixed array inside the library, which every
+ * GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * All pointers are DEVICE memory owned by the caller:
+ *   pos3        double[3*n]  interleaved bubble centres (inside the box);
+ *   half_width  double[n]    window half-widths n_b = width_factor * d_b;
+ *   active      int[n]       non-zero for bubbles to bin;
+ *   tile_offsets int[T+1]    out: per-tile start into tile_items, tiles of the
+ *                            shape lbm_get_bins reports, T = ceil(nx/32) *
+ *                            ceil(ny/4) * ceil(nz/4), numbered x-fastest;
+ *   tile_items  int[cap_items] out: bubble ids, ascending within each tile;
+ *   status      int[1]       out: 0, or 1 if more than cap_items ids were due.
+ * The work is enqueued on `stream` (a cudaStream_t, may be NULL) and is
+ * complete when that stream is.  The first call on a device looks up the
+ * scratch array's device address for that device (a CUDA runtime query);
+ * make that first call before any stream capture begins.  Every call shares
+ * the one scratch array and clears what it needs at its start, so calls that
+ * overlap on the GPU (other streams, other host threads) race.
+ * Returns LBM_ERR_ARG for bad sizes or walls, or when T exceeds
+ * LBM_NOALLOC_MAX_TILES; LBM_ERR_CUDA if a CUDA call fails. */
+#define LBM_NOALLOC_MAX_TILES 262144
+int lbm_bin_bubbles_noalloc(int nx, int ny, int nz, unsigned walls, int n,
+                            const double* pos3, const double* half_width, const int* active,
+                            int* tile_offsets, int* tile_items, int cap_items, int* status,
+                            void* stream);
+
 /* Number of kernels this context has launched since it was created. */
 long long lbm_launch_count(const lbm_ctx* ctx);
 

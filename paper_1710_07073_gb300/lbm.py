@@ -98,6 +98,7 @@ def lib():
         "lbm_set_kernel_timing": (i, [vp, i]),
         "lbm_get_kernel_time": (i, [vp, P(d), P(i)]),
         "lbm_launch_count": (ll, [vp]),
+        "lbm_bin_bubbles_noalloc": (i, [i, i, i, u, i, vp, vp, vp, vp, vp, i, vp, vp]),
         "lbm_sync": (i, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_status_string": (ctypes.c_char_p, [i]),
@@ -289,6 +290,22 @@ def lbm_get_kernel_time(ctx):
     n = ctypes.c_int(0)
     _check(ctx, lib().lbm_get_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+LBM_NOALLOC_MAX_TILES = 262144
+
+
+def lbm_bin_bubbles_noalloc(nx, ny, nz, walls, n, pos3_ptr, half_width_ptr, active_ptr,
+                            tile_offsets_ptr, tile_items_ptr, cap_items, status_ptr, stream=0):
+    """Bin bubbles into tiles without any allocation in the library.
+
+    Every pointer is a device address (an int, e.g. ``tensor.data_ptr()``) of
+    caller-owned memory; see lbm.h.  Raises LbmError on a bad argument."""
+    code = lib().lbm_bin_bubbles_noalloc(nx, ny, nz, walls, n, pos3_ptr, half_width_ptr,
+                                         active_ptr, tile_offsets_ptr, tile_items_ptr,
+                                         int(cap_items), status_ptr, stream)
+    if code != LBM_OK:
+        raise LbmError(code, "lbm_bin_bubbles_noalloc")
 
 
 def lbm_launch_count(ctx):
