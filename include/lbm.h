@@ -110,7 +110,7 @@ void lbm_velocity_set(int* c57, double* w19);
  * (Eq. 9: nu = (1/omega - 1/2)/3; omega must lie in (0, 2)) and the given
  * wall bits, FP32 storage.  The liquid starts at f = f^eq(rho_l, 0)
  * (Algorithm 1 initialisation).  Device memory is allocated on first use.
- * Returns LBM_ERR_ARG for non-positive sizes, S >= 2^31 sites, omega out of
+ * Returns LBM_ERR_ARG for non-positive sizes, 19 S >= 2^32, omega out of
  * range or mismatched wall bits. */
 int lbm_create(int nx, int ny, int nz, double omega, unsigned walls, lbm_ctx** out);
 

@@ -49,15 +49,20 @@ __device__ __forceinline__ void make_record(const double* xb, double n, const Ge
     r.pz = (float)(psi[2] / norm);
 }
 
+// One CTA of BUBBLE_THREADS threads per bubble: the threads stride over the
+// window's nodes for the forward coupling, thread 0 integrates the bubble.
+constexpr int BUBBLE_THREADS = 128;
+
 template <int ST>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(BUBBLE_THREADS)
 k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, BubbleDev B,
           BubbleConst bc, int* __restrict__ flag) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    __shared__ double red[3][BUBBLE_THREADS / 32];
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x;
     if (b >= B.nb) return;
     if (!B.active[b]) {
-        if (lane == 0) {
+        if (tid == 0) {
             B.spread[b] = 0;
             B.cell[b] = -1;
         }
@@ -69,7 +74,7 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
     if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) {
         // A non-finite centre can only come from an unstable liquid: stop
         // coupling this bubble and report the instability.
-        if (lane == 0) {
+        if (tid == 0) {
             B.active[b] = 0;
             B.spread[b] = 0;
             B.cell[b] = -1;
@@ -99,10 +104,11 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
     }
     const float inv_n = (float)(1.0 / n), hh = (float)(0.5 / n);
 
-    // Forward coupling (Eq. 20): lanes stride over the window's nodes.
+    // Forward coupling (Eq. 20): threads stride over the window's nodes and
+    // weight the bare Eq. 10 velocity of the current populations.
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
     const int M = cnt[0] * cnt[1] * cnt[2];
-    for (int m = lane; m < M; m += 32) {
+    for (int m = tid; m < M; m += BUBBLE_THREADS) {
         const int ix = m % cnt[0];
         const int rest = m / cnt[0];
         const int iy = rest % cnt[1];
@@ -136,7 +142,19 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
     }
-    if (lane != 0) return;
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = sx;
+        red[1][tid >> 5] = sy;
+        red[2][tid >> 5] = sz;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    sx = sy = sz = 0.0;
+    for (int w = 0; w < BUBBLE_THREADS / 32; ++w) {
+        sx += red[0][w];
+        sy += red[1][w];
+        sz += red[2][w];
+    }
 
     const double ul[3] = {sx / norm, sy / norm, sz / norm};
     double dul[3] = {0.0, 0.0, 0.0};
@@ -145,32 +163,37 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
     }
 
     // Table 1 forces and the Newton update of Eq. 4 with the added mass on
-    // the left (m_eff), sub-stepped with dt_b (Table 2).
+    // the left (m_eff), sub-stepped with dt_b (Table 2).  The state (velocity,
+    // position) is integrated in FP64; the drag coefficient C_D |v| is a
+    // closure evaluated in FP32.
     const double d = B.d[b];
     const double r = 0.5 * d;
     const double vol = M_PI * d * d * d / 6.0;
-    const double meff = (bc.rho_b + bc.c_am * bc.rho_l) * vol;
+    const double kdt = bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol);   // dt_b / m_eff
     const double fb = (bc.rho_l - bc.rho_b) * vol * bc.g;
     const double eo = (bc.rho_l - bc.rho_b) * bc.g * d * d / bc.sigma;
-    const double eo_term = 8.0 / 3.0 * eo / (eo + 4.0);
+    const float eo_term = (float)(8.0 / 3.0 * eo / (eo + 4.0));
     const double drag_pref = 0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale;
-    const double visc_a0 = 24.0 * bc.nu / d, visc_b = 48.0 * bc.nu / d;
+    const float visc_a0 = (float)(24.0 * bc.nu / d), visc_b = (float)(48.0 * bc.nu / d);
+    const float re_per_speed = (float)(d / bc.nu);
+    const float sn_coeff = (float)bc.sn_coeff, sn_exp = (float)bc.sn_exp;
     const double fvm[3] = {bc.c_am * bc.rho_l * vol * dul[0], bc.c_am * bc.rho_l * vol * dul[1],
                            bc.c_am * bc.rho_l * vol * dul[2]};
     double u[3] = {B.u[3 * b], B.u[3 * b + 1], B.u[3 * b + 2]};
     double fd_sum[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < bc.substeps; ++k) {
         const double v0 = u[0] - ul[0], v1 = u[1] - ul[1], v2 = u[2] - ul[2];
-        const double speed = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-        const double re = speed * d / bc.nu;
-        const double visc_a = visc_a0 * (1.0 + bc.sn_coeff * pow(re, bc.sn_exp));
-        const double cdv = fmax(fmin(visc_a, visc_b), eo_term * speed);   // C_D |v|
+        const float vf0 = (float)v0, vf1 = (float)v1, vf2 = (float)v2;
+        const float speed = sqrtf(vf0 * vf0 + vf1 * vf1 + vf2 * vf2);
+        const float re = speed * re_per_speed;
+        const float visc_a = visc_a0 * (1.0f + sn_coeff * powf(re, sn_exp));
+        const double cdv = (double)fmaxf(fminf(visc_a, visc_b), eo_term * speed);   // C_D |v|
         const double fd[3] = {-drag_pref * cdv * v0, -drag_pref * cdv * v1,
                               -drag_pref * cdv * v2};
         const double fz_buoy[3] = {0.0, 0.0, fb};
         for (int a = 0; a < 3; ++a) {
             fd_sum[a] += fd[a];
-            u[a] = u[a] + (fz_buoy[a] + fd[a] + fvm[a]) / meff * bc.dt_b;
+            u[a] = u[a] + (fz_buoy[a] + fd[a] + fvm[a]) * kdt;
             xb[a] = xb[a] + u[a] * bc.dt_b;
             if (g.walls & (1u << (2 * a))) {
                 if (xb[a] < r) {
@@ -217,13 +240,16 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
-    const int threads = 128;
-    const int blocks = (b.nb * 32 + threads - 1) / threads;
     switch (storage) {
-        case 0: k_bubbles<0><<<blocks, threads, 0, st>>>((const float*)f, g, cp, b, bc, flag); break;
-        case 1: k_bubbles<1><<<blocks, threads, 0, st>>>((const __half*)f, g, cp, b, bc, flag); break;
+        case 0:
+            k_bubbles<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, g, cp, b, bc, flag);
+            break;
+        case 1:
+            k_bubbles<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, g, cp, b, bc, flag);
+            break;
         default:
-            k_bubbles<2><<<blocks, threads, 0, st>>>((const __nv_bfloat16*)f, g, cp, b, bc, flag);
+            k_bubbles<2><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, g, cp, b, bc,
+                                                          flag);
             break;
     }
     return cudaGetLastError();
@@ -391,6 +417,79 @@ cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, c
     if (e != cudaSuccess) return e;
     if (b.nb > 0) k_bin<true><<<bb, tb, 0, st>>>(g, b, bins);
     k_bin_sort<<<(bins.T + 127) / 128, 128, 0, st>>>(bins);
+    return cudaGetLastError();
+}
+
+// Few pairs: one CTA enumerates every (tile, bubble) pair, sorts the keys
+// (tile << 32 | bubble) with a bitonic network in shared memory and writes the
+// runs.  The per-tile counts stay valid between calls because only the tiles
+// the previous call touched are cleared first.
+constexpr int SMALL_THREADS = 1024;
+
+__global__ void __launch_bounds__(SMALL_THREADS) k_bin_small(Geo g, BubbleDev B, SmallBins sb) {
+    __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
+    __shared__ int s_n;
+    const int tid = threadIdx.x;
+    const int prev = min(max(*sb.prev_n, 0), SMALL_MAX_PAIRS);
+    for (int i = tid; i < prev; i += SMALL_THREADS) {
+        const int t = sb.prev_tiles[i];
+        if (t >= 0 && t < sb.T) sb.count[t] = 0;
+    }
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    const int L[3] = {g.nx, g.ny, g.nz};
+    const int T[3] = {TX, TY, TZ};
+    for (int b = tid; b < B.nb; b += SMALL_THREADS) {
+        if (!B.spread[b]) continue;
+        int tl[3][MAX_AXIS_TILES];
+        int nt[3];
+        const double n = B.n[b];
+        for (int a = 0; a < 3; ++a)
+            nt[a] = axis_tiles(B.x[3 * b + a], n, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
+        for (int iz = 0; iz < nt[2]; ++iz)
+            for (int iy = 0; iy < nt[1]; ++iy)
+                for (int ix = 0; ix < nt[0]; ++ix) {
+                    const unsigned t = (unsigned)((tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix]);
+                    const int k = atomicAdd(&s_n, 1);
+                    if (k < SMALL_MAX_PAIRS) keys[k] = ((unsigned long long)t << 32) | (unsigned)b;
+                    else atomicOr(sb.overflow, 1);
+                }
+    }
+    __syncthreads();
+    const int n = min(s_n, SMALL_MAX_PAIRS);
+    int p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    for (int i = n + tid; i < p2; i += SMALL_THREADS) keys[i] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= p2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < p2; i += SMALL_THREADS) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = keys[i], c = keys[l];
+                    const bool up = (i & k) == 0;
+                    if ((a > c) == up) {
+                        keys[i] = c;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += SMALL_THREADS) {
+        const int t = (int)(keys[i] >> 32);
+        sb.items[i] = (int)(keys[i] & 0xffffffffu);
+        sb.prev_tiles[i] = t;
+        if (i == 0 || (int)(keys[i - 1] >> 32) != t) sb.start[t] = i;
+        atomicAdd(&sb.count[t], 1);
+    }
+    if (tid == 0) *sb.prev_n = n;
+}
+
+cudaError_t launch_binning_small(const Geo& g, const BubbleDev& b, const SmallBins& sb,
+                                 cudaStream_t st) {
+    k_bin_small<<<1, SMALL_THREADS, 0, st>>>(g, b, sb);
     return cudaGetLastError();
 }
 

@@ -37,8 +37,11 @@ struct lbm_ctx {
     // bubbles
     BubbleDev bub{};
     int nb_cap = 0;
-    // bins
+    // bins: the large path (count, scan, fill, sort) or, for few pairs, the
+    // single-launch small path
     Bins bins{};
+    SmallBins small{};
+    bool use_small = false;
     bool bins_valid = false;
 
     // timing of the collide-stream launches
@@ -193,13 +196,17 @@ int axis_tile_bound(double n, int T) {
 
 void free_bubbles(lbm_ctx* c) {
     BubbleDev& b = c->bub;
+    SmallBins& sb = c->small;
     void* ptrs[] = {b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
-                    b.cell, b.rec, c->bins.items};
+                    b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items, sb.prev_tiles,
+                    sb.prev_n, sb.overflow};
     for (void* p : ptrs) dfree(c, p);
     b = BubbleDev{};
+    sb = SmallBins{};
     c->bins.items = nullptr;
     c->bins.cap = 0;
     c->nb_cap = 0;
+    c->use_small = false;
 }
 
 }  // namespace
@@ -237,7 +244,7 @@ int lbm_create_storage(int nx, int ny, int nz, double omega, unsigned walls, int
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     if (nx <= 0 || ny <= 0 || nz <= 0) return LBM_ERR_ARG;
-    if ((long long)nx * ny * nz >= (1LL << 31)) return LBM_ERR_ARG;
+    if ((long long)nx * ny * nz * Q >= (1LL << 32)) return LBM_ERR_ARG;   // 32-bit indices
     if (!(omega > 0.0 && omega < 2.0)) return LBM_ERR_ARG;
     if (!check_walls(walls)) return LBM_ERR_ARG;
     if (storage < LBM_STORE_F32 || storage > LBM_STORE_BF16) return LBM_ERR_ARG;
@@ -449,12 +456,33 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         free_bubbles(c);
         return fail(c, LBM_ERR_ARG, "too many bubbles for the tile lists");
     }
-    c->bins.cap = (int)cap;
-    c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
+    bool lists_ok = true;
+    c->use_small = cap <= SMALL_MAX_PAIRS;
+    if (c->use_small) {
+        SmallBins& sb = c->small;
+        sb.T = c->bins.T;
+        sb.start = (int*)dalloc(c, sizeof(int) * (size_t)sb.T);
+        sb.count = (int*)dalloc(c, sizeof(int) * (size_t)sb.T);
+        sb.items = (int*)dalloc(c, sizeof(int) * SMALL_MAX_PAIRS);
+        sb.prev_tiles = (int*)dalloc(c, sizeof(int) * SMALL_MAX_PAIRS);
+        sb.prev_n = (int*)dalloc(c, sizeof(int));
+        sb.overflow = (int*)dalloc(c, sizeof(int));
+        lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow;
+    } else {
+        c->bins.cap = (int)cap;
+        c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
+        lists_ok = c->bins.items != nullptr;
+    }
     if (!B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
-        !B.active || !B.spread || !B.cell || !B.rec || !c->bins.items) {
+        !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
         free_bubbles(c);
         return fail(c, LBM_ERR_ALLOC, "bubble state");
+    }
+    if (c->use_small) {
+        SmallBins& sb = c->small;
+        LBM_CUDA(cudaMemsetAsync(sb.count, 0, sizeof(int) * (size_t)sb.T, c->stream), "count");
+        LBM_CUDA(cudaMemsetAsync(sb.prev_n, 0, sizeof(int), c->stream), "prev_n");
+        LBM_CUDA(cudaMemsetAsync(sb.overflow, 0, sizeof(int), c->stream), "overflow");
     }
     B.nb = n;
     std::vector<double> hn(n), zeros(3 * (size_t)n, 0.0);
@@ -493,9 +521,14 @@ int lbm_step(lbm_ctx* c, int nsteps) {
         if (bubbles) {
             LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bc, c->flag_d, c->stream),
                      "bubble update");
-            LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
+            if (c->use_small) {
+                LBM_CUDA(launch_binning_small(g, c->bub, c->small, c->stream), "binning");
+                c->launches += 2;
+            } else {
+                LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
+                c->launches += 1 + BINNING_LAUNCHES;
+            }
             c->bins_valid = true;
-            c->launches += 1 + BINNING_LAUNCHES;
         }
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (c->timing) {
@@ -510,8 +543,11 @@ int lbm_step(lbm_ctx* c, int nsteps) {
             ++c->events_used;
             LBM_CUDA(cudaEventRecord(e0, c->stream), "event record");
         }
+        TileLists tl{};
+        if (c->use_small) tl = TileLists{c->small.start, c->small.count, c->small.items, SMALL_MAX_PAIRS};
+        else tl = TileLists{c->bins.off, c->bins.cnt, c->bins.items, c->bins.cap};
         LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
-                                       two_way ? &c->bins : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
+                                       two_way ? &tl : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
                                        c->stream),
                  "collide-stream");
         if (c->timing) LBM_CUDA(cudaEventRecord(e1, c->stream), "event record");
@@ -527,7 +563,8 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     }
     if (c->bins_valid) {
         int ov = 0;
-        LBM_CUDA(cudaMemcpy(&ov, c->bins.overflow, sizeof(int), cudaMemcpyDeviceToHost), "overflow");
+        LBM_CUDA(cudaMemcpy(&ov, c->use_small ? c->small.overflow : c->bins.overflow, sizeof(int),
+                            cudaMemcpyDeviceToHost), "overflow");
         if (ov) return fail(c, LBM_ERR_STATE, "tile list capacity exceeded");
     }
     return LBM_OK;
@@ -621,16 +658,31 @@ int lbm_get_bins(lbm_ctx* c, int* cell, int* tile3, int* ntiles, int* offsets, i
     cudaStream_t s = c->stream;
     LBM_CUDA(cudaStreamSynchronize(s), "bins sync");
     int total = 0;
-    LBM_CUDA(cudaMemcpy(&total, c->bins.off + T, sizeof(int), cudaMemcpyDeviceToHost), "bins total");
+    const int* items_d = c->use_small ? c->small.items : c->bins.items;
+    if (c->use_small) {
+        // Offsets are the running sum of the per-tile counts (pairs are
+        // sorted by tile, so the runs are in tile order).
+        std::vector<int> cnt((size_t)T);
+        LBM_CUDA(cudaMemcpy(cnt.data(), c->small.count, sizeof(int) * (size_t)T,
+                            cudaMemcpyDeviceToHost), "bins counts");
+        if (offsets) offsets[0] = 0;
+        for (int t = 0; t < T; ++t) {
+            total += cnt[t];
+            if (offsets) offsets[t + 1] = total;
+        }
+    } else {
+        LBM_CUDA(cudaMemcpy(&total, c->bins.off + T, sizeof(int), cudaMemcpyDeviceToHost),
+                 "bins total");
+        if (offsets)
+            LBM_CUDA(cudaMemcpy(offsets, c->bins.off, sizeof(int) * ((size_t)T + 1),
+                                cudaMemcpyDeviceToHost), "bins offsets");
+    }
     if (nitems) *nitems = total;
-    if (offsets)
-        LBM_CUDA(cudaMemcpy(offsets, c->bins.off, sizeof(int) * ((size_t)T + 1),
-                            cudaMemcpyDeviceToHost), "bins offsets");
     if (items) {
         const int k = total < cap_items ? total : cap_items;
         if (k > 0)
-            LBM_CUDA(cudaMemcpy(items, c->bins.items, sizeof(int) * (size_t)k,
-                                cudaMemcpyDeviceToHost), "bins items");
+            LBM_CUDA(cudaMemcpy(items, items_d, sizeof(int) * (size_t)k, cudaMemcpyDeviceToHost),
+                     "bins items");
     }
     if (cell && c->bub.nb > 0)
         LBM_CUDA(cudaMemcpy(cell, c->bub.cell, sizeof(int) * (size_t)c->bub.nb,

@@ -9,6 +9,11 @@
 // forcing with the Guo term (Eq. 12, 15), and writes the post-collision
 // populations of its own node.  All arithmetic is FP32 on populations shifted
 // by w_j rho0.
+//
+// The sweep is bound by issue as much as by HBM, so the common case is kept
+// short: nodes away from the box faces address their 19 sources with one
+// 32-bit offset each, tiles without bubbles skip the forcing terms, and each
+// pair of opposite directions shares its equilibrium terms.
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -43,27 +48,103 @@ __device__ __forceinline__ void add_bubble_force(const BubbleRec& r, const Geo& 
     Fz = fmaf(w, r.pz, Fz);
 }
 
-template <int ST, int J>
-__device__ __forceinline__ void relax_store(typename Store<ST>::T* __restrict__ fout, size_t S,
-                                            int site, float gj, float drho, float rho, float ux,
-                                            float uy, float uz, float usq, float Fx, float Fy,
-                                            float Fz, float uF, const CollideParams& cp) {
+// Offset of the source of direction J from the receiving node, x fastest.
+template <int J>
+__device__ __forceinline__ unsigned src_delta(unsigned nx, unsigned nxy) {
+    return (unsigned)cx(J) + (unsigned)cy(J) * nx + (unsigned)cz(J) * nxy;
+}
+
+// Pull-gather for a node whose 18 neighbours are all inside the box: no
+// bounce-back and no wrap.  Indices are 32-bit (19 S < 2^32 is enforced at
+// creation); source of J is J*S + site - (c_J . (1, nx, nx ny)).
+template <int ST>
+__device__ __forceinline__ void gather_interior(const typename Store<ST>::T* __restrict__ f,
+                                                unsigned S, unsigned site, unsigned nx,
+                                                unsigned nxy, const CollideParams& cp,
+                                                float gv[Q]) {
+#define LBM_PULL(J) gv[J] = Store<ST>::template load<J>(f + ((unsigned)(J) * S + site - src_delta<J>(nx, nxy)), cp)
+    LBM_PULL(0); LBM_PULL(1); LBM_PULL(2); LBM_PULL(3); LBM_PULL(4);
+    LBM_PULL(5); LBM_PULL(6); LBM_PULL(7); LBM_PULL(8); LBM_PULL(9);
+    LBM_PULL(10); LBM_PULL(11); LBM_PULL(12); LBM_PULL(13); LBM_PULL(14);
+    LBM_PULL(15); LBM_PULL(16); LBM_PULL(17); LBM_PULL(18);
+#undef LBM_PULL
+}
+
+// One pair of opposite directions (J, J+1 = opp(J)): Eq. 6 equilibrium split
+// into its even part (shared) and odd part (sign flips), BGK relaxation in the
+// form (1 - omega) g + omega g^eq, and the Guo term of Eq. 12 when forced.
+template <int ST, int J, bool FORCED>
+__device__ __forceinline__ void relax_pair(typename Store<ST>::T* __restrict__ fout, unsigned S,
+                                           unsigned site, const float gv[Q], float base,
+                                           float rho, float ux, float uy, float uz, float Fx,
+                                           float Fy, float Fz, float uF,
+                                           const CollideParams& cp) {
     constexpr float w = wf(J);
-    float cu = (float)cx(J) * ux + (float)cy(J) * uy + (float)cz(J) * uz;
-    float cF = (float)cx(J) * Fx + (float)cy(J) * Fy + (float)cz(J) * Fz;
-    // Eq. 6 shifted by w_j rho0: g^eq = w_j [drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)]
-    float geq = w * (drho + rho * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
-    // Eq. 14 then Eq. 15 with the Guo term of Eq. 12.
-    float out = gj - cp.omega * (gj - geq) + cp.pref * w * (3.0f * (cF - uF) + 9.0f * cu * cF);
-    Store<ST>::template store<J>(fout + (size_t)J * S + site, out, cp);
+    const float cu = (float)cx(J) * ux + (float)cy(J) * uy + (float)cz(J) * uz;
+    const float even = w * fmaf(4.5f * rho * cu, cu, base);
+    const float odd = w * 3.0f * rho * cu;
+    const float om = cp.omega, om1 = 1.0f - cp.omega;
+    float a = fmaf(om1, gv[J], om * (even + odd));
+    float b = fmaf(om1, gv[J + 1], om * (even - odd));
+    if (FORCED) {
+        const float cF = (float)cx(J) * Fx + (float)cy(J) * Fy + (float)cz(J) * Fz;
+        const float ge = cp.pref * w * (9.0f * cu * cF - 3.0f * uF);
+        const float go = cp.pref * w * 3.0f * cF;
+        a += ge + go;
+        b += ge - go;
+    }
+    Store<ST>::template store<J>(fout + ((unsigned)J * S + site), a, cp);
+    Store<ST>::template store<J + 1>(fout + ((unsigned)(J + 1) * S + site), b, cp);
+}
+
+template <int ST, bool FORCED>
+__device__ __forceinline__ void collide_store(typename Store<ST>::T* __restrict__ fout,
+                                              unsigned S, unsigned site, const float gv[Q],
+                                              float Fx, float Fy, float Fz,
+                                              const CollideParams& cp, int* flag) {
+    // Eq. 10 / Eq. 13 moments on shifted populations (sum_j w_j c_j = 0).
+    float drho = 0.0f;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) drho += gv[j];
+    const float jx = (gv[1] - gv[2]) + (gv[7] - gv[8]) + (gv[9] - gv[10]) + (gv[11] - gv[12]) +
+                     (gv[13] - gv[14]);
+    const float jy = (gv[3] - gv[4]) + (gv[7] - gv[8]) + (gv[10] - gv[9]) + (gv[15] - gv[16]) +
+                     (gv[17] - gv[18]);
+    const float jz = (gv[5] - gv[6]) + (gv[11] - gv[12]) + (gv[14] - gv[13]) + (gv[15] - gv[16]) +
+                     (gv[18] - gv[17]);
+    const float rho = cp.rho0 + drho;
+    const float inv_rho = 1.0f / rho;
+    float ux, uy, uz;
+    if (FORCED) {
+        ux = fmaf(0.5f, Fx, jx) * inv_rho;
+        uy = fmaf(0.5f, Fy, jy) * inv_rho;
+        uz = fmaf(0.5f, Fz, jz) * inv_rho;
+    } else {
+        ux = jx * inv_rho;
+        uy = jy * inv_rho;
+        uz = jz * inv_rho;
+    }
+    const float usq = ux * ux + uy * uy + uz * uz;
+    if (!(usq < 0.09f)) atomicOr(flag, 1);   // non-finite or beyond |u| = 0.3
+    const float uF = FORCED ? (ux * Fx + uy * Fy + uz * Fz) : 0.0f;
+    // Common part of g^eq_j / w_j: drho - 3/2 rho u^2.
+    const float base = fmaf(-1.5f * rho, usq, drho);
+    float rest = fmaf(1.0f - cp.omega, gv[0], cp.omega * wf(0) * base);
+    if (FORCED) rest -= 3.0f * cp.pref * wf(0) * uF;   // Eq. 12 with c_0 = 0
+    Store<ST>::template store<0>(fout + site, rest, cp);
+#define LBM_PAIR(J) relax_pair<ST, J, FORCED>(fout, S, site, gv, base, rho, ux, uy, uz, Fx, Fy, Fz, uF, cp)
+    LBM_PAIR(1); LBM_PAIR(3); LBM_PAIR(5); LBM_PAIR(7); LBM_PAIR(9);
+    LBM_PAIR(11); LBM_PAIR(13); LBM_PAIR(15); LBM_PAIR(17);
+#undef LBM_PAIR
 }
 
 template <int ST>
 __global__ void __launch_bounds__(TX * TY, 8)
 k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
                  typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
-                 const int* __restrict__ tile_off, const int* __restrict__ items, int cap,
-                 const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
+                 const int* __restrict__ tile_start, const int* __restrict__ tile_count,
+                 const int* __restrict__ items, int cap, const BubbleRec* __restrict__ recs,
+                 int nb, int* __restrict__ flag) {
     __shared__ BubbleRec srec[TX * TY];
     const int x = blockIdx.x * TX + threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
@@ -71,77 +152,65 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
     const bool inside = (x < g.nx) && (y < g.ny);
 
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
-    if (tile_off != nullptr) {
+    bool forced = false;   // uniform over the CTA
+    if (tile_count != nullptr) {
         const int t = ((z / TZ) * g.nty + blockIdx.y) * g.ntx + blockIdx.x;
-        const int beg = tile_off[t], end = min(tile_off[t + 1], cap);
-        const int tid = threadIdx.y * TX + threadIdx.x;
-        for (int c0 = beg; c0 < end; c0 += TX * TY) {
-            const int cnt = min(TX * TY, end - c0);
-            __syncthreads();
-            if (tid < cnt) {
-                const int id = items[c0 + tid];
-                if (id >= 0 && id < nb) srec[tid] = recs[id];
-                else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int n_t = tile_count[t];
+        if (n_t > 0) {
+            forced = true;
+            const int beg = tile_start[t];
+            const int end = min(beg + n_t, cap);
+            const int tid = threadIdx.y * TX + threadIdx.x;
+            for (int c0 = beg; c0 < end; c0 += TX * TY) {
+                const int cnt = min(TX * TY, end - c0);
+                __syncthreads();
+                if (tid < cnt) {
+                    const int id = items[c0 + tid];
+                    if (id >= 0 && id < nb) srec[tid] = recs[id];
+                    else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                }
+                __syncthreads();
+                if (inside)
+                    for (int k = 0; k < cnt; ++k) add_bubble_force(srec[k], g, x, y, z, Fx, Fy, Fz);
             }
-            __syncthreads();
-            if (inside)
-                for (int k = 0; k < cnt; ++k) add_bubble_force(srec[k], g, x, y, z, Fx, Fy, Fz);
         }
     }
     if (!inside) return;
 
+    const unsigned S = (unsigned)g.S;
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    const unsigned site = (unsigned)z * nxy + (unsigned)y * nx + (unsigned)x;
     float gv[Q];
-    gather<ST>(fin, g, cp, x, y, z, gv);
+    const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+    if (interior) gather_interior<ST>(fin, S, site, nx, nxy, cp, gv);
+    else gather<ST>(fin, g, cp, x, y, z, gv);
 
-    // Eq. 10 / Eq. 13 moments on shifted populations (sum_j w_j c_j = 0).
-    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        drho += gv[j];
-        if (cx(j) != 0) jx += (float)cx(j) * gv[j];
-        if (cy(j) != 0) jy += (float)cy(j) * gv[j];
-        if (cz(j) != 0) jz += (float)cz(j) * gv[j];
-    }
-    const float rho = cp.rho0 + drho;
-    const float inv_rho = 1.0f / rho;
-    const float ux = (jx + 0.5f * Fx) * inv_rho;
-    const float uy = (jy + 0.5f * Fy) * inv_rho;
-    const float uz = (jz + 0.5f * Fz) * inv_rho;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    if (!(usq < 0.09f)) atomicOr(flag, 1);   // non-finite or beyond |u| = 0.3
-    const float uF = ux * Fx + uy * Fy + uz * Fz;
-
-    const size_t S = (size_t)g.S;
-    const int site = site_index(g, x, y, z);
-#define LBM_RELAX(J) relax_store<ST, J>(fout, S, site, gv[J], drho, rho, ux, uy, uz, usq, Fx, Fy, Fz, uF, cp)
-    LBM_RELAX(0); LBM_RELAX(1); LBM_RELAX(2); LBM_RELAX(3); LBM_RELAX(4);
-    LBM_RELAX(5); LBM_RELAX(6); LBM_RELAX(7); LBM_RELAX(8); LBM_RELAX(9);
-    LBM_RELAX(10); LBM_RELAX(11); LBM_RELAX(12); LBM_RELAX(13); LBM_RELAX(14);
-    LBM_RELAX(15); LBM_RELAX(16); LBM_RELAX(17); LBM_RELAX(18);
-#undef LBM_RELAX
+    if (forced) collide_store<ST, true>(fout, S, site, gv, Fx, Fy, Fz, cp, flag);
+    else collide_store<ST, false>(fout, S, site, gv, 0.0f, 0.0f, 0.0f, cp, flag);
 }
 
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
-                                  const CollideParams& cp, const Bins* bins,
+                                  const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, cudaStream_t st) {
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.nz);
-    const int* off = bins ? bins->off : nullptr;
-    const int* items = bins ? bins->items : nullptr;
-    const int cap = bins ? bins->cap : 0;
+    const int* start = tl ? tl->start : nullptr;
+    const int* count = tl ? tl->count : nullptr;
+    const int* items = tl ? tl->items : nullptr;
+    const int cap = tl ? tl->cap : 0;
     switch (storage) {
         case 0:
-            k_collide_stream<0><<<grid, block, 0, st>>>((const float*)fin, (float*)fout, g, cp, off,
-                                                        items, cap, recs, nb, flag);
+            k_collide_stream<0><<<grid, block, 0, st>>>((const float*)fin, (float*)fout, g, cp,
+                                                        start, count, items, cap, recs, nb, flag);
             break;
         case 1:
             k_collide_stream<1><<<grid, block, 0, st>>>((const __half*)fin, (__half*)fout, g, cp,
-                                                        off, items, cap, recs, nb, flag);
+                                                        start, count, items, cap, recs, nb, flag);
             break;
         default:
             k_collide_stream<2><<<grid, block, 0, st>>>((const __nv_bfloat16*)fin,
-                                                        (__nv_bfloat16*)fout, g, cp, off, items,
-                                                        cap, recs, nb, flag);
+                                                        (__nv_bfloat16*)fout, g, cp, start, count,
+                                                        items, cap, recs, nb, flag);
             break;
     }
     return cudaGetLastError();

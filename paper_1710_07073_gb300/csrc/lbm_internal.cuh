@@ -106,10 +106,35 @@ struct Bins {
     int* overflow;     // set to 1 if items would exceed cap
 };
 
+// Per-tile bubble lists as the collide-stream sweep reads them: tile t holds
+// items[start[t] .. start[t] + count[t]) (start is only read when count > 0).
+struct TileLists {
+    const int* start;
+    const int* count;
+    const int* items;
+    int cap;
+};
+
+// Single-launch binning for few (tile, bubble) pairs: pairs are sorted by
+// (tile, bubble) in shared memory; only the tiles touched by the previous step
+// are cleared, so no work scales with the tile count.
+constexpr int SMALL_MAX_PAIRS = 4096;
+struct SmallBins {
+    int T;
+    int* start;        // [T]
+    int* count;        // [T], zero except on tiles listed in prev_tiles
+    int* items;        // [SMALL_MAX_PAIRS]
+    int* prev_tiles;   // [SMALL_MAX_PAIRS] tile of each pair of the last binning
+    int* prev_n;       // [1] number of pairs of the last binning
+    int* overflow;     // [1]
+};
+
 // ---- launchers (defined in the kernel translation units) -------------------
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
-                                  const CollideParams& cp, const Bins* bins,
+                                  const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
+cudaError_t launch_binning_small(const Geo& g, const BubbleDev& b, const SmallBins& sb,
+                                 cudaStream_t st);
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st);
 // Kernels launched by one launch_binning call (count, 3-pass scan, fill, sort).

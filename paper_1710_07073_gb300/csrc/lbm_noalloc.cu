@@ -57,7 +57,7 @@ extern "C" int lbm_bin_bubbles_noalloc(int nx, int ny, int nz, unsigned walls, i
                                        const int* active, int* tile_offsets, int* tile_items,
                                        int cap_items, int* status, void* stream) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || n < 0 || cap_items < 0) return LBM_ERR_ARG;
-    if ((long long)nx * ny * nz >= (1LL << 31)) return LBM_ERR_ARG;
+    if ((long long)nx * ny * nz * 19 >= (1LL << 32)) return LBM_ERR_ARG;
     if (walls & ~0x3Fu) return LBM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (!(walls & (1u << (2 * a))) != !(walls & (1u << (2 * a + 1)))) return LBM_ERR_ARG;

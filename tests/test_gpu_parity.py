@@ -135,11 +135,15 @@ def test_single_bubble_1000_steps():
     assert rel_linf(b["vel"], sim.u) < U_RTOL
 
 
-def test_swarm_crop_100_steps():
+@pytest.mark.parametrize("count", [None, 200])
+def test_swarm_crop_100_steps(count):
     # Dispersed swarm: lognormal diameters (mean 1.5, sd 0.3), uniform in the
-    # bottom 20 %, count scaled by volume from 100 000 bubbles in 384x384x768.
+    # bottom 20 %, count scaled by volume from 100 000 bubbles in 384x384x768
+    # (58 bubbles: single-launch binning), or 200 bubbles (count-scan-fill-sort
+    # binning).
     dims = (32, 32, 64)
-    count = workloads.swarm_count_for_crop(workloads.SWARM_FULL, 100_000, dims)
+    if count is None:
+        count = workloads.swarm_count_for_crop(workloads.SWARM_FULL, 100_000, dims)
     pos, vel, diam = workloads.swarm(dims, count, seed=1234)
     p = lbm.lbm_default_params()
     p.g = 1e-4
@@ -154,10 +158,14 @@ def test_swarm_crop_100_steps():
     assert (b["active"] == sim.active).all()
 
 
+@pytest.mark.parametrize("count", [None, 40])
 @pytest.mark.parametrize("walls", [olat.ALL_WALLS, olat.WALL_ZM | olat.WALL_ZP])
-def test_binning_bit_exact(walls):
+def test_binning_bit_exact(walls, count):
+    # 463 bubbles (volume-scaled swarm) use the count-scan-fill-sort binning,
+    # 40 bubbles the single-launch path; both must give the same lists.
     dims = workloads.SWARM_CROP
-    count = workloads.swarm_count_for_crop(workloads.SWARM_FULL, 100_000, dims)
+    if count is None:
+        count = workloads.swarm_count_for_crop(workloads.SWARM_FULL, 100_000, dims)
     pos, vel, diam = workloads.swarm(dims, count, seed=99)
     col = lbm.Column(dims, 1.7, walls)
     lbm.lbm_set_bubbles(col.ctx, pos.reshape(-1), vel.reshape(-1), diam)
