@@ -18,12 +18,12 @@ namespace lbm {
 
 // Window normalisation along one axis: the integral of the mapping over the
 // in-box part of [-n, n] (without 15/16); the full 16/15 on a periodic axis.
-__device__ __forceinline__ double axis_norm(double xa, double n, int L, bool periodic) {
+__device__ __forceinline__ double axis_norm(double xa, double inv_n, int L, bool periodic) {
     if (periodic) return cell_poly_d(-1.0, 1.0);
-    return cell_poly_d(-xa / n, ((double)L - xa) / n);
+    return cell_poly_d(-xa * inv_n, ((double)L - xa) * inv_n);
 }
 
-__device__ __forceinline__ void make_record(const double* xb, double n, const Geo& g,
+__device__ __forceinline__ void make_record(const double* xb, double inv_n, const Geo& g,
                                             const double* psi, BubbleRec& r) {
     int anc[3];
     float fr[3];
@@ -33,8 +33,9 @@ __device__ __forceinline__ void make_record(const double* xb, double n, const Ge
         double fl = floor(xb[a]);
         anc[a] = (int)fl;
         fr[a] = (float)(xb[a] - fl);
-        norm *= axis_norm(xb[a], n, L[a], !(g.walls & (1u << (2 * a))));
+        norm *= axis_norm(xb[a], inv_n, L[a], !(g.walls & (1u << (2 * a))));
     }
+    const double inv_norm = 1.0 / norm;
     r.ax = anc[0];
     r.ay = anc[1];
     r.az = anc[2];
@@ -42,11 +43,11 @@ __device__ __forceinline__ void make_record(const double* xb, double n, const Ge
     r.fx = fr[0];
     r.fy = fr[1];
     r.fz = fr[2];
-    r.inv_n = (float)(1.0 / n);
-    r.h = (float)(0.5 / n);
-    r.px = (float)(psi[0] / norm);
-    r.py = (float)(psi[1] / norm);
-    r.pz = (float)(psi[2] / norm);
+    r.inv_n = (float)inv_n;
+    r.h = (float)(0.5 * inv_n);
+    r.px = (float)(psi[0] * inv_norm);
+    r.py = (float)(psi[1] * inv_norm);
+    r.pz = (float)(psi[2] * inv_norm);
 }
 
 // One CTA of BUBBLE_THREADS threads per bubble: the threads stride over the
@@ -71,6 +72,7 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
     const int L[3] = {g.nx, g.ny, g.nz};
     double xb[3] = {B.x[3 * b], B.x[3 * b + 1], B.x[3 * b + 2]};
     const double n = B.n[b];
+    const BubbleK K = B.k[b];
     if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) {
         // A non-finite centre can only come from an unstable liquid: stop
         // coupling this bubble and report the instability.
@@ -100,9 +102,9 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
         double fl = floor(xb[a]);
         anc[a] = (int)fl;
         fr[a] = (float)(xb[a] - fl);
-        norm *= axis_norm(xb[a], n, L[a], periodic);
+        norm *= axis_norm(xb[a], K.inv_n, L[a], periodic);
     }
-    const float inv_n = (float)(1.0 / n), hh = (float)(0.5 / n);
+    const float inv_n = (float)K.inv_n, hh = (float)(0.5 * K.inv_n);
 
     // Forward coupling (Eq. 20): threads stride over the window's nodes and
     // weight the bare Eq. 10 velocity of the current populations.
@@ -156,29 +158,23 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
         sz += red[2][w];
     }
 
-    const double ul[3] = {sx / norm, sy / norm, sz / norm};
+    const double inv_norm = 1.0 / norm;
+    const double ul[3] = {sx * inv_norm, sy * inv_norm, sz * inv_norm};
     double dul[3] = {0.0, 0.0, 0.0};
     if (B.has_prev[b]) {
-        for (int a = 0; a < 3; ++a) dul[a] = (ul[a] - B.ulprev[3 * b + a]) / bc.dt_l;
+        const double inv_dt = 1.0 / bc.dt_l;
+        for (int a = 0; a < 3; ++a) dul[a] = (ul[a] - B.ulprev[3 * b + a]) * inv_dt;
     }
 
     // Table 1 forces and the Newton update of Eq. 4 with the added mass on
     // the left (m_eff), sub-stepped with dt_b (Table 2).  The state (velocity,
     // position) is integrated in FP64; the drag coefficient C_D |v| is a
     // closure evaluated in FP32.
-    const double d = B.d[b];
-    const double r = 0.5 * d;
-    const double vol = M_PI * d * d * d / 6.0;
-    const double kdt = bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol);   // dt_b / m_eff
-    const double fb = (bc.rho_l - bc.rho_b) * vol * bc.g;
-    const double eo = (bc.rho_l - bc.rho_b) * bc.g * d * d / bc.sigma;
-    const float eo_term = (float)(8.0 / 3.0 * eo / (eo + 4.0));
-    const double drag_pref = 0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale;
-    const float visc_a0 = (float)(24.0 * bc.nu / d), visc_b = (float)(48.0 * bc.nu / d);
-    const float re_per_speed = (float)(d / bc.nu);
+    const double r = K.r, kdt = K.kdt, fb = K.fb, drag_pref = K.drag_pref;
+    const float eo_term = K.eo_term, visc_a0 = K.visc_a0, visc_b = K.visc_b;
+    const float re_per_speed = K.re_per_speed;
     const float sn_coeff = (float)bc.sn_coeff, sn_exp = (float)bc.sn_exp;
-    const double fvm[3] = {bc.c_am * bc.rho_l * vol * dul[0], bc.c_am * bc.rho_l * vol * dul[1],
-                           bc.c_am * bc.rho_l * vol * dul[2]};
+    const double fvm[3] = {K.fvm_coef * dul[0], K.fvm_coef * dul[1], K.fvm_coef * dul[2]};
     double u[3] = {B.u[3 * b], B.u[3 * b + 1], B.u[3 * b + 2]};
     double fd_sum[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < bc.substeps; ++k) {
@@ -232,9 +228,38 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
     int ci[3];
     for (int a = 0; a < 3; ++a) ci[a] = min(max((int)floor(xb[a]), 0), L[a] - 1);
     B.cell[b] = (ci[2] * g.ny + ci[1]) * g.nx + ci[0];
-    make_record(xb, n, g, psi, B.rec[b]);
+    make_record(xb, K.inv_n, g, psi, B.rec[b]);
     // Algorithm 1: the bubble stops once it reaches the top of the liquid.
     if ((g.walls & 0x20) && xb[2] >= (double)g.nz - r) B.active[b] = 0;
+}
+
+// Table 1 / Eq. 3 constants of each bubble (FP64).
+__global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_factor) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nb) return;
+    const double d = B.d[b];
+    const double r = 0.5 * d;
+    const double vol = M_PI * d * d * d / 6.0;
+    const double eo = (bc.rho_l - bc.rho_b) * bc.g * d * d / bc.sigma;   // Eq. 3 with d^2
+    BubbleK K;
+    K.inv_n = 1.0 / B.n[b];
+    K.r = r;
+    K.kdt = bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol);
+    K.fb = (bc.rho_l - bc.rho_b) * vol * bc.g;
+    K.drag_pref = 0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale;
+    K.fvm_coef = bc.c_am * bc.rho_l * vol;
+    K.visc_a0 = (float)(24.0 * bc.nu / d);
+    K.visc_b = (float)(48.0 * bc.nu / d);
+    K.re_per_speed = (float)(d / bc.nu);
+    K.eo_term = (float)(8.0 / 3.0 * eo / (eo + 4.0));
+    B.k[b] = K;
+    (void)width_factor;
+}
+
+cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    k_bubble_constants<<<(b.nb + 127) / 128, 128, 0, st>>>(b, bc, 0.0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,

@@ -197,7 +197,7 @@ int axis_tile_bound(double n, int T) {
 void free_bubbles(lbm_ctx* c) {
     BubbleDev& b = c->bub;
     SmallBins& sb = c->small;
-    void* ptrs[] = {b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
+    void* ptrs[] = {b.k, b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
                     b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items, sb.prev_tiles,
                     sb.prev_n, sb.overflow};
     for (void* p : ptrs) dfree(c, p);
@@ -315,6 +315,8 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
             return fail(c, LBM_ERR_STATE, "set width_factor before lbm_set_bubbles");
     }
     c->p = *p;
+    if (c->bub.nb > 0)
+        LBM_CUDA(launch_bubble_constants(c->bub, bubble_const(c), c->stream), "bubble constants");
     return LBM_OK;
 }
 
@@ -445,6 +447,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     B.spread = (int*)dalloc(c, i1);
     B.cell = (int*)dalloc(c, i1);
     B.rec = (BubbleRec*)dalloc(c, sizeof(BubbleRec) * (size_t)n);
+    B.k = (BubbleK*)dalloc(c, sizeof(BubbleK) * (size_t)n);
     // Upper bound of (tile, bubble) pairs from the largest window.
     double dmax = 0.0;
     for (int b = 0; b < n; ++b) dmax = std::fmax(dmax, diam[b]);
@@ -473,7 +476,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
         lists_ok = c->bins.items != nullptr;
     }
-    if (!B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
+    if (!B.k || !B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
         !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
         free_bubbles(c);
         return fail(c, LBM_ERR_ALLOC, "bubble state");
@@ -502,6 +505,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     LBM_CUDA(cudaMemcpyAsync(B.spread, izero.data(), i1, cudaMemcpyHostToDevice, s), "spread");
     LBM_CUDA(cudaMemcpyAsync(B.cell, minus.data(), i1, cudaMemcpyHostToDevice, s), "cell");
     LBM_CUDA(cudaMemsetAsync(B.rec, 0, sizeof(BubbleRec) * (size_t)n, s), "rec");
+    LBM_CUDA(launch_bubble_constants(B, bubble_const(c), s), "bubble constants");
     LBM_CUDA(cudaStreamSynchronize(s), "bubble upload");
     c->nb_cap = n;
     return LBM_OK;

@@ -54,15 +54,28 @@ __device__ __forceinline__ unsigned src_delta(unsigned nx, unsigned nxy) {
     return (unsigned)cx(J) + (unsigned)cy(J) * nx + (unsigned)cz(J) * nxy;
 }
 
-// Pull-gather for a node whose 18 neighbours are all inside the box: no
-// bounce-back and no wrap.  Indices are 32-bit (19 S < 2^32 is enforced at
-// creation); source of J is J*S + site - (c_J . (1, nx, nx ny)).
+// Pull-gather of raw stored values for a node whose y and z neighbours are
+// inside the box (all rows but the first and last of each face).  Indices are
+// 32-bit (19 S < 2^32 is enforced at creation): the source of J is
+// J*S + site - (c_J . (1, nx, nx ny)).  A node on an x face takes its
+// x-crossing populations from the opposite plane at its own site (wall) or
+// from the other end of the row (periodic), by selects rather than branches.
+template <int ST, int J>
+__device__ __forceinline__ float pull_raw(const typename Store<ST>::T* __restrict__ f,
+                                          unsigned S, unsigned site, unsigned nx, unsigned nxy,
+                                          bool xlo, bool xhi, bool wallx) {
+    unsigned idx = (unsigned)J * S + site - src_delta<J>(nx, nxy);
+    if (cx(J) == 1 && xlo) idx = wallx ? (unsigned)opp(J) * S + site : idx + nx;
+    if (cx(J) == -1 && xhi) idx = wallx ? (unsigned)opp(J) * S + site : idx - nx;
+    return Store<ST>::load_raw(f + idx);
+}
+
 template <int ST>
-__device__ __forceinline__ void gather_interior(const typename Store<ST>::T* __restrict__ f,
-                                                unsigned S, unsigned site, unsigned nx,
-                                                unsigned nxy, const CollideParams& cp,
-                                                float gv[Q]) {
-#define LBM_PULL(J) gv[J] = Store<ST>::template load<J>(f + ((unsigned)(J) * S + site - src_delta<J>(nx, nxy)), cp)
+__device__ __forceinline__ void gather_rows(const typename Store<ST>::T* __restrict__ f,
+                                            unsigned S, unsigned site, unsigned nx,
+                                            unsigned nxy, bool xlo, bool xhi, bool wallx,
+                                            float rv[Q]) {
+#define LBM_PULL(J) rv[J] = pull_raw<ST, J>(f, S, site, nx, nxy, xlo, xhi, wallx)
     LBM_PULL(0); LBM_PULL(1); LBM_PULL(2); LBM_PULL(3); LBM_PULL(4);
     LBM_PULL(5); LBM_PULL(6); LBM_PULL(7); LBM_PULL(8); LBM_PULL(9);
     LBM_PULL(10); LBM_PULL(11); LBM_PULL(12); LBM_PULL(13); LBM_PULL(14);
@@ -70,48 +83,81 @@ __device__ __forceinline__ void gather_interior(const typename Store<ST>::T* __r
 #undef LBM_PULL
 }
 
-// One pair of opposite directions (J, J+1 = opp(J)): Eq. 6 equilibrium split
-// into its even part (shared) and odd part (sign flips), BGK relaxation in the
-// form (1 - omega) g + omega g^eq, and the Guo term of Eq. 12 when forced.
+// General pull-gather of raw values (any node, any walls).
+template <int ST, int J>
+__device__ __forceinline__ float pull_raw_any(const typename Store<ST>::T* __restrict__ f,
+                                              const Geo& g, int x, int y, int z) {
+    int plane, idx;
+    pull_source<J>(g, x, y, z, plane, idx);
+    return Store<ST>::load_raw(f + (size_t)plane * (size_t)g.S + idx);
+}
+
+template <int ST>
+__device__ __forceinline__ void gather_any(const typename Store<ST>::T* __restrict__ f,
+                                           const Geo& g, int x, int y, int z, float rv[Q]) {
+#define LBM_PULL(J) rv[J] = pull_raw_any<ST, J>(f, g, x, y, z)
+    LBM_PULL(0); LBM_PULL(1); LBM_PULL(2); LBM_PULL(3); LBM_PULL(4);
+    LBM_PULL(5); LBM_PULL(6); LBM_PULL(7); LBM_PULL(8); LBM_PULL(9);
+    LBM_PULL(10); LBM_PULL(11); LBM_PULL(12); LBM_PULL(13); LBM_PULL(14);
+    LBM_PULL(15); LBM_PULL(16); LBM_PULL(17); LBM_PULL(18);
+#undef LBM_PULL
+}
+
+// One pair of opposite directions (J, J+1 = opp(J)) in raw storage units.
+// Eq. 6 is split into its even part (shared by the pair) and odd part (sign
+// flips); g^eq_j / w_j = base + 9/2 rho cu^2 +- 3 rho cu.  BGK relaxation
+// (Eq. 14) is r' = (1 - omega) r + C [omega g^eq / w], and the Guo term of
+// Eq. 12 adds C pref [(9 cu cF - 3 u.F) +- 3 cF], where C = w_J for FP32
+// storage and C = scale for the 16-bit formats (r = g scale / w).
 template <int ST, int J, bool FORCED>
 __device__ __forceinline__ void relax_pair(typename Store<ST>::T* __restrict__ fout, unsigned S,
-                                           unsigned site, const float gv[Q], float base,
+                                           unsigned site, const float rv[Q], float base,
                                            float rho, float ux, float uy, float uz, float Fx,
                                            float Fy, float Fz, float uF,
                                            const CollideParams& cp) {
-    constexpr float w = wf(J);
+    const float C = Store<ST>::kScaled ? cp.scale : wf(J);
     const float cu = (float)cx(J) * ux + (float)cy(J) * uy + (float)cz(J) * uz;
-    const float even = w * fmaf(4.5f * rho * cu, cu, base);
-    const float odd = w * 3.0f * rho * cu;
-    const float om = cp.omega, om1 = 1.0f - cp.omega;
-    float a = fmaf(om1, gv[J], om * (even + odd));
-    float b = fmaf(om1, gv[J + 1], om * (even - odd));
+    float even = cp.omega * fmaf(4.5f * rho * cu, cu, base);
+    float odd = cp.omega * 3.0f * rho * cu;
     if (FORCED) {
         const float cF = (float)cx(J) * Fx + (float)cy(J) * Fy + (float)cz(J) * Fz;
-        const float ge = cp.pref * w * (9.0f * cu * cF - 3.0f * uF);
-        const float go = cp.pref * w * 3.0f * cF;
-        a += ge + go;
-        b += ge - go;
+        even = fmaf(cp.pref, 9.0f * cu * cF - 3.0f * uF, even);
+        odd = fmaf(cp.pref, 3.0f * cF, odd);
     }
-    Store<ST>::template store<J>(fout + ((unsigned)J * S + site), a, cp);
-    Store<ST>::template store<J + 1>(fout + ((unsigned)(J + 1) * S + site), b, cp);
+    const float om1 = 1.0f - cp.omega;
+    Store<ST>::store_raw(fout + ((unsigned)J * S + site), fmaf(om1, rv[J], C * (even + odd)));
+    Store<ST>::store_raw(fout + ((unsigned)(J + 1) * S + site),
+                         fmaf(om1, rv[J + 1], C * (even - odd)));
 }
 
 template <int ST, bool FORCED>
 __device__ __forceinline__ void collide_store(typename Store<ST>::T* __restrict__ fout,
-                                              unsigned S, unsigned site, const float gv[Q],
+                                              unsigned S, unsigned site, const float rv[Q],
                                               float Fx, float Fy, float Fz,
                                               const CollideParams& cp, int* flag) {
-    // Eq. 10 / Eq. 13 moments on shifted populations (sum_j w_j c_j = 0).
-    float drho = 0.0f;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) drho += gv[j];
-    const float jx = (gv[1] - gv[2]) + (gv[7] - gv[8]) + (gv[9] - gv[10]) + (gv[11] - gv[12]) +
-                     (gv[13] - gv[14]);
-    const float jy = (gv[3] - gv[4]) + (gv[7] - gv[8]) + (gv[10] - gv[9]) + (gv[15] - gv[16]) +
-                     (gv[17] - gv[18]);
-    const float jz = (gv[5] - gv[6]) + (gv[11] - gv[12]) + (gv[14] - gv[13]) + (gv[15] - gv[16]) +
-                     (gv[18] - gv[17]);
+    // Eq. 10 / Eq. 13 moments of g = r k, k = 1 (FP32) or w_j / scale
+    // (16-bit); sum_j w_j c_j = 0 so the shift drops out of the momentum.
+    const float s_rest = rv[0];
+    const float s_axis = (rv[1] + rv[2]) + (rv[3] + rv[4]) + (rv[5] + rv[6]);
+    const float s_edge = ((rv[7] + rv[8]) + (rv[9] + rv[10])) + ((rv[11] + rv[12]) + (rv[13] + rv[14])) +
+                         ((rv[15] + rv[16]) + (rv[17] + rv[18]));
+    const float ax_x = rv[1] - rv[2], ax_y = rv[3] - rv[4], ax_z = rv[5] - rv[6];
+    const float ed_x = (rv[7] - rv[8]) + (rv[9] - rv[10]) + (rv[11] - rv[12]) + (rv[13] - rv[14]);
+    const float ed_y = (rv[7] - rv[8]) + (rv[10] - rv[9]) + (rv[15] - rv[16]) + (rv[17] - rv[18]);
+    const float ed_z = (rv[11] - rv[12]) + (rv[14] - rv[13]) + (rv[15] - rv[16]) + (rv[18] - rv[17]);
+    float drho, jx, jy, jz;
+    if (Store<ST>::kScaled) {
+        const float k0 = wf(0) * cp.inv_scale, ka = wf(1) * cp.inv_scale, ke = wf(7) * cp.inv_scale;
+        drho = fmaf(k0, s_rest, fmaf(ka, s_axis, ke * s_edge));
+        jx = fmaf(ka, ax_x, ke * ed_x);
+        jy = fmaf(ka, ax_y, ke * ed_y);
+        jz = fmaf(ka, ax_z, ke * ed_z);
+    } else {
+        drho = s_rest + s_axis + s_edge;
+        jx = ax_x + ed_x;
+        jy = ax_y + ed_y;
+        jz = ax_z + ed_z;
+    }
     const float rho = cp.rho0 + drho;
     const float inv_rho = 1.0f / rho;
     float ux, uy, uz;
@@ -129,10 +175,11 @@ __device__ __forceinline__ void collide_store(typename Store<ST>::T* __restrict_
     const float uF = FORCED ? (ux * Fx + uy * Fy + uz * Fz) : 0.0f;
     // Common part of g^eq_j / w_j: drho - 3/2 rho u^2.
     const float base = fmaf(-1.5f * rho, usq, drho);
-    float rest = fmaf(1.0f - cp.omega, gv[0], cp.omega * wf(0) * base);
-    if (FORCED) rest -= 3.0f * cp.pref * wf(0) * uF;   // Eq. 12 with c_0 = 0
-    Store<ST>::template store<0>(fout + site, rest, cp);
-#define LBM_PAIR(J) relax_pair<ST, J, FORCED>(fout, S, site, gv, base, rho, ux, uy, uz, Fx, Fy, Fz, uF, cp)
+    float e0 = cp.omega * base;
+    if (FORCED) e0 = fmaf(cp.pref, -3.0f * uF, e0);   // Eq. 12 with c_0 = 0
+    const float C0 = Store<ST>::kScaled ? cp.scale : wf(0);
+    Store<ST>::store_raw(fout + site, fmaf(1.0f - cp.omega, rv[0], C0 * e0));
+#define LBM_PAIR(J) relax_pair<ST, J, FORCED>(fout, S, site, rv, base, rho, ux, uy, uz, Fx, Fy, Fz, uF, cp)
     LBM_PAIR(1); LBM_PAIR(3); LBM_PAIR(5); LBM_PAIR(7); LBM_PAIR(9);
     LBM_PAIR(11); LBM_PAIR(13); LBM_PAIR(15); LBM_PAIR(17);
 #undef LBM_PAIR
@@ -180,13 +227,15 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
     const unsigned S = (unsigned)g.S;
     const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
     const unsigned site = (unsigned)z * nxy + (unsigned)y * nx + (unsigned)x;
-    float gv[Q];
-    const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
-    if (interior) gather_interior<ST>(fin, S, site, nx, nxy, cp, gv);
-    else gather<ST>(fin, g, cp, x, y, z, gv);
+    float rv[Q];
+    // Rows away from the y and z faces (uniform over a warp, which is one row).
+    if (y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1)
+        gather_rows<ST>(fin, S, site, nx, nxy, x == 0, x == g.nx - 1, (g.walls & 0x01) != 0, rv);
+    else
+        gather_any<ST>(fin, g, x, y, z, rv);
 
-    if (forced) collide_store<ST, true>(fout, S, site, gv, Fx, Fy, Fz, cp, flag);
-    else collide_store<ST, false>(fout, S, site, gv, 0.0f, 0.0f, 0.0f, cp, flag);
+    if (forced) collide_store<ST, true>(fout, S, site, rv, Fx, Fy, Fz, cp, flag);
+    else collide_store<ST, false>(fout, S, site, rv, 0.0f, 0.0f, 0.0f, cp, flag);
 }
 
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,

@@ -9,11 +9,16 @@ namespace lbm {
 
 // ---- population storage ------------------------------------------------------
 // Stored value of population j is the shifted deviation g_j = f_j - w_j rho0:
-// as is for FP32, times scale / w_j for the 16-bit formats.
+// as is for FP32, times scale / w_j for the 16-bit formats.  load/store convert
+// to and from g_j; load_raw/store_raw move the stored value itself (the
+// "raw" value, r_j = g_j for FP32 and g_j scale / w_j for 16 bits).
 template <int ST> struct Store;
 
 template <> struct Store<0> {
     using T = float;
+    static constexpr bool kScaled = false;
+    static __device__ __forceinline__ float load_raw(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ void store_raw(T* p, float v) { __stcs(p, v); }
     template <int J>
     static __device__ __forceinline__ float load(const T* p, const CollideParams&) {
         return __ldg(p);
@@ -32,6 +37,11 @@ template <> struct Store<0> {
 
 template <> struct Store<1> {
     using T = __half;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float load_raw(const T* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void store_raw(T* p, float v) {
+        __stcs(p, __float2half_rn(v));
+    }
     template <int J>
     static __device__ __forceinline__ float load(const T* p, const CollideParams& cp) {
         return __half2float(__ldg(p)) * (wf(J) * cp.inv_scale);
@@ -50,6 +60,13 @@ template <> struct Store<1> {
 
 template <> struct Store<2> {
     using T = __nv_bfloat16;
+    static constexpr bool kScaled = true;
+    static __device__ __forceinline__ float load_raw(const T* p) {
+        return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ void store_raw(T* p, float v) {
+        __stcs(p, __float2bfloat16_rn(v));
+    }
     template <int J>
     static __device__ __forceinline__ float load(const T* p, const CollideParams& cp) {
         return __bfloat162float(__ldg(p)) * (wf(J) * cp.inv_scale);

@@ -74,8 +74,24 @@ struct __align__(16) BubbleRec {
     float px, py, pz, h;   // h = 0.5 * inv_n
 };
 
+// Per-bubble constants of the closures (Table 1) and of the mapping window,
+// derived from the diameter and the parameters whenever either changes.
+struct BubbleK {
+    double inv_n;       // 1 / n, n = width_factor * d
+    double r;           // d / 2
+    double kdt;         // dt_b / m_eff, m_eff = (rho_b + C_A rho_l) V_b
+    double fb;          // (rho_l - rho_b) V_b g
+    double drag_pref;   // 1/2 rho_l pi r^2 * drag_scale
+    double fvm_coef;    // C_A rho_l V_b
+    float visc_a0;      // 24 nu / d
+    float visc_b;       // 48 nu / d
+    float re_per_speed; // d / nu
+    float eo_term;      // 8/3 Eo / (Eo + 4)
+};
+
 struct BubbleDev {
     int nb;
+    BubbleK* k;       // [nb]
     double* x;        // [3*nb] interleaved position
     double* u;        // [3*nb] velocity
     double* d;        // [nb] diameter
@@ -137,6 +153,7 @@ cudaError_t launch_binning_small(const Geo& g, const BubbleDev& b, const SmallBi
                                  cudaStream_t st);
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st);
+cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st);
 // Kernels launched by one launch_binning call (count, 3-pass scan, fill, sort).
 constexpr int BINNING_LAUNCHES = 6;
 cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st);
