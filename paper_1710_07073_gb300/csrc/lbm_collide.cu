@@ -238,15 +238,306 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
     else collide_store<ST, false>(fout, S, site, rv, 0.0f, 0.0f, 0.0f, cp, flag);
 }
 
+// ---------------------------------------------------------------------------
+// Two nodes per thread (even nx).  Each thread owns the x-pair (x0, x0 + 1),
+// x0 even, so every plane row is read and written with aligned 2-wide vector
+// accesses (float2, half2, bfloat162) and the collision runs on packed FP32
+// pairs (FFMA2 / FADD2 / FMUL2).  Populations crossing x come from the
+// neighbouring pair in the same row through a warp shuffle; the two lanes at
+// the ends of a 16-lane row group, and nodes on the box faces, take those
+// from the general pull instead.  A CTA is 16 x 4 x 2 threads = 32 x 4 x 2
+// nodes, inside one binning tile.
+// ---------------------------------------------------------------------------
+constexpr int PX = TX / 2;   // threads along x
+constexpr int PZ = 2;        // z-planes per CTA (TZ is a multiple of 2)
+static_assert(PX == 16 && (PX * TY) % 32 == 0 && TZ % PZ == 0,
+              "a warp must hold two whole 16-lane rows of one z-plane");
+
+template <int ST> struct Vec2;
+template <> struct Vec2<0> {
+    static __device__ __forceinline__ float2 load(const float* p) {
+        return __ldg(reinterpret_cast<const float2*>(p));
+    }
+    static __device__ __forceinline__ void store(float* p, float2 v) {
+        __stcs(reinterpret_cast<float2*>(p), v);
+    }
+};
+template <> struct Vec2<1> {
+    static __device__ __forceinline__ float2 load(const __half* p) {
+        return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+    }
+    static __device__ __forceinline__ void store(__half* p, float2 v) {
+        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(v.x, v.y));
+    }
+};
+template <> struct Vec2<2> {
+    static __device__ __forceinline__ float2 load(const __nv_bfloat16* p) {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float2 v) {
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(v.x, v.y));
+    }
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// Force of one bubble record on the pair (x0, x0 + 1) at (y, z), Eq. 19 and 21.
+__device__ __forceinline__ void add_bubble_force_pair(const BubbleRec& r, const Geo& g, int x0,
+                                                      int y, int z, float2& Fx, float2& Fy,
+                                                      float2& Fz) {
+    float ry = (float)(y - r.ay) + 0.5f - r.fy;
+    float rz = (float)(z - r.az) + 0.5f - r.fz;
+    if (!(g.walls & 0x04)) {
+        if (ry > 0.5f * g.ny) ry -= (float)g.ny;
+        else if (ry < -0.5f * g.ny) ry += (float)g.ny;
+    }
+    if (!(g.walls & 0x10)) {
+        if (rz > 0.5f * g.nz) rz -= (float)g.nz;
+        else if (rz < -0.5f * g.nz) rz += (float)g.nz;
+    }
+    const float wy = cell_poly(ry * r.inv_n, r.h);
+    if (wy == 0.0f) return;
+    const float wyz = wy * cell_poly(rz * r.inv_n, r.h);
+    if (wyz == 0.0f) return;
+    float w[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float rx = (float)(x0 + k - r.ax) + 0.5f - r.fx;
+        if (!(g.walls & 0x01)) {
+            if (rx > 0.5f * g.nx) rx -= (float)g.nx;
+            else if (rx < -0.5f * g.nx) rx += (float)g.nx;
+        }
+        w[k] = cell_poly(rx * r.inv_n, r.h) * wyz;
+    }
+    const float2 wv = make_float2(w[0], w[1]);
+    Fx = fma2(wv, f2(r.px), Fx);
+    Fy = fma2(wv, f2(r.py), Fy);
+    Fz = fma2(wv, f2(r.pz), Fz);
+}
+
+// Raw values of direction J arriving at the pair (x0, x0 + 1) of a row whose
+// y and z neighbours are inside the box.
+// A warp holds two rows (16 lanes each) that may take different gather paths,
+// so each shuffle names only its own row's lanes (`row_mask`).
+template <int ST, int J>
+__device__ __forceinline__ float2 pull_pair(const typename Store<ST>::T* __restrict__ f,
+                                            const Geo& g, unsigned S, unsigned site0,
+                                            unsigned nx, unsigned nxy, unsigned row_mask,
+                                            int lane16, int x0, int y, int z) {
+    const unsigned row = (unsigned)J * S + site0 - ((unsigned)cy(J) * nx + (unsigned)cz(J) * nxy);
+    const float2 P = Vec2<ST>::load(f + row);   // the source row at (x0, x0 + 1)
+    if (cx(J) == 0) return P;
+    if (cx(J) == 1) {
+        // node x0 receives x0 - 1 (high half of the left pair), x0 + 1 receives x0
+        float m = __shfl_up_sync(row_mask, P.y, 1, PX);
+        if (lane16 == 0 || x0 == 0) m = pull_raw_any<ST, J>(f, g, x0, y, z);
+        return make_float2(m, P.x);
+    }
+    // cx == -1: node x0 receives x0 + 1, x0 + 1 receives x0 + 2 (low half of the right pair)
+    float p = __shfl_down_sync(row_mask, P.x, 1, PX);
+    if (lane16 == PX - 1 || x0 + 2 >= g.nx) p = pull_raw_any<ST, J>(f, g, x0 + 1, y, z);
+    return make_float2(P.y, p);
+}
+
+template <int ST, int J>
+__device__ __forceinline__ float2 pull_pair_any(const typename Store<ST>::T* __restrict__ f,
+                                                const Geo& g, int x0, int y, int z) {
+    return make_float2(pull_raw_any<ST, J>(f, g, x0, y, z), pull_raw_any<ST, J>(f, g, x0 + 1, y, z));
+}
+
+template <int ST, int J, bool FORCED>
+__device__ __forceinline__ void relax_pair2(typename Store<ST>::T* __restrict__ fout, unsigned S,
+                                            unsigned site0, const float2 rv[Q], float2 base,
+                                            float2 rho, float2 ux, float2 uy, float2 uz,
+                                            float2 Fx, float2 Fy, float2 Fz, float2 uF,
+                                            const CollideParams& cp, bool store) {
+    const float C = Store<ST>::kScaled ? cp.scale : wf(J);
+    float2 cu = f2(0.0f);
+    if (cx(J) != 0) cu = fma2(f2((float)cx(J)), ux, cu);
+    if (cy(J) != 0) cu = fma2(f2((float)cy(J)), uy, cu);
+    if (cz(J) != 0) cu = fma2(f2((float)cz(J)), uz, cu);
+    const float2 rcu = mul2(rho, cu);
+    float2 even = mul2(f2(cp.omega), fma2(mul2(f2(4.5f), rcu), cu, base));
+    float2 odd = mul2(f2(3.0f * cp.omega), rcu);
+    if (FORCED) {
+        float2 cF = f2(0.0f);
+        if (cx(J) != 0) cF = fma2(f2((float)cx(J)), Fx, cF);
+        if (cy(J) != 0) cF = fma2(f2((float)cy(J)), Fy, cF);
+        if (cz(J) != 0) cF = fma2(f2((float)cz(J)), Fz, cF);
+        even = fma2(f2(cp.pref), fma2(mul2(f2(9.0f), cu), cF, mul2(f2(-3.0f), uF)), even);
+        odd = fma2(f2(3.0f * cp.pref), cF, odd);
+    }
+    const float2 om1 = f2(1.0f - cp.omega);
+    const float2 a = fma2(om1, rv[J], mul2(f2(C), add2(even, odd)));
+    const float2 b = fma2(om1, rv[J + 1], mul2(f2(C), sub2(even, odd)));
+    if (store) {
+        Vec2<ST>::store(fout + ((unsigned)J * S + site0), a);
+        Vec2<ST>::store(fout + ((unsigned)(J + 1) * S + site0), b);
+    }
+}
+
+template <int ST, bool FORCED>
+__device__ __forceinline__ void collide_store_pair(typename Store<ST>::T* __restrict__ fout,
+                                                   unsigned S, unsigned site0, const float2 rv[Q],
+                                                   float2 Fx, float2 Fy, float2 Fz,
+                                                   const CollideParams& cp, int* flag,
+                                                   bool store) {
+    const float2 s_axis = add2(add2(add2(rv[1], rv[2]), add2(rv[3], rv[4])), add2(rv[5], rv[6]));
+    const float2 s_edge = add2(add2(add2(add2(rv[7], rv[8]), add2(rv[9], rv[10])),
+                                    add2(add2(rv[11], rv[12]), add2(rv[13], rv[14]))),
+                               add2(add2(rv[15], rv[16]), add2(rv[17], rv[18])));
+    const float2 ax_x = sub2(rv[1], rv[2]), ax_y = sub2(rv[3], rv[4]), ax_z = sub2(rv[5], rv[6]);
+    const float2 d78 = sub2(rv[7], rv[8]), d910 = sub2(rv[9], rv[10]);
+    const float2 d1112 = sub2(rv[11], rv[12]), d1314 = sub2(rv[13], rv[14]);
+    const float2 d1516 = sub2(rv[15], rv[16]), d1718 = sub2(rv[17], rv[18]);
+    const float2 ed_x = add2(add2(d78, d910), add2(d1112, d1314));
+    const float2 ed_y = add2(sub2(d78, d910), add2(d1516, d1718));
+    const float2 ed_z = add2(sub2(d1112, d1314), sub2(d1516, d1718));
+    float2 drho, jx, jy, jz;
+    if (Store<ST>::kScaled) {
+        const float2 k0 = f2(wf(0) * cp.inv_scale), ka = f2(wf(1) * cp.inv_scale),
+                     ke = f2(wf(7) * cp.inv_scale);
+        drho = fma2(k0, rv[0], fma2(ka, s_axis, mul2(ke, s_edge)));
+        jx = fma2(ka, ax_x, mul2(ke, ed_x));
+        jy = fma2(ka, ax_y, mul2(ke, ed_y));
+        jz = fma2(ka, ax_z, mul2(ke, ed_z));
+    } else {
+        drho = add2(rv[0], add2(s_axis, s_edge));
+        jx = add2(ax_x, ed_x);
+        jy = add2(ax_y, ed_y);
+        jz = add2(ax_z, ed_z);
+    }
+    const float2 rho = add2(f2(cp.rho0), drho);
+    const float2 inv_rho = make_float2(1.0f / rho.x, 1.0f / rho.y);
+    float2 ux, uy, uz;
+    if (FORCED) {
+        ux = mul2(fma2(f2(0.5f), Fx, jx), inv_rho);
+        uy = mul2(fma2(f2(0.5f), Fy, jy), inv_rho);
+        uz = mul2(fma2(f2(0.5f), Fz, jz), inv_rho);
+    } else {
+        ux = mul2(jx, inv_rho);
+        uy = mul2(jy, inv_rho);
+        uz = mul2(jz, inv_rho);
+    }
+    const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+    if (store && !(usq.x < 0.09f && usq.y < 0.09f)) atomicOr(flag, 1);
+    const float2 uF = FORCED ? fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz))) : f2(0.0f);
+    const float2 base = fma2(mul2(f2(-1.5f), rho), usq, drho);
+    float2 e0 = mul2(f2(cp.omega), base);
+    if (FORCED) e0 = fma2(f2(-3.0f * cp.pref), uF, e0);
+    const float C0 = Store<ST>::kScaled ? cp.scale : wf(0);
+    const float2 r0 = fma2(f2(1.0f - cp.omega), rv[0], mul2(f2(C0), e0));
+    if (store) Vec2<ST>::store(fout + site0, r0);
+#define LBM_PAIR2(J) relax_pair2<ST, J, FORCED>(fout, S, site0, rv, base, rho, ux, uy, uz, Fx, Fy, Fz, uF, cp, store)
+    LBM_PAIR2(1); LBM_PAIR2(3); LBM_PAIR2(5); LBM_PAIR2(7); LBM_PAIR2(9);
+    LBM_PAIR2(11); LBM_PAIR2(13); LBM_PAIR2(15); LBM_PAIR2(17);
+#undef LBM_PAIR2
+}
+
+template <int ST>
+__global__ void __launch_bounds__(PX * TY * PZ, 6)
+k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
+                      typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
+                      const int* __restrict__ tile_start, const int* __restrict__ tile_count,
+                      const int* __restrict__ items, int cap,
+                      const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
+    __shared__ BubbleRec srec[PX * TY * PZ];
+    const int lane16 = threadIdx.x;
+    const int x0 = blockIdx.x * TX + 2 * threadIdx.x;
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z = blockIdx.z * PZ + threadIdx.z;
+    const bool active = (x0 < g.nx) && (y < g.ny) && (z < g.nz);
+    // Inactive threads still take part in the row shuffles, at a valid node.
+    const int xa = active ? x0 : 0;
+    const int ya = min(y, g.ny - 1), za = min(z, g.nz - 1);
+
+    float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
+    bool forced = false;   // uniform over the CTA (one tile)
+    if (tile_count != nullptr) {
+        const int t = (((blockIdx.z * PZ) / TZ) * g.nty + blockIdx.y) * g.ntx + blockIdx.x;
+        const int n_t = tile_count[t];
+        if (n_t > 0) {
+            forced = true;
+            const int beg = tile_start[t];
+            const int end = min(beg + n_t, cap);
+            const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
+            constexpr int NT = PX * TY * PZ;
+            for (int c0 = beg; c0 < end; c0 += NT) {
+                const int cnt = min(NT, end - c0);
+                __syncthreads();
+                if (tid < cnt) {
+                    const int id = items[c0 + tid];
+                    if (id >= 0 && id < nb) srec[tid] = recs[id];
+                    else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                }
+                __syncthreads();
+                if (active)
+                    for (int k = 0; k < cnt; ++k)
+                        add_bubble_force_pair(srec[k], g, x0, y, z, Fx, Fy, Fz);
+            }
+        }
+    }
+
+    const unsigned S = (unsigned)g.S;
+    const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+    const unsigned site0 = (unsigned)za * nxy + (unsigned)ya * nx + (unsigned)xa;
+    float2 rv[Q];
+    if (ya > 0 && ya < g.ny - 1 && za > 0 && za < g.nz - 1) {
+        // Lanes 0-15 or 16-31 of the warp: PX * TY is a multiple of 32, so the
+        // row's half is threadIdx.y & 1.
+        const unsigned row_mask = 0xffffu << (16 * (threadIdx.y & 1));
+#define LBM_PP(J) rv[J] = pull_pair<ST, J>(fin, g, S, site0, nx, nxy, row_mask, lane16, xa, ya, za)
+        LBM_PP(0); LBM_PP(1); LBM_PP(2); LBM_PP(3); LBM_PP(4);
+        LBM_PP(5); LBM_PP(6); LBM_PP(7); LBM_PP(8); LBM_PP(9);
+        LBM_PP(10); LBM_PP(11); LBM_PP(12); LBM_PP(13); LBM_PP(14);
+        LBM_PP(15); LBM_PP(16); LBM_PP(17); LBM_PP(18);
+#undef LBM_PP
+    } else {
+#define LBM_PA(J) rv[J] = pull_pair_any<ST, J>(fin, g, xa, ya, za)
+        LBM_PA(0); LBM_PA(1); LBM_PA(2); LBM_PA(3); LBM_PA(4);
+        LBM_PA(5); LBM_PA(6); LBM_PA(7); LBM_PA(8); LBM_PA(9);
+        LBM_PA(10); LBM_PA(11); LBM_PA(12); LBM_PA(13); LBM_PA(14);
+        LBM_PA(15); LBM_PA(16); LBM_PA(17); LBM_PA(18);
+#undef LBM_PA
+    }
+    if (forced) collide_store_pair<ST, true>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
+    else collide_store_pair<ST, false>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
+}
+
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, cudaStream_t st) {
-    dim3 block(TX, TY, 1);
-    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.nz);
     const int* start = tl ? tl->start : nullptr;
     const int* count = tl ? tl->count : nullptr;
     const int* items = tl ? tl->items : nullptr;
     const int cap = tl ? tl->cap : 0;
+    if ((g.nx & 1) == 0) {
+        // Even rows: two nodes per thread with aligned vector accesses.
+        dim3 block(PX, TY, PZ);
+        dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + PZ - 1) / PZ);
+        switch (storage) {
+            case 0:
+                k_collide_stream_pair<0><<<grid, block, 0, st>>>(
+                    (const float*)fin, (float*)fout, g, cp, start, count, items, cap, recs, nb, flag);
+                break;
+            case 1:
+                k_collide_stream_pair<1><<<grid, block, 0, st>>>(
+                    (const __half*)fin, (__half*)fout, g, cp, start, count, items, cap, recs, nb, flag);
+                break;
+            default:
+                k_collide_stream_pair<2><<<grid, block, 0, st>>>(
+                    (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, g, cp, start, count, items,
+                    cap, recs, nb, flag);
+                break;
+        }
+        return cudaGetLastError();
+    }
+    dim3 block(TX, TY, 1);
+    dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.nz);
     switch (storage) {
         case 0:
             k_collide_stream<0><<<grid, block, 0, st>>>((const float*)fin, (float*)fout, g, cp,

@@ -56,10 +56,12 @@ def test_population_roundtrip(dims, walls):
     assert np.abs(back - f).max() < 1e-9
 
 
+@pytest.mark.parametrize("dims", [(37, 9, 11), (38, 9, 11), (2, 3, 5), (96, 6, 7)])
 @pytest.mark.parametrize("omega", [1.0, 1.6, 1.9])
 @pytest.mark.parametrize("walls", WALL_CASES)
-def test_one_step_random_populations(omega, walls):
-    dims = (37, 9, 11)          # two x tiles with a ragged tail, 3 y and 3 z tiles
+def test_one_step_random_populations(omega, walls, dims):
+    # Odd nx runs the one-node-per-thread sweep, even nx the two-node one.
+    # Ragged tails in every axis: x tiles of 32, y tiles of 4, z pairs.
     f = _random_pops(dims, 5)
     col = lbm.Column(dims, omega, walls)
     lbm.lbm_set_populations(col.ctx, oracle_pops_to_lib(f))
@@ -67,6 +69,25 @@ def test_one_step_random_populations(omega, walls):
     got = lib_pops_to_oracle(lbm.lbm_get_populations(col.ctx), dims)
     want = olat.lb_step(f, omega, walls)
     assert np.abs(got - want).max() < POP_ATOL
+
+
+@pytest.mark.parametrize("storage,scale,tol", [(lbm.LBM_STORE_F16, 256.0, 2.0 ** -11),
+                                               (lbm.LBM_STORE_BF16, 1.0, 2.0 ** -8)])
+@pytest.mark.parametrize("dims", [(37, 9, 11), (38, 9, 11)])
+def test_one_step_16bit_from_representable_input(storage, scale, tol, dims):
+    # Both sweeps in 16-bit storage: from populations the format holds exactly,
+    # one step differs from the FP64 step by FP32 arithmetic plus one rounding
+    # of each stored value (half an ulp, relative to f - w rho0).
+    rho, u = workloads.random_fields(dims, seed=8, amp=1e-3, rho_amp=1e-3)
+    f = olat.equilibrium(rho, u)
+    col = lbm.Column(dims, 1.7, olat.ALL_WALLS, storage, scale)
+    lbm.lbm_set_populations(col.ctx, oracle_pops_to_lib(f))
+    f_exact = lib_pops_to_oracle(lbm.lbm_get_populations(col.ctx), dims)
+    lbm.lbm_step(col.ctx, 1)
+    got = lib_pops_to_oracle(lbm.lbm_get_populations(col.ctx), dims)
+    want = olat.lb_step(f_exact, 1.7, olat.ALL_WALLS)
+    dev = np.abs(want - olat.W[:, None, None, None])
+    assert (np.abs(got - want) <= tol * dev + 1e-10).all()
 
 
 def test_fifty_steps_fields():
