@@ -242,16 +242,12 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
 // Two nodes per thread (even nx).  Each thread owns the x-pair (x0, x0 + 1),
 // x0 even, so every plane row is read and written with aligned 2-wide vector
 // accesses (float2, half2, bfloat162) and the collision runs on packed FP32
-// pairs (FFMA2 / FADD2 / FMUL2).  Populations crossing x come from the
-// neighbouring pair in the same row through a warp shuffle; the two lanes at
-// the ends of a 16-lane row group, and nodes on the box faces, take those
-// from the general pull instead.  A CTA is 16 x 4 x 2 threads = 32 x 4 x 2
+// pairs (FFMA2 / FADD2 / FMUL2).  A CTA is 16 x 4 x 2 threads = 32 x 4 x 2
 // nodes, inside one binning tile.
 // ---------------------------------------------------------------------------
 constexpr int PX = TX / 2;   // threads along x
 constexpr int PZ = 2;        // z-planes per CTA (TZ is a multiple of 2)
-static_assert(PX == 16 && (PX * TY) % 32 == 0 && TZ % PZ == 0,
-              "a warp must hold two whole 16-lane rows of one z-plane");
+static_assert(TZ % PZ == 0, "a CTA's z-planes must lie in one binning tile");
 
 template <int ST> struct Vec2;
 template <> struct Vec2<0> {
@@ -321,26 +317,29 @@ __device__ __forceinline__ void add_bubble_force_pair(const BubbleRec& r, const 
 
 // Raw values of direction J arriving at the pair (x0, x0 + 1) of a row whose
 // y and z neighbours are inside the box.
-// A warp holds two rows (16 lanes each) that may take different gather paths,
-// so each shuffle names only its own row's lanes (`row_mask`).
+// Raw values of direction J arriving at the pair (x0, x0 + 1) of a row whose
+// y and z neighbours are inside the box.  The aligned pair of the source row
+// covers one of the two; the population crossing x for the other node is one
+// scalar load, at x0 - 1 or x0 + 2 of the source row, or, on an x face, at the
+// opposite plane of the node itself (wall) or the other end of the row
+// (periodic).  Every lane issues the same loads, so none waits on another.
 template <int ST, int J>
 __device__ __forceinline__ float2 pull_pair(const typename Store<ST>::T* __restrict__ f,
-                                            const Geo& g, unsigned S, unsigned site0,
-                                            unsigned nx, unsigned nxy, unsigned row_mask,
-                                            int lane16, int x0, int y, int z) {
+                                            unsigned S, unsigned site0, unsigned nx,
+                                            unsigned nxy, int x0, bool wallx) {
     const unsigned row = (unsigned)J * S + site0 - ((unsigned)cy(J) * nx + (unsigned)cz(J) * nxy);
     const float2 P = Vec2<ST>::load(f + row);   // the source row at (x0, x0 + 1)
     if (cx(J) == 0) return P;
     if (cx(J) == 1) {
-        // node x0 receives x0 - 1 (high half of the left pair), x0 + 1 receives x0
-        float m = __shfl_up_sync(row_mask, P.y, 1, PX);
-        if (lane16 == 0 || x0 == 0) m = pull_raw_any<ST, J>(f, g, x0, y, z);
-        return make_float2(m, P.x);
+        // node x0 receives x0 - 1, node x0 + 1 receives x0
+        unsigned a = row - 1u;
+        if (x0 == 0) a = wallx ? (unsigned)opp(J) * S + site0 : row + nx - 1u;
+        return make_float2(Store<ST>::load_raw(f + a), P.x);
     }
-    // cx == -1: node x0 receives x0 + 1, x0 + 1 receives x0 + 2 (low half of the right pair)
-    float p = __shfl_down_sync(row_mask, P.x, 1, PX);
-    if (lane16 == PX - 1 || x0 + 2 >= g.nx) p = pull_raw_any<ST, J>(f, g, x0 + 1, y, z);
-    return make_float2(P.y, p);
+    // cx == -1: node x0 receives x0 + 1, node x0 + 1 receives x0 + 2
+    unsigned a = row + 2u;
+    if ((unsigned)x0 + 2u >= nx) a = wallx ? (unsigned)opp(J) * S + site0 + 1u : row - (unsigned)x0;
+    return make_float2(P.y, Store<ST>::load_raw(f + a));
 }
 
 template <int ST, int J>
@@ -446,12 +445,11 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                       const int* __restrict__ items, int cap,
                       const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
     __shared__ BubbleRec srec[PX * TY * PZ];
-    const int lane16 = threadIdx.x;
     const int x0 = blockIdx.x * TX + 2 * threadIdx.x;
     const int y = blockIdx.y * TY + threadIdx.y;
     const int z = blockIdx.z * PZ + threadIdx.z;
     const bool active = (x0 < g.nx) && (y < g.ny) && (z < g.nz);
-    // Inactive threads still take part in the row shuffles, at a valid node.
+    // Inactive threads gather at a valid node and store nothing.
     const int xa = active ? x0 : 0;
     const int ya = min(y, g.ny - 1), za = min(z, g.nz - 1);
 
@@ -487,10 +485,8 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
     const unsigned site0 = (unsigned)za * nxy + (unsigned)ya * nx + (unsigned)xa;
     float2 rv[Q];
     if (ya > 0 && ya < g.ny - 1 && za > 0 && za < g.nz - 1) {
-        // Lanes 0-15 or 16-31 of the warp: PX * TY is a multiple of 32, so the
-        // row's half is threadIdx.y & 1.
-        const unsigned row_mask = 0xffffu << (16 * (threadIdx.y & 1));
-#define LBM_PP(J) rv[J] = pull_pair<ST, J>(fin, g, S, site0, nx, nxy, row_mask, lane16, xa, ya, za)
+        const bool wallx = (g.walls & 0x01) != 0;
+#define LBM_PP(J) rv[J] = pull_pair<ST, J>(fin, S, site0, nx, nxy, xa, wallx)
         LBM_PP(0); LBM_PP(1); LBM_PP(2); LBM_PP(3); LBM_PP(4);
         LBM_PP(5); LBM_PP(6); LBM_PP(7); LBM_PP(8); LBM_PP(9);
         LBM_PP(10); LBM_PP(11); LBM_PP(12); LBM_PP(13); LBM_PP(14);
