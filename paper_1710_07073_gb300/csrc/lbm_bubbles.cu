@@ -52,14 +52,12 @@ __device__ __forceinline__ void make_record(const double* xb, double inv_n, cons
 
 // One CTA of BUBBLE_THREADS threads per bubble: the threads stride over the
 // window's nodes for the forward coupling, thread 0 integrates the bubble.
-constexpr int BUBBLE_THREADS = 128;
+constexpr int BUBBLE_THREADS = 256;
 
 template <int ST>
-__global__ void __launch_bounds__(BUBBLE_THREADS)
-k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, BubbleDev B,
-          BubbleConst bc, int* __restrict__ flag) {
-    __shared__ double red[3][BUBBLE_THREADS / 32];
-    const int b = blockIdx.x;
+__device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const Geo& g,
+                              const CollideParams& cp, const BubbleDev& B, const BubbleConst& bc,
+                              int* __restrict__ flag, int b, double (*red)[BUBBLE_THREADS / 32]) {
     const int tid = threadIdx.x;
     if (b >= B.nb) return;
     if (!B.active[b]) {
@@ -182,7 +180,7 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
         const float vf0 = (float)v0, vf1 = (float)v1, vf2 = (float)v2;
         const float speed = sqrtf(vf0 * vf0 + vf1 * vf1 + vf2 * vf2);
         const float re = speed * re_per_speed;
-        const float visc_a = visc_a0 * (1.0f + sn_coeff * powf(re, sn_exp));
+        const float visc_a = visc_a0 * (1.0f + sn_coeff * __powf(re, sn_exp));
         const double cdv = (double)fmaxf(fminf(visc_a, visc_b), eo_term * speed);   // C_D |v|
         const double fd[3] = {-drag_pref * cdv * v0, -drag_pref * cdv * v1,
                               -drag_pref * cdv * v2};
@@ -233,6 +231,14 @@ k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, 
     if ((g.walls & 0x20) && xb[2] >= (double)g.nz - r) B.active[b] = 0;
 }
 
+template <int ST>
+__global__ void __launch_bounds__(BUBBLE_THREADS)
+k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, BubbleDev B,
+          BubbleConst bc, int* __restrict__ flag) {
+    __shared__ double red[3][BUBBLE_THREADS / 32];
+    bubble_update<ST>(f, g, cp, B, bc, flag, blockIdx.x, red);
+}
+
 // Table 1 / Eq. 3 constants of each bubble (FP64).
 __global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_factor) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -259,24 +265,6 @@ __global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_fac
 cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
     k_bubble_constants<<<(b.nb + 127) / 128, 128, 0, st>>>(b, bc, 0.0);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
-                           const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st) {
-    if (b.nb == 0) return cudaSuccess;
-    switch (storage) {
-        case 0:
-            k_bubbles<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, g, cp, b, bc, flag);
-            break;
-        case 1:
-            k_bubbles<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, g, cp, b, bc, flag);
-            break;
-        default:
-            k_bubbles<2><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, g, cp, b, bc,
-                                                          flag);
-            break;
-    }
     return cudaGetLastError();
 }
 
@@ -448,47 +436,46 @@ cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, c
 // Few pairs: one CTA enumerates every (tile, bubble) pair, sorts the keys
 // (tile << 32 | bubble) with a bitonic network in shared memory and writes the
 // runs.  The per-tile counts stay valid between calls because only the tiles
-// the previous call touched are cleared first.
-constexpr int SMALL_THREADS = 1024;
-
-__global__ void __launch_bounds__(SMALL_THREADS) k_bin_small(Geo g, BubbleDev B, SmallBins sb) {
-    __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
-    __shared__ int s_n;
-    const int tid = threadIdx.x;
-    const int prev = min(max(*sb.prev_n, 0), SMALL_MAX_PAIRS);
-    for (int i = tid; i < prev; i += SMALL_THREADS) {
-        const int t = sb.prev_tiles[i];
+// the previous call touched are cleared first.  The bubble state is read with
+// __ldcg: it was written by other CTAs of the same launch.
+__device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBins& sb,
+                                unsigned long long* keys, int* s_n) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int prev = min(max(__ldcg(sb.prev_n), 0), SMALL_MAX_PAIRS);
+    for (int i = tid; i < prev; i += nt) {
+        const int t = __ldcg(sb.prev_tiles + i);
         if (t >= 0 && t < sb.T) sb.count[t] = 0;
     }
-    if (tid == 0) s_n = 0;
+    if (tid == 0) *s_n = 0;
     __syncthreads();
     const int L[3] = {g.nx, g.ny, g.nz};
     const int T[3] = {TX, TY, TZ};
-    for (int b = tid; b < B.nb; b += SMALL_THREADS) {
-        if (!B.spread[b]) continue;
+    for (int b = tid; b < B.nb; b += nt) {
+        if (!__ldcg(B.spread + b)) continue;
         int tl[3][MAX_AXIS_TILES];
-        int nt[3];
-        const double n = B.n[b];
+        int ntl[3];
+        const double n = __ldcg(B.n + b);
         for (int a = 0; a < 3; ++a)
-            nt[a] = axis_tiles(B.x[3 * b + a], n, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
-        for (int iz = 0; iz < nt[2]; ++iz)
-            for (int iy = 0; iy < nt[1]; ++iy)
-                for (int ix = 0; ix < nt[0]; ++ix) {
+            ntl[a] = axis_tiles(__ldcg(B.x + 3 * b + a), n, L[a], !(g.walls & (1u << (2 * a))),
+                                T[a], tl[a]);
+        for (int iz = 0; iz < ntl[2]; ++iz)
+            for (int iy = 0; iy < ntl[1]; ++iy)
+                for (int ix = 0; ix < ntl[0]; ++ix) {
                     const unsigned t = (unsigned)((tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix]);
-                    const int k = atomicAdd(&s_n, 1);
+                    const int k = atomicAdd(s_n, 1);
                     if (k < SMALL_MAX_PAIRS) keys[k] = ((unsigned long long)t << 32) | (unsigned)b;
                     else atomicOr(sb.overflow, 1);
                 }
     }
     __syncthreads();
-    const int n = min(s_n, SMALL_MAX_PAIRS);
+    const int n = min(*s_n, SMALL_MAX_PAIRS);
     int p2 = 1;
     while (p2 < n) p2 <<= 1;
-    for (int i = n + tid; i < p2; i += SMALL_THREADS) keys[i] = ~0ull;
+    for (int i = n + tid; i < p2; i += nt) keys[i] = ~0ull;
     __syncthreads();
     for (int k = 2; k <= p2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < p2; i += SMALL_THREADS) {
+            for (int i = tid; i < p2; i += nt) {
                 const int l = i ^ j;
                 if (l > i) {
                     const unsigned long long a = keys[i], c = keys[l];
@@ -502,7 +489,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bin_small(Geo g, BubbleDev B,
             __syncthreads();
         }
     }
-    for (int i = tid; i < n; i += SMALL_THREADS) {
+    for (int i = tid; i < n; i += nt) {
         const int t = (int)(keys[i] >> 32);
         sb.items[i] = (int)(keys[i] & 0xffffffffu);
         sb.prev_tiles[i] = t;
@@ -512,9 +499,62 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bin_small(Geo g, BubbleDev B,
     if (tid == 0) *sb.prev_n = n;
 }
 
-cudaError_t launch_binning_small(const Geo& g, const BubbleDev& b, const SmallBins& sb,
-                                 cudaStream_t st) {
-    k_bin_small<<<1, SMALL_THREADS, 0, st>>>(g, b, sb);
+// Bubble update with the few-pair binning fused behind it: every CTA updates
+// its bubble, then counts itself done; the CTA that finds all others done
+// (no waiting: it is simply the last to arrive) bins all bubbles.
+template <int ST>
+__global__ void __launch_bounds__(BUBBLE_THREADS)
+k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
+                 BubbleDev B, BubbleConst bc, int* __restrict__ flag, SmallBins sb) {
+    __shared__ double red[3][BUBBLE_THREADS / 32];
+    __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
+    __shared__ int s_n, s_last;
+    bubble_update<ST>(f, g, cp, B, bc, flag, blockIdx.x, red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();                                 // publish this bubble's state
+        s_last = atomicAdd(sb.done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    bin_small_block(g, B, sb, keys, &s_n);
+    if (threadIdx.x == 0) *sb.done = 0;                  // ready for the next launch
+}
+
+cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
+                           const BubbleDev& b, const BubbleConst& bc, int* flag,
+                           const SmallBins* fused, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    if (fused) {
+        switch (storage) {
+            case 0:
+                k_bubbles_binned<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, g, cp, b, bc,
+                                                                     flag, *fused);
+                break;
+            case 1:
+                k_bubbles_binned<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, g, cp, b, bc,
+                                                                     flag, *fused);
+                break;
+            default:
+                k_bubbles_binned<2><<<b.nb, BUBBLE_THREADS, 0, st>>>(
+                    (const __nv_bfloat16*)f, g, cp, b, bc, flag, *fused);
+                break;
+        }
+        return cudaGetLastError();
+    }
+    switch (storage) {
+        case 0:
+            k_bubbles<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, g, cp, b, bc, flag);
+            break;
+        case 1:
+            k_bubbles<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, g, cp, b, bc, flag);
+            break;
+        default:
+            k_bubbles<2><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, g, cp, b, bc,
+                                                          flag);
+            break;
+    }
     return cudaGetLastError();
 }
 

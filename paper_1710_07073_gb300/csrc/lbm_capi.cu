@@ -199,7 +199,7 @@ void free_bubbles(lbm_ctx* c) {
     SmallBins& sb = c->small;
     void* ptrs[] = {b.k, b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
                     b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items, sb.prev_tiles,
-                    sb.prev_n, sb.overflow};
+                    sb.prev_n, sb.overflow, sb.done};
     for (void* p : ptrs) dfree(c, p);
     b = BubbleDev{};
     sb = SmallBins{};
@@ -470,7 +470,9 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sb.prev_tiles = (int*)dalloc(c, sizeof(int) * SMALL_MAX_PAIRS);
         sb.prev_n = (int*)dalloc(c, sizeof(int));
         sb.overflow = (int*)dalloc(c, sizeof(int));
-        lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow;
+        sb.done = (int*)dalloc(c, sizeof(int));
+        lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow &&
+                   sb.done;
     } else {
         c->bins.cap = (int)cap;
         c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
@@ -486,6 +488,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         LBM_CUDA(cudaMemsetAsync(sb.count, 0, sizeof(int) * (size_t)sb.T, c->stream), "count");
         LBM_CUDA(cudaMemsetAsync(sb.prev_n, 0, sizeof(int), c->stream), "prev_n");
         LBM_CUDA(cudaMemsetAsync(sb.overflow, 0, sizeof(int), c->stream), "overflow");
+        LBM_CUDA(cudaMemsetAsync(sb.done, 0, sizeof(int), c->stream), "done");
     }
     B.nb = n;
     std::vector<double> hn(n), zeros(3 * (size_t)n, 0.0);
@@ -523,11 +526,11 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     const bool two_way = bubbles && c->p.two_way;
     for (int s = 0; s < nsteps; ++s) {
         if (bubbles) {
-            LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bc, c->flag_d, c->stream),
+            LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bc, c->flag_d,
+                                    c->use_small ? &c->small : nullptr, c->stream),
                      "bubble update");
             if (c->use_small) {
-                LBM_CUDA(launch_binning_small(g, c->bub, c->small, c->stream), "binning");
-                c->launches += 2;
+                c->launches += 1;   // binning fused into the bubble update
             } else {
                 LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
                 c->launches += 1 + BINNING_LAUNCHES;

@@ -245,6 +245,10 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
 // pairs (FFMA2 / FADD2 / FMUL2).  A CTA is 16 x 4 x 2 threads = 32 x 4 x 2
 // nodes, inside one binning tile.
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM the register budget is sized for: FP32 rows move twice
+// the bytes per thread and keep more registers; the 16-bit formats need more
+// warps in flight to cover memory latency (measured on GB300).
+template <int ST> struct PairOccupancy { static constexpr int kMinBlocks = ST == 0 ? 6 : 8; };
 constexpr int PX = TX / 2;   // threads along x
 constexpr int PZ = 2;        // z-planes per CTA (TZ is a multiple of 2)
 static_assert(TZ % PZ == 0, "a CTA's z-planes must lie in one binning tile");
@@ -438,7 +442,7 @@ __device__ __forceinline__ void collide_store_pair(typename Store<ST>::T* __rest
 }
 
 template <int ST>
-__global__ void __launch_bounds__(PX * TY * PZ, 6)
+__global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
 k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                       typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
                       const int* __restrict__ tile_start, const int* __restrict__ tile_count,

@@ -143,16 +143,18 @@ struct SmallBins {
     int* prev_tiles;   // [SMALL_MAX_PAIRS] tile of each pair of the last binning
     int* prev_n;       // [1] number of pairs of the last binning
     int* overflow;     // [1]
+    int* done;         // [1] CTAs of the bubble update that have finished (0 between launches)
 };
 
 // ---- launchers (defined in the kernel translation units) -------------------
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
-cudaError_t launch_binning_small(const Geo& g, const BubbleDev& b, const SmallBins& sb,
-                                 cudaStream_t st);
+
+// Bubble update; with `fused` the few-pair binning runs in the same launch.
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
-                           const BubbleDev& b, const BubbleConst& bc, int* flag, cudaStream_t st);
+                           const BubbleDev& b, const BubbleConst& bc, int* flag,
+                           const SmallBins* fused, cudaStream_t st);
 cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st);
 // Kernels launched by one launch_binning call (count, 3-pass scan, fill, sort).
 constexpr int BINNING_LAUNCHES = 6;
