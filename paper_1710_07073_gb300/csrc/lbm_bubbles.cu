@@ -18,24 +18,29 @@ namespace lbm {
 
 // Window normalisation along one axis: the integral of the mapping over the
 // in-box part of [-n, n] (without 15/16); the full 16/15 on a periodic axis.
-__device__ __forceinline__ double axis_norm(double xa, double inv_n, int L, bool periodic) {
-    if (periodic) return cell_poly_d(-1.0, 1.0);
-    return cell_poly_d(-xa * inv_n, ((double)L - xa) * inv_n);
+__device__ __forceinline__ float axis_norm(double xa, float inv_n, int L, bool periodic) {
+    if (periodic) return 16.0f / 15.0f;
+    const float lo = (float)(-xa) * inv_n, hi = (float)((double)L - xa) * inv_n;
+    const float a = fmaxf(lo, -1.0f), b = fminf(hi, 1.0f);
+    if (!(b > a)) return 0.0f;
+    const float a2 = a * a, b2 = b * b, ab = a * b;
+    const float p4 = b2 * b2 + b2 * ab + ab * ab + ab * a2 + a2 * a2;
+    return (b - a) * (p4 * 0.2f - (b2 + ab + a2) * (2.0f / 3.0f) + 1.0f);
 }
 
-__device__ __forceinline__ void make_record(const double* xb, double inv_n, const Geo& g,
-                                            const double* psi, BubbleRec& r) {
+__device__ __forceinline__ void make_record(const double* xb, float inv_n, const Geo& g,
+                                            const float* psi, BubbleRec& r) {
     int anc[3];
     float fr[3];
-    double norm = 1.0;
+    float norm = 1.0f;
     const int L[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
-        double fl = floor(xb[a]);
+        const double fl = floor(xb[a]);
         anc[a] = (int)fl;
         fr[a] = (float)(xb[a] - fl);
         norm *= axis_norm(xb[a], inv_n, L[a], !(g.walls & (1u << (2 * a))));
     }
-    const double inv_norm = 1.0 / norm;
+    const float inv_norm = 1.0f / norm;
     r.ax = anc[0];
     r.ay = anc[1];
     r.az = anc[2];
@@ -43,21 +48,26 @@ __device__ __forceinline__ void make_record(const double* xb, double inv_n, cons
     r.fx = fr[0];
     r.fy = fr[1];
     r.fz = fr[2];
-    r.inv_n = (float)inv_n;
-    r.h = (float)(0.5 * inv_n);
-    r.px = (float)(psi[0] * inv_norm);
-    r.py = (float)(psi[1] * inv_norm);
-    r.pz = (float)(psi[2] * inv_norm);
+    r.inv_n = inv_n;
+    r.h = 0.5f * inv_n;
+    r.px = psi[0] * inv_norm;
+    r.py = psi[1] * inv_norm;
+    r.pz = psi[2] * inv_norm;
 }
 
 // One CTA of BUBBLE_THREADS threads per bubble: the threads stride over the
 // window's nodes for the forward coupling, thread 0 integrates the bubble.
+//
+// Precision: positions are integrated in FP64 (they reach hundreds of lattice
+// units and move by 1e-5 per sub-step); velocities, forces and the mapping
+// weights are FP32.  FP64 latency on this GPU is long, so only the position
+// update, the window bounds and the wall tests use it.
 constexpr int BUBBLE_THREADS = 256;
 
 template <int ST>
 __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const Geo& g,
                               const CollideParams& cp, const BubbleDev& B, const BubbleConst& bc,
-                              int* __restrict__ flag, int b, double (*red)[BUBBLE_THREADS / 32]) {
+                              int* __restrict__ flag, int b, float (*red)[BUBBLE_THREADS / 32]) {
     const int tid = threadIdx.x;
     if (b >= B.nb) return;
     if (!B.active[b]) {
@@ -84,9 +94,10 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
     }
 
     // Window cells per axis (Algorithm 1 step 2): cells overlapping (x - n, x + n).
+    const float inv_n = K.inv_nf, hh = 0.5f * K.inv_nf;
     int lo[3], cnt[3], anc[3];
     float fr[3];
-    double norm = 1.0;
+    float norm = 1.0f;
     for (int a = 0; a < 3; ++a) {
         const bool periodic = !(g.walls & (1u << (2 * a)));
         int l = (int)floor(xb[a] - n);
@@ -97,12 +108,11 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
         }
         lo[a] = l;
         cnt[a] = min(max(h - l + 1, 0), 2 * (int)MAX_HALF_WIDTH + 2);
-        double fl = floor(xb[a]);
+        const double fl = floor(xb[a]);
         anc[a] = (int)fl;
         fr[a] = (float)(xb[a] - fl);
-        norm *= axis_norm(xb[a], K.inv_n, L[a], periodic);
+        norm *= axis_norm(xb[a], inv_n, L[a], periodic);
     }
-    const float inv_n = (float)K.inv_n, hh = (float)(0.5 * K.inv_n);
 
     // Forward coupling (Eq. 20): threads stride over the window's nodes and
     // weight the bare Eq. 10 velocity of the current populations.
@@ -135,77 +145,72 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
         ay = fmaf(w, jy * inv_rho, ay);
         az = fmaf(w, jz * inv_rho, az);
     }
-    double sx = ax, sy = ay, sz = az;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
     }
     if ((tid & 31) == 0) {
-        red[0][tid >> 5] = sx;
-        red[1][tid >> 5] = sy;
-        red[2][tid >> 5] = sz;
+        red[0][tid >> 5] = ax;
+        red[1][tid >> 5] = ay;
+        red[2][tid >> 5] = az;
     }
     __syncthreads();
     if (tid != 0) return;
-    sx = sy = sz = 0.0;
+    ax = ay = az = 0.0f;
     for (int w = 0; w < BUBBLE_THREADS / 32; ++w) {
-        sx += red[0][w];
-        sy += red[1][w];
-        sz += red[2][w];
+        ax += red[0][w];
+        ay += red[1][w];
+        az += red[2][w];
     }
 
-    const double inv_norm = 1.0 / norm;
-    const double ul[3] = {sx * inv_norm, sy * inv_norm, sz * inv_norm};
-    double dul[3] = {0.0, 0.0, 0.0};
+    const float inv_norm = 1.0f / norm;
+    const float ul[3] = {ax * inv_norm, ay * inv_norm, az * inv_norm};
+    float fvm[3] = {0.0f, 0.0f, 0.0f};   // C_A rho_l V_b D_t u_l
     if (B.has_prev[b]) {
-        const double inv_dt = 1.0 / bc.dt_l;
-        for (int a = 0; a < 3; ++a) dul[a] = (ul[a] - B.ulprev[3 * b + a]) * inv_dt;
+        for (int a = 0; a < 3; ++a)
+            fvm[a] = K.fvm_coef_dt * (ul[a] - (float)B.ulprev[3 * b + a]);
     }
 
     // Table 1 forces and the Newton update of Eq. 4 with the added mass on
-    // the left (m_eff), sub-stepped with dt_b (Table 2).  The state (velocity,
-    // position) is integrated in FP64; the drag coefficient C_D |v| is a
-    // closure evaluated in FP32.
-    const double r = K.r, kdt = K.kdt, fb = K.fb, drag_pref = K.drag_pref;
-    const float eo_term = K.eo_term, visc_a0 = K.visc_a0, visc_b = K.visc_b;
-    const float re_per_speed = K.re_per_speed;
+    // the left (m_eff), sub-stepped with dt_b (Table 2).
+    const double dt_b = bc.dt_b;
+    const double r = K.r;
     const float sn_coeff = (float)bc.sn_coeff, sn_exp = (float)bc.sn_exp;
-    const double fvm[3] = {K.fvm_coef * dul[0], K.fvm_coef * dul[1], K.fvm_coef * dul[2]};
-    double u[3] = {B.u[3 * b], B.u[3 * b + 1], B.u[3 * b + 2]};
-    double fd_sum[3] = {0.0, 0.0, 0.0};
+    const float fb[3] = {0.0f, 0.0f, K.fb};
+    float u[3] = {(float)B.u[3 * b], (float)B.u[3 * b + 1], (float)B.u[3 * b + 2]};
+    float fd_sum[3] = {0.0f, 0.0f, 0.0f};
     for (int k = 0; k < bc.substeps; ++k) {
-        const double v0 = u[0] - ul[0], v1 = u[1] - ul[1], v2 = u[2] - ul[2];
-        const float vf0 = (float)v0, vf1 = (float)v1, vf2 = (float)v2;
-        const float speed = sqrtf(vf0 * vf0 + vf1 * vf1 + vf2 * vf2);
-        const float re = speed * re_per_speed;
-        const float visc_a = visc_a0 * (1.0f + sn_coeff * __powf(re, sn_exp));
-        const double cdv = (double)fmaxf(fminf(visc_a, visc_b), eo_term * speed);   // C_D |v|
-        const double fd[3] = {-drag_pref * cdv * v0, -drag_pref * cdv * v1,
-                              -drag_pref * cdv * v2};
-        const double fz_buoy[3] = {0.0, 0.0, fb};
+        const float v0 = u[0] - ul[0], v1 = u[1] - ul[1], v2 = u[2] - ul[2];
+        const float speed = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+        const float re = speed * K.re_per_speed;
+        const float visc_a = K.visc_a0 * (1.0f + sn_coeff * __powf(re, sn_exp));
+        const float cdv = fmaxf(fminf(visc_a, K.visc_b), K.eo_term * speed);   // C_D |v|
+        const float kd = -K.drag_pref * cdv;
+        const float fd[3] = {kd * v0, kd * v1, kd * v2};
         for (int a = 0; a < 3; ++a) {
             fd_sum[a] += fd[a];
-            u[a] = u[a] + (fz_buoy[a] + fd[a] + fvm[a]) * kdt;
-            xb[a] = xb[a] + u[a] * bc.dt_b;
+            u[a] = fmaf(fb[a] + fd[a] + fvm[a], K.kdt, u[a]);
+            xb[a] = fma((double)u[a], dt_b, xb[a]);
             if (g.walls & (1u << (2 * a))) {
                 if (xb[a] < r) {
                     xb[a] = r;
-                    u[a] = fmax(u[a], 0.0);
+                    u[a] = fmaxf(u[a], 0.0f);
                 }
                 if (xb[a] > (double)L[a] - r) {
                     xb[a] = (double)L[a] - r;
-                    u[a] = fmin(u[a], 0.0);
+                    u[a] = fminf(u[a], 0.0f);
                 }
             } else {
                 xb[a] = __dsub_rn(xb[a], __dmul_rn((double)L[a], floor(xb[a] / (double)L[a])));
             }
         }
     }
-    double psi[3];
+    float psi[3];
+    const float inv_sub = 1.0f / (float)bc.substeps;
     for (int a = 0; a < 3; ++a) {
-        psi[a] = -fd_sum[a] / (double)bc.substeps;
+        psi[a] = -fd_sum[a] * inv_sub;
         B.x[3 * b + a] = xb[a];
         B.u[3 * b + a] = u[a];
         B.ul[3 * b + a] = ul[a];
@@ -226,7 +231,7 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
     int ci[3];
     for (int a = 0; a < 3; ++a) ci[a] = min(max((int)floor(xb[a]), 0), L[a] - 1);
     B.cell[b] = (ci[2] * g.ny + ci[1]) * g.nx + ci[0];
-    make_record(xb, K.inv_n, g, psi, B.rec[b]);
+    make_record(xb, inv_n, g, psi, B.rec[b]);
     // Algorithm 1: the bubble stops once it reaches the top of the liquid.
     if ((g.walls & 0x20) && xb[2] >= (double)g.nz - r) B.active[b] = 0;
 }
@@ -235,7 +240,7 @@ template <int ST>
 __global__ void __launch_bounds__(BUBBLE_THREADS)
 k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, BubbleDev B,
           BubbleConst bc, int* __restrict__ flag) {
-    __shared__ double red[3][BUBBLE_THREADS / 32];
+    __shared__ float red[3][BUBBLE_THREADS / 32];
     bubble_update<ST>(f, g, cp, B, bc, flag, blockIdx.x, red);
 }
 
@@ -248,12 +253,12 @@ __global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_fac
     const double vol = M_PI * d * d * d / 6.0;
     const double eo = (bc.rho_l - bc.rho_b) * bc.g * d * d / bc.sigma;   // Eq. 3 with d^2
     BubbleK K;
-    K.inv_n = 1.0 / B.n[b];
+    K.inv_nf = (float)(1.0 / B.n[b]);
     K.r = r;
-    K.kdt = bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol);
-    K.fb = (bc.rho_l - bc.rho_b) * vol * bc.g;
-    K.drag_pref = 0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale;
-    K.fvm_coef = bc.c_am * bc.rho_l * vol;
+    K.kdt = (float)(bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol));
+    K.fb = (float)((bc.rho_l - bc.rho_b) * vol * bc.g);
+    K.drag_pref = (float)(0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale);
+    K.fvm_coef_dt = (float)(bc.c_am * bc.rho_l * vol / bc.dt_l);
     K.visc_a0 = (float)(24.0 * bc.nu / d);
     K.visc_b = (float)(48.0 * bc.nu / d);
     K.re_per_speed = (float)(d / bc.nu);
@@ -506,7 +511,7 @@ template <int ST>
 __global__ void __launch_bounds__(BUBBLE_THREADS)
 k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
                  BubbleDev B, BubbleConst bc, int* __restrict__ flag, SmallBins sb) {
-    __shared__ double red[3][BUBBLE_THREADS / 32];
+    __shared__ float red[3][BUBBLE_THREADS / 32];
     __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
     __shared__ int s_n, s_last;
     bubble_update<ST>(f, g, cp, B, bc, flag, blockIdx.x, red);

@@ -77,12 +77,12 @@ struct __align__(16) BubbleRec {
 // Per-bubble constants of the closures (Table 1) and of the mapping window,
 // derived from the diameter and the parameters whenever either changes.
 struct BubbleK {
-    double inv_n;       // 1 / n, n = width_factor * d
-    double r;           // d / 2
-    double kdt;         // dt_b / m_eff, m_eff = (rho_b + C_A rho_l) V_b
-    double fb;          // (rho_l - rho_b) V_b g
-    double drag_pref;   // 1/2 rho_l pi r^2 * drag_scale
-    double fvm_coef;    // C_A rho_l V_b
+    double r;           // d / 2 (wall tests on the FP64 position)
+    float inv_nf;       // 1 / n, n = width_factor * d
+    float kdt;          // dt_b / m_eff, m_eff = (rho_b + C_A rho_l) V_b
+    float fb;           // (rho_l - rho_b) V_b g
+    float drag_pref;    // 1/2 rho_l pi r^2 * drag_scale
+    float fvm_coef_dt;  // C_A rho_l V_b / dt_l
     float visc_a0;      // 24 nu / d
     float visc_b;       // 48 nu / d
     float re_per_speed; // d / nu
