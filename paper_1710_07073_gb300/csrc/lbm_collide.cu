@@ -248,9 +248,17 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
 // Resident CTAs per SM the register budget is sized for: FP32 rows move twice
 // the bytes per thread and keep more registers; the 16-bit formats need more
 // warps in flight to cover memory latency (measured on GB300).
-template <int ST> struct PairOccupancy { static constexpr int kMinBlocks = ST == 0 ? 6 : 8; };
+#ifndef LBM_PAIR_MINB_16
+#define LBM_PAIR_MINB_16 8
+#endif
+#ifndef LBM_PAIR_PZ
+#define LBM_PAIR_PZ 2
+#endif
+template <int ST> struct PairOccupancy {
+    static constexpr int kMinBlocks = ST == 0 ? 6 : LBM_PAIR_MINB_16;
+};
 constexpr int PX = TX / 2;   // threads along x
-constexpr int PZ = 2;        // z-planes per CTA (TZ is a multiple of 2)
+constexpr int PZ = LBM_PAIR_PZ;   // z-planes per CTA (divides TZ)
 static_assert(TZ % PZ == 0, "a CTA's z-planes must lie in one binning tile");
 
 template <int ST> struct Vec2;
