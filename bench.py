@@ -49,6 +49,13 @@ def workload(name):
         pos, vel, diam = wl.single_bubble(dims)
         return dict(name="single bubble column 256x256x512", dims=dims, omega=1.6,
                     pos=pos, vel=vel, diam=diam, g=1e-5)
+    if name == "batch":
+        cols = wl.batch_columns(64, seed=1234)
+        return dict(name="batch of 64 single-bubble columns (sizes 32x32x64..128x128x256, omega 1.0-1.9)",
+                    columns=cols, dims=None, omega=None, g=1e-5,
+                    pos=np.concatenate([c[2] for c in cols]),
+                    vel=np.concatenate([c[3] for c in cols]),
+                    diam=np.concatenate([c[4] for c in cols]))
     if name == "swarm":
         dims = wl.SWARM_FULL
         pos, vel, diam = wl.swarm(dims, 100_000, seed=1234)
@@ -216,6 +223,91 @@ def run_reference(args, wl):
     return 0
 
 
+def run_batch(args, wl):
+    """All columns of the batch in one persistent launch per step (graph replays)."""
+    import torch
+    from paper_1710_07073_gb300 import lbm
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lbm.lib()
+    cols = wl["columns"]
+    params = lbm.lbm_default_params()
+    params.g = wl["g"]
+    storage = args.storage
+    b = lbm.Batch([c[0] for c in cols], [c[1] for c in cols], None, STORAGES[storage],
+                  STORAGE_SCALE[storage], params=params)
+    stream = torch.cuda.Stream()
+    lbm.lbm_batch_set_stream(b.h, stream.cuda_stream)
+    lbm.lbm_batch_set_bubbles(b.h, [1] * len(cols), wl["pos"].reshape(-1), wl["vel"].reshape(-1),
+                              wl["diam"])
+    S = lbm.lbm_batch_sites(b.h)
+    depth, grid = lbm.lbm_batch_tune(b.h, 8)
+    lbm.lbm_batch_step(b.h, args.warmup)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3 if sampler.proc else 0.0)
+    launches0 = lbm.lbm_batch_launch_count(b.h)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.mark()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lbm.lbm_batch_step(b.h, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark()
+    ms = ev0.elapsed_time(ev1)
+    launches = lbm.lbm_batch_launch_count(b.h) - launches0
+    clocks = sampler.stop()
+    # Average duration of the persistent collide-stream launch, timed per launch.
+    lbm.lbm_batch_set_kernel_timing(b.h, True)
+    lbm.lbm_batch_step(b.h, min(args.steps, 50))
+    k_ms, k_n = lbm.lbm_batch_get_kernel_time(b.h)
+    lbm.lbm_batch_set_kernel_timing(b.h, False)
+    b.close()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    value = world * S * args.steps / (ms * 1e-3) / 1e6
+    bytes_per_site = 2 * 19 * (4 if storage == "f32" else 2)
+    avg_kernel_s = (k_ms / max(1, k_n)) * 1e-3
+    achieved = bytes_per_site * S / avg_kernel_s / 1e9
+    peak, peak_kind = measured_peak()
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "columns": len(cols), "sites": S, "storage": storage,
+                   "tuned": {"depth": depth, "grid": grid},
+                   "l2": "inputs larger than L2 (%.2f GB populations), no flush" % (
+                       19 * S * (4 if storage == "f32" else 2) / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "k_collide_batch<%s>" % storage,
+                     "algorithmic_bytes_per_launch": bytes_per_site * S,
+                     "avg_launch_ms": round(avg_kernel_s * 1e3, 5), "launches": k_n,
+                     "peak_kind": peak_kind, "timed": "separate per-launch pass after the graph run"},
+        "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def run_gpu(args, wl):
     import torch
     from paper_1710_07073_gb300 import lbm
@@ -358,7 +450,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
-    ap.add_argument("--workload", choices=("single_large", "swarm"), default="single_large")
+    ap.add_argument("--workload", choices=("single_large", "swarm", "batch"), default="single_large")
     ap.add_argument("--storage", choices=tuple(STORAGES), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default=None,
@@ -377,7 +469,11 @@ def main():
         wl.update(dims=dims, pos=pos, vel=vel, diam=diam,
                   name="%s resized to %dx%dx%d" % (wl["name"], *dims))
     if args.impl == "reference":
+        if wl.get("columns"):
+            raise SystemExit("the reference arm times the single-column workloads")
         return run_reference(args, wl)
+    if wl.get("columns"):
+        return run_batch(args, wl)
     return run_gpu(args, wl)
 
 

@@ -201,6 +201,57 @@ int lbm_bytes_per_site(const lbm_ctx* ctx);
 int lbm_set_kernel_timing(lbm_ctx* ctx, int on);
 int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
 
+/* ---- Batches: many independent columns in one launch ---------------------
+ * The grid-independence and stability studies of the paper (Sec. 4.2-4.3,
+ * Tables 5-6, Fig. 5) run the same single-bubble problem on many columns of
+ * different size and relaxation frequency.  A batch advances such columns
+ * together: per coupled step one bubble-update launch for all columns (binning
+ * fused behind it) and one persistent collide-stream launch over all columns'
+ * work items; pairs of steps are captured into a CUDA graph and replayed.
+ * Each column follows exactly the single-column step (the results are
+ * identical to lbm_step on that column alone).
+ *
+ * Limits: every nx must be even; at most 256 columns; the (tile, bubble)
+ * pairs of all bubbles must fit 4096 (about 80 bubbles of d <= 4).  Storage
+ * precision as in lbm_create_storage.  A batch runs on its own non-blocking
+ * stream unless lbm_batch_set_stream gives one (the default stream cannot be
+ * captured). */
+typedef struct lbm_batch lbm_batch;
+
+/* dims3: int[3*ncols] (nx, ny, nz per column); omegas: double[ncols] in
+ * (0, 2); walls: unsigned[ncols] or NULL for bounce-back on all faces. */
+int lbm_batch_create(int ncols, const int* dims3, const double* omegas, const unsigned* walls,
+                     int storage, double scale, lbm_batch** out);
+void lbm_batch_destroy(lbm_batch* b);
+int lbm_batch_set_stream(lbm_batch* b, void* stream);
+int lbm_batch_set_allocator(lbm_batch* b, lbm_alloc_fn alloc, lbm_free_fn free_fn, void* user);
+/* Closure parameters shared by all columns (rho_l only before first use). */
+int lbm_batch_set_params(lbm_batch* b, const lbm_params* p);
+/* counts: int[ncols] bubbles per column; pos3/vel3/diam hold them column
+ * after column (positions in each column's own coordinates). */
+int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, const double* vel3,
+                          const double* diam);
+/* Advance every column by nsteps coupled steps (graph replays). */
+int lbm_batch_step(lbm_batch* b, int nsteps);
+/* Autotuner: times each candidate launch shape -- work-item depth in
+ * z-blocks {1, 2, 4, 8} x persistent CTAs per SM -- for trial_steps steps on
+ * this batch, keeps the fastest, and restores the state the trials advanced.
+ * Either output may be NULL. */
+int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out);
+/* Fields of one column (as lbm_get_fields). */
+int lbm_batch_get_fields(lbm_batch* b, int col, double* rho, double* u3);
+/* All bubbles, column after column (as lbm_get_bubbles). */
+int lbm_batch_get_bubbles(lbm_batch* b, int cap, int* n, double* pos3, double* vel3, double* ul3,
+                          double* psi3, int* active);
+long long lbm_batch_sites(const lbm_batch* b);
+/* Per-launch timing of the persistent collide-stream (steps then run without
+ * the graph); as lbm_set_kernel_timing / lbm_get_kernel_time. */
+int lbm_batch_set_kernel_timing(lbm_batch* b, int on);
+int lbm_batch_get_kernel_time(lbm_batch* b, double* ms, int* launches);
+long long lbm_batch_launch_count(const lbm_batch* b);
+int lbm_batch_sync(lbm_batch* b);
+const char* lbm_batch_last_error(const lbm_batch* b);
+
 /* ---- Binning that allocates nothing -------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory when they need the binning: code running while

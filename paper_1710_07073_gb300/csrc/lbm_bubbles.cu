@@ -443,8 +443,12 @@ cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, c
 // runs.  The per-tile counts stay valid between calls because only the tiles
 // the previous call touched are cleared first.  The bubble state is read with
 // __ldcg: it was written by other CTAs of the same launch.
+// With `cols` set (a batch), bubble b lives in column bubble_col[b], whose
+// tiles are numbered from cols[c].tile_base in the shared tile space.
 __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBins& sb,
-                                unsigned long long* keys, int* s_n) {
+                                unsigned long long* keys, int* s_n,
+                                const BatchColumn* cols = nullptr,
+                                const int* bubble_col = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int prev = min(max(__ldcg(sb.prev_n), 0), SMALL_MAX_PAIRS);
     for (int i = tid; i < prev; i += nt) {
@@ -453,20 +457,23 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
     }
     if (tid == 0) *s_n = 0;
     __syncthreads();
-    const int L[3] = {g.nx, g.ny, g.nz};
     const int T[3] = {TX, TY, TZ};
     for (int b = tid; b < B.nb; b += nt) {
         if (!__ldcg(B.spread + b)) continue;
+        const Geo& gb = cols ? cols[bubble_col[b]].g : g;
+        const int base = cols ? cols[bubble_col[b]].tile_base : 0;
+        const int L[3] = {gb.nx, gb.ny, gb.nz};
         int tl[3][MAX_AXIS_TILES];
         int ntl[3];
         const double n = __ldcg(B.n + b);
         for (int a = 0; a < 3; ++a)
-            ntl[a] = axis_tiles(__ldcg(B.x + 3 * b + a), n, L[a], !(g.walls & (1u << (2 * a))),
+            ntl[a] = axis_tiles(__ldcg(B.x + 3 * b + a), n, L[a], !(gb.walls & (1u << (2 * a))),
                                 T[a], tl[a]);
         for (int iz = 0; iz < ntl[2]; ++iz)
             for (int iy = 0; iy < ntl[1]; ++iy)
                 for (int ix = 0; ix < ntl[0]; ++ix) {
-                    const unsigned t = (unsigned)((tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix]);
+                    const unsigned t = (unsigned)(base + (tl[2][iz] * gb.nty + tl[1][iy]) * gb.ntx +
+                                                  tl[0][ix]);
                     const int k = atomicAdd(s_n, 1);
                     if (k < SMALL_MAX_PAIRS) keys[k] = ((unsigned long long)t << 32) | (unsigned)b;
                     else atomicOr(sb.overflow, 1);
@@ -560,6 +567,85 @@ cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const Colli
                                                           flag);
             break;
     }
+    return cudaGetLastError();
+}
+
+// Bubble update of a batch: bubble b moves in column bubble_col[b]; the
+// few-pair binning of all columns is fused behind it as for one column.
+template <int ST>
+__global__ void __launch_bounds__(BUBBLE_THREADS)
+k_bubbles_batch(const typename Store<ST>::T* __restrict__ f, const BatchColumn* __restrict__ cols,
+                const int* __restrict__ bubble_col, BubbleDev B, BubbleConst bc,
+                int* __restrict__ flag, SmallBins sb) {
+    __shared__ float red[3][BUBBLE_THREADS / 32];
+    __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
+    __shared__ int s_n, s_last;
+    const int b = blockIdx.x;
+    const BatchColumn& col = cols[bubble_col[b]];
+    bubble_update<ST>(f + col.pop_offset, col.g, col.cp, B, bc, flag, b, red);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(sb.done, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    bin_small_block(col.g, B, sb, keys, &s_n, cols, bubble_col);
+    if (threadIdx.x == 0) *sb.done = 0;
+}
+
+cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* cols,
+                                 const int* bubble_col, const BubbleDev& b, const BubbleConst& bc,
+                                 int* flag, const SmallBins& sb, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    switch (storage) {
+        case 0:
+            k_bubbles_batch<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, cols, bubble_col,
+                                                                b, bc, flag, sb);
+            break;
+        case 1:
+            k_bubbles_batch<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, cols, bubble_col,
+                                                                b, bc, flag, sb);
+            break;
+        default:
+            k_bubbles_batch<2><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, cols,
+                                                                bubble_col, b, bc, flag, sb);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+// Per-bubble closure constants for a batch: nu from each bubble's column.
+__global__ void k_bubble_constants_batch(BubbleDev B, BubbleConst bc, const double* col_nu,
+                                         const int* bubble_col) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nb) return;
+    BubbleConst c = bc;
+    c.nu = col_nu[bubble_col[b]];
+    const double d = B.d[b];
+    const double r = 0.5 * d;
+    const double vol = M_PI * d * d * d / 6.0;
+    const double eo = (c.rho_l - c.rho_b) * c.g * d * d / c.sigma;
+    BubbleK K;
+    K.inv_nf = (float)(1.0 / B.n[b]);
+    K.r = r;
+    K.kdt = (float)(c.dt_b / ((c.rho_b + c.c_am * c.rho_l) * vol));
+    K.fb = (float)((c.rho_l - c.rho_b) * vol * c.g);
+    K.drag_pref = (float)(0.5 * c.rho_l * M_PI * r * r * c.drag_scale);
+    K.fvm_coef_dt = (float)(c.c_am * c.rho_l * vol / c.dt_l);
+    K.visc_a0 = (float)(24.0 * c.nu / d);
+    K.visc_b = (float)(48.0 * c.nu / d);
+    K.re_per_speed = (float)(d / c.nu);
+    K.eo_term = (float)(8.0 / 3.0 * eo / (eo + 4.0));
+    B.k[b] = K;
+}
+
+cudaError_t launch_bubble_constants_batch(const BubbleDev& b, const BubbleConst& bc,
+                                          const double* col_nu, const int* bubble_col,
+                                          cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    k_bubble_constants_batch<<<(b.nb + 127) / 128, 128, 0, st>>>(b, bc, col_nu, bubble_col);
     return cudaGetLastError();
 }
 

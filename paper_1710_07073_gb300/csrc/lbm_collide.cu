@@ -449,17 +449,22 @@ __device__ __forceinline__ void collide_store_pair(typename Store<ST>::T* __rest
 #undef LBM_PAIR2
 }
 
+// One CTA's block of the sweep: x-pairs of 32 nodes, TY rows, PZ planes at
+// block coordinates (bx, by, bz).  `srec` is the CTA's staging of bubble
+// records; every thread of the CTA must call this with the same block.
 template <int ST>
-__global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
-k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
-                      typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
-                      const int* __restrict__ tile_start, const int* __restrict__ tile_count,
-                      const int* __restrict__ items, int cap,
-                      const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
-    __shared__ BubbleRec srec[PX * TY * PZ];
-    const int x0 = blockIdx.x * TX + 2 * threadIdx.x;
-    const int y = blockIdx.y * TY + threadIdx.y;
-    const int z = blockIdx.z * PZ + threadIdx.z;
+__device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restrict__ fin,
+                                            typename Store<ST>::T* __restrict__ fout,
+                                            const Geo& g, const CollideParams& cp,
+                                            const int* __restrict__ tile_start,
+                                            const int* __restrict__ tile_count,
+                                            const int* __restrict__ items, int cap,
+                                            const BubbleRec* __restrict__ recs, int nb,
+                                            int* __restrict__ flag, int bx, int by, int bz,
+                                            BubbleRec* srec) {
+    const int x0 = bx * TX + 2 * threadIdx.x;
+    const int y = by * TY + threadIdx.y;
+    const int z = bz * PZ + threadIdx.z;
     const bool active = (x0 < g.nx) && (y < g.ny) && (z < g.nz);
     // Inactive threads gather at a valid node and store nothing.
     const int xa = active ? x0 : 0;
@@ -468,7 +473,7 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
     float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
     bool forced = false;   // uniform over the CTA (one tile)
     if (tile_count != nullptr) {
-        const int t = (((blockIdx.z * PZ) / TZ) * g.nty + blockIdx.y) * g.ntx + blockIdx.x;
+        const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
         const int n_t = tile_count[t];
         if (n_t > 0) {
             forced = true;
@@ -489,6 +494,7 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                     for (int k = 0; k < cnt; ++k)
                         add_bubble_force_pair(srec[k], g, x0, y, z, Fx, Fy, Fz);
             }
+            __syncthreads();   // srec is reused by the CTA's next block
         }
     }
 
@@ -514,6 +520,100 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
     }
     if (forced) collide_store_pair<ST, true>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
     else collide_store_pair<ST, false>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
+k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
+                      typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
+                      const int* __restrict__ tile_start, const int* __restrict__ tile_count,
+                      const int* __restrict__ items, int cap,
+                      const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
+    __shared__ BubbleRec srec[PX * TY * PZ];
+    sweep_block<ST>(fin, fout, g, cp, tile_start, tile_count, items, cap, recs, nb, flag,
+                    blockIdx.x, blockIdx.y, blockIdx.z, srec);
+}
+
+// ---------------------------------------------------------------------------
+// Batched sweep: many independent columns in one persistent launch.  Each CTA
+// takes work items -- `depth` consecutive z-blocks of one (column, x-block,
+// y-block) -- from a global counter until all are done; columns keep their
+// own size, omega and walls.  Results do not depend on which CTA takes which
+// item.
+// ---------------------------------------------------------------------------
+constexpr int MAX_BATCH_COLUMNS = 256;
+
+template <int ST>
+__global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
+k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
+                typename Store<ST>::T* __restrict__ fout, const BatchColumn* __restrict__ cols,
+                int ncols, int total_items, int depth, int* __restrict__ work_counter,
+                const int* __restrict__ tile_start, const int* __restrict__ tile_count,
+                const int* __restrict__ items, int cap, const BubbleRec* __restrict__ recs,
+                int nb, int* __restrict__ flag) {
+    __shared__ BubbleRec srec[PX * TY * PZ];
+    __shared__ int s_item_base[MAX_BATCH_COLUMNS + 1];
+    __shared__ int s_item;
+    const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
+    for (int c = tid; c <= ncols; c += PX * TY * PZ)
+        s_item_base[c] = c < ncols ? cols[c].item_base : total_items;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(work_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total_items) break;
+        int lo = 0, hi = ncols - 1;   // column with item_base <= item < next base
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_item_base[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchColumn& col = cols[lo];
+        const int local = item - s_item_base[lo];
+        const int bx = local % col.g.ntx;
+        const int rest = local / col.g.ntx;
+        const int by = rest % col.g.nty;
+        const int bz0 = (rest / col.g.nty) * depth;
+        const int nbz = (col.g.nz + PZ - 1) / PZ;
+        for (int bz = bz0; bz < min(bz0 + depth, nbz); ++bz)
+            sweep_block<ST>(fin + col.pop_offset, fout + col.pop_offset, col.g, col.cp,
+                            tile_start + col.tile_base, tile_count + col.tile_base, items, cap,
+                            recs, nb, flag, bx, by, bz, srec);
+    }
+}
+
+cudaError_t launch_collide_batch(int storage, const void* fin, void* fout,
+                                 const BatchColumn* cols, int ncols, int total_items, int depth,
+                                 int grid, int* work_counter, const TileLists& tl,
+                                 const BubbleRec* recs, int nb, int* flag, cudaStream_t st) {
+    if (ncols > MAX_BATCH_COLUMNS) return cudaErrorInvalidValue;
+    dim3 block(PX, TY, PZ);
+    switch (storage) {
+        case 0:
+            k_collide_batch<0><<<grid, block, 0, st>>>((const float*)fin, (float*)fout, cols, ncols,
+                                                       total_items, depth, work_counter, tl.start,
+                                                       tl.count, tl.items, tl.cap, recs, nb, flag);
+            break;
+        case 1:
+            k_collide_batch<1><<<grid, block, 0, st>>>((const __half*)fin, (__half*)fout, cols,
+                                                       ncols, total_items, depth, work_counter,
+                                                       tl.start, tl.count, tl.items, tl.cap, recs,
+                                                       nb, flag);
+            break;
+        default:
+            k_collide_batch<2><<<grid, block, 0, st>>>(
+                (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, cols, ncols, total_items, depth,
+                work_counter, tl.start, tl.count, tl.items, tl.cap, recs, nb, flag);
+            break;
+    }
+    return cudaGetLastError();
+}
+
+int batch_block_threads() { return PX * TY * PZ; }
+int batch_z_block() { return PZ; }
+int pair_min_blocks(int storage) {
+    return storage == 0 ? PairOccupancy<0>::kMinBlocks : PairOccupancy<1>::kMinBlocks;
 }
 
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,

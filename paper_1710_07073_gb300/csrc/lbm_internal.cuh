@@ -146,6 +146,17 @@ struct SmallBins {
     int* done;         // [1] CTAs of the bubble update that have finished (0 between launches)
 };
 
+// One column of a batch: its geometry and relaxation, where its populations
+// start in the batch buffers (elements), and the first global tile and work
+// item that belong to it.
+struct BatchColumn {
+    Geo g;
+    CollideParams cp;
+    unsigned long long pop_offset;
+    int tile_base;
+    int item_base;
+};
+
 // ---- launchers (defined in the kernel translation units) -------------------
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
@@ -169,6 +180,19 @@ cudaError_t launch_set_equilibrium(int storage, const double* rho, const double*
                                    const Geo& g, const CollideParams& cp, cudaStream_t st);
 cudaError_t launch_totals(int storage, const void* f, const Geo& g, const CollideParams& cp,
                           double* partials, int npartials, double* out4, cudaStream_t st);
+cudaError_t launch_collide_batch(int storage, const void* fin, void* fout,
+                                 const BatchColumn* cols, int ncols, int total_items, int depth,
+                                 int grid, int* work_counter, const TileLists& tl,
+                                 const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
+cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* cols,
+                                 const int* bubble_col, const BubbleDev& b, const BubbleConst& bc,
+                                 int* flag, const SmallBins& sb, cudaStream_t st);
+cudaError_t launch_bubble_constants_batch(const BubbleDev& b, const BubbleConst& bc,
+                                          const double* col_nu, const int* bubble_col,
+                                          cudaStream_t st);
+int batch_block_threads();
+int batch_z_block();
+int pair_min_blocks(int storage);
 int totals_partials(const Geo& g);
 int scan_blocks(int T);
 

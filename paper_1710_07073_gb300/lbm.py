@@ -98,6 +98,22 @@ def lib():
         "lbm_set_kernel_timing": (i, [vp, i]),
         "lbm_get_kernel_time": (i, [vp, P(d), P(i)]),
         "lbm_launch_count": (ll, [vp]),
+        "lbm_batch_create": (i, [i, P(i), P(d), P(u), i, d, P(vp)]),
+        "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_set_stream": (i, [vp, vp]),
+        "lbm_batch_set_allocator": (i, [vp, ALLOC_FN, FREE_FN, vp]),
+        "lbm_batch_set_params": (i, [vp, P(lbm_params)]),
+        "lbm_batch_set_bubbles": (i, [vp, P(i), P(d), P(d), P(d)]),
+        "lbm_batch_step": (i, [vp, i]),
+        "lbm_batch_tune": (i, [vp, i, P(i), P(i)]),
+        "lbm_batch_get_fields": (i, [vp, i, P(d), P(d)]),
+        "lbm_batch_get_bubbles": (i, [vp, i, P(i), P(d), P(d), P(d), P(d), P(i)]),
+        "lbm_batch_sites": (ll, [vp]),
+        "lbm_batch_set_kernel_timing": (i, [vp, i]),
+        "lbm_batch_get_kernel_time": (i, [vp, P(d), P(i)]),
+        "lbm_batch_launch_count": (ll, [vp]),
+        "lbm_batch_sync": (i, [vp]),
+        "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
         "lbm_bin_bubbles_noalloc": (i, [i, i, i, u, i, vp, vp, vp, vp, vp, i, vp, vp]),
         "lbm_sync": (i, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
@@ -322,6 +338,137 @@ def lbm_last_error(ctx):
 
 def lbm_status_string(code):
     return lib().lbm_status_string(code).decode()
+
+
+# ---- batches ---------------------------------------------------------------------
+
+def _bcheck(b, code):
+    if code != LBM_OK:
+        raise LbmError(code, lib().lbm_batch_last_error(b).decode() if b else "")
+
+
+def lbm_batch_create(dims_list, omegas, walls=None, storage=LBM_STORE_F32, scale=1.0):
+    n = len(dims_list)
+    dims = np.ascontiguousarray(np.asarray(dims_list, dtype=np.int32).reshape(-1))
+    om = _f64(omegas, n)
+    w = None
+    if walls is not None:
+        w = np.ascontiguousarray(np.asarray(walls, dtype=np.uint32))
+    h = ctypes.c_void_p()
+    code = lib().lbm_batch_create(n, _iptr(dims), _dptr(om),
+                                  w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)) if w is not None
+                                  else None, storage, float(scale), ctypes.byref(h))
+    _bcheck(None, code)
+    return h
+
+
+def lbm_batch_destroy(b):
+    lib().lbm_batch_destroy(b)
+
+
+def lbm_batch_set_stream(b, stream_handle):
+    _bcheck(b, lib().lbm_batch_set_stream(b, ctypes.c_void_p(stream_handle)))
+
+
+def lbm_batch_set_allocator(b, alloc, free, user=None):
+    _bcheck(b, lib().lbm_batch_set_allocator(b, alloc, free, user))
+
+
+def lbm_batch_set_params(b, params):
+    _bcheck(b, lib().lbm_batch_set_params(b, ctypes.byref(params)))
+
+
+def lbm_batch_set_bubbles(b, counts, pos3, vel3, diam):
+    c = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
+    d = _f64(diam).reshape(-1)
+    p = _f64(pos3, 3 * d.size)
+    v = _f64(vel3, 3 * d.size) if vel3 is not None else None
+    _bcheck(b, lib().lbm_batch_set_bubbles(b, _iptr(c), _dptr(p), _dptr(v), _dptr(d)))
+
+
+def lbm_batch_step(b, nsteps=1):
+    _bcheck(b, lib().lbm_batch_step(b, int(nsteps)))
+
+
+def lbm_batch_tune(b, trial_steps=10):
+    depth = ctypes.c_int(0)
+    grid = ctypes.c_int(0)
+    _bcheck(b, lib().lbm_batch_tune(b, int(trial_steps), ctypes.byref(depth), ctypes.byref(grid)))
+    return depth.value, grid.value
+
+
+def lbm_batch_get_fields(b, col, sites, rho=True, u=True):
+    r = np.empty(sites, dtype=np.float64) if rho else None
+    v = np.empty(3 * sites, dtype=np.float64) if u else None
+    _bcheck(b, lib().lbm_batch_get_fields(b, int(col), _dptr(r), _dptr(v)))
+    return r, v
+
+
+def lbm_batch_get_bubbles(b):
+    n = ctypes.c_int(0)
+    _bcheck(b, lib().lbm_batch_get_bubbles(b, 0, ctypes.byref(n), None, None, None, None, None))
+    k = n.value
+    pos, vel, ul, psi = (np.empty(3 * k) for _ in range(4))
+    act = np.empty(k, dtype=np.int32)
+    if k:
+        _bcheck(b, lib().lbm_batch_get_bubbles(b, k, ctypes.byref(n), _dptr(pos), _dptr(vel),
+                                               _dptr(ul), _dptr(psi), _iptr(act)))
+    return {"pos": pos.reshape(k, 3), "vel": vel.reshape(k, 3), "ul": ul.reshape(k, 3),
+            "psi": psi.reshape(k, 3), "active": act.astype(bool)}
+
+
+def lbm_batch_sites(b):
+    return int(lib().lbm_batch_sites(b))
+
+
+def lbm_batch_set_kernel_timing(b, on=True):
+    _bcheck(b, lib().lbm_batch_set_kernel_timing(b, 1 if on else 0))
+
+
+def lbm_batch_get_kernel_time(b):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int(0)
+    _bcheck(b, lib().lbm_batch_get_kernel_time(b, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def lbm_batch_launch_count(b):
+    return int(lib().lbm_batch_launch_count(b))
+
+
+def lbm_batch_sync(b):
+    _bcheck(b, lib().lbm_batch_sync(b))
+
+
+def lbm_batch_last_error(b):
+    return lib().lbm_batch_last_error(b).decode()
+
+
+class Batch:
+    """Owning wrapper of a batch of independent columns."""
+
+    def __init__(self, dims_list, omegas, walls=None, storage=LBM_STORE_F32, scale=1.0,
+                 params=None):
+        self.dims = [tuple(int(v) for v in d) for d in dims_list]
+        self.h = lbm_batch_create(self.dims, omegas, walls, storage, scale)
+        if params is not None:
+            lbm_batch_set_params(self.h, params)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fields(self, col):
+        nx, ny, nz = self.dims[col]
+        rho, u = lbm_batch_get_fields(self.h, col, nx * ny * nz)
+        return rho.reshape(nz, ny, nx), u.reshape(3, nz, ny, nx)
 
 
 # ---- PyTorch plumbing ------------------------------------------------------------
