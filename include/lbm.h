@@ -201,6 +201,33 @@ int lbm_bytes_per_site(const lbm_ctx* ctx);
 int lbm_set_kernel_timing(lbm_ctx* ctx, int on);
 int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
 
+/* ---- Reverse mode: gradients of a terminal-velocity mismatch ----------------
+ * Objective: L = (ubar - target)^2, where ubar is the bubble rise velocity
+ * u_b,z averaged over all bubbles and over the last `window` of `nsteps`
+ * coupled steps (the terminal velocity of Sec. 4.1 / Table 4).
+ *
+ * lbm_adj_forward advances the context by nsteps steps exactly as lbm_step
+ * does, keeping a checkpoint of the full state every `checkpoint_every`
+ * steps, and returns L.  lbm_adj_backward then runs the hand-written adjoint
+ * of every step in reverse (each segment between checkpoints is recomputed
+ * forward first) and returns, scaled by dloss (= dOuter/dL):
+ *   grad_drag_scale  dL/ds_D, s_D the drag scale of lbm_params;
+ *   grad_diam        double[n] dL/dd_b per bubble (volume, mass, buoyancy,
+ *                    drag closure and the mapping window n = width_factor d_b);
+ *   grad_u0          double[3*S] SoA dL/du0, the initial liquid velocity, for
+ *                    initial populations f = f^eq(rho, u0) as lbm_set_fields
+ *                    sets them (NULL to skip).
+ * Wall contacts of the bubble (clamped centre) and the stop at the top are
+ * treated as fixed switches.  Needs FP32 storage, 1..64 bubbles.  After the
+ * backward the context is back at the state the forward ended in.  Any call
+ * that changes the state between the two (lbm_step, lbm_set_*) discards the
+ * record; lbm_adj_backward then returns LBM_ERR_STATE.  Memory: one state per
+ * checkpoint plus checkpoint_every states during the backward. */
+int lbm_adj_forward(lbm_ctx* ctx, int nsteps, int checkpoint_every, int window, double target,
+                    double* loss);
+int lbm_adj_backward(lbm_ctx* ctx, double dloss, double* grad_drag_scale, double* grad_diam,
+                     double* grad_u0);
+
 /* ---- Batches: many independent columns in one launch ---------------------
  * The grid-independence and stability studies of the paper (Sec. 4.2-4.3,
  * Tables 5-6, Fig. 5) run the same single-bubble problem on many columns of

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
-SOURCES = ("lbm_capi.cu", "lbm_collide.cu", "lbm_bubbles.cu", "lbm_noalloc.cu", "lbm_batch.cu")
+SOURCES = ("lbm_capi.cu", "lbm_collide.cu", "lbm_bubbles.cu", "lbm_noalloc.cu", "lbm_batch.cu", "lbm_adjoint.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(os.path.dirname(HERE), "include")]

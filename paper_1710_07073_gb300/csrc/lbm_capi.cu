@@ -14,50 +14,8 @@
 
 using namespace lbm;
 
-struct lbm_ctx {
-    int nx = 0, ny = 0, nz = 0;
-    unsigned walls = 0;
-    double omega = 1.0;
-    int storage = LBM_STORE_F32;
-    double scale = 1.0;
-    lbm_params p{};
-    cudaStream_t stream = nullptr;
-    lbm_alloc_fn af = nullptr;
-    lbm_free_fn ff = nullptr;
-    void* au = nullptr;
+#include "lbm_ctx.hpp"
 
-    bool dev_ready = false;
-    int device = 0;
-    void* f[2] = {nullptr, nullptr};
-    int cur = 0;
-    int* flag_d = nullptr;
-    int* flag_h = nullptr;       // pinned
-    bool unstable = false;
-
-    // bubbles
-    BubbleDev bub{};
-    int nb_cap = 0;
-    // bins: the large path (count, scan, fill, sort) or, for few pairs, the
-    // single-launch small path
-    Bins bins{};
-    SmallBins small{};
-    bool use_small = false;
-    bool bins_valid = false;
-
-    // timing of the collide-stream launches
-    bool timing = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
-    size_t events_used = 0;
-
-    long long launches = 0;      // kernels enqueued by this context
-
-    std::vector<std::pair<void*, size_t>> allocs;
-    std::string err;
-};
-
-namespace {
-
-int fail(lbm_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
 int fail(lbm_ctx* c, int code, const char* fmt, ...) {
     if (c) {
         char buf[512];
@@ -73,12 +31,6 @@ int fail(lbm_ctx* c, int code, const char* fmt, ...) {
 int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
     return fail(c, LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
-
-#define LBM_CUDA(call, what)                                 \
-    do {                                                     \
-        cudaError_t e_ = (call);                             \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
-    } while (0)
 
 void* dalloc(lbm_ctx* c, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -179,6 +131,8 @@ int ensure_device(lbm_ctx* c) {
     return LBM_OK;
 }
 
+namespace {
+
 int check_walls(unsigned walls) {
     if (walls & ~0x3Fu) return 0;
     for (int a = 0; a < 3; ++a) {
@@ -210,6 +164,67 @@ void free_bubbles(lbm_ctx* c) {
 }
 
 }  // namespace
+
+int enqueue_one_step(lbm_ctx* c) {
+    const Geo g = geo_of(c);
+    const CollideParams cp = collide_params(c);
+    const bool bubbles = c->bub.nb > 0;
+    const bool two_way = bubbles && c->p.two_way;
+    if (bubbles) {
+        LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c), c->flag_d,
+                                c->use_small ? &c->small : nullptr, c->stream),
+                 "bubble update");
+        if (c->use_small) {
+            c->launches += 1;   // binning fused into the bubble update
+        } else {
+            LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
+            c->launches += 1 + BINNING_LAUNCHES;
+        }
+        c->bins_valid = true;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->timing) {
+        if (c->events_used == c->events.size()) {
+            cudaEvent_t a, b;
+            LBM_CUDA(cudaEventCreate(&a), "event");
+            LBM_CUDA(cudaEventCreate(&b), "event");
+            c->events.emplace_back(a, b);
+        }
+        e0 = c->events[c->events_used].first;
+        e1 = c->events[c->events_used].second;
+        ++c->events_used;
+        LBM_CUDA(cudaEventRecord(e0, c->stream), "event record");
+    }
+    TileLists tl{};
+    if (c->use_small) tl = TileLists{c->small.start, c->small.count, c->small.items, SMALL_MAX_PAIRS};
+    else tl = TileLists{c->bins.off, c->bins.cnt, c->bins.items, c->bins.cap};
+    LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
+                                   two_way ? &tl : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
+                                   c->stream),
+             "collide-stream");
+    if (c->timing) LBM_CUDA(cudaEventRecord(e1, c->stream), "event record");
+    c->launches += 1;
+    c->cur ^= 1;
+    return LBM_OK;
+}
+
+// Wait for the enqueued steps and report the instability flag / overflow.
+int finish_steps(lbm_ctx* c) {
+    LBM_CUDA(cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int), cudaMemcpyDeviceToHost,
+                             c->stream), "read flag");
+    LBM_CUDA(cudaStreamSynchronize(c->stream), "step");
+    if (*c->flag_h) {
+        c->unstable = true;
+        return fail(c, LBM_ERR_UNSTABLE, "non-finite value or |u| >= 0.3 in the liquid");
+    }
+    if (c->bins_valid) {
+        int ov = 0;
+        LBM_CUDA(cudaMemcpy(&ov, c->use_small ? c->small.overflow : c->bins.overflow, sizeof(int),
+                            cudaMemcpyDeviceToHost), "overflow");
+        if (ov) return fail(c, LBM_ERR_STATE, "tile list capacity exceeded");
+    }
+    return LBM_OK;
+}
 
 extern "C" {
 
@@ -269,6 +284,7 @@ int lbm_create(int nx, int ny, int nz, double omega, unsigned walls, lbm_ctx** o
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     if (c->dev_ready) cudaStreamSynchronize(c->stream);
+    adjoint_free(c);
     for (auto& e : c->events) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -314,6 +330,7 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
         if (p->width_factor != c->p.width_factor)
             return fail(c, LBM_ERR_STATE, "set width_factor before lbm_set_bubbles");
     }
+    adjoint_free(c);
     c->p = *p;
     if (c->bub.nb > 0)
         LBM_CUDA(launch_bubble_constants(c->bub, bubble_const(c), c->stream), "bubble constants");
@@ -328,6 +345,7 @@ int lbm_get_params(const lbm_ctx* c, lbm_params* p) {
 
 int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u3) {
     if (!c) return LBM_ERR_ARG;
+    adjoint_free(c);
     int rc = ensure_device(c);
     if (rc) return rc;
     const Geo g = geo_of(c);
@@ -362,6 +380,7 @@ int lbm_set_fields(lbm_ctx* c, const double* rho, const double* u3) {
 
 int lbm_set_populations(lbm_ctx* c, const double* f) {
     if (!c || !f) return LBM_ERR_ARG;
+    adjoint_free(c);
     int rc = ensure_device(c);
     if (rc) return rc;
     const Geo g = geo_of(c);
@@ -427,6 +446,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     }
     int rc = ensure_device(c);
     if (rc) return rc;
+    adjoint_free(c);
     LBM_CUDA(cudaStreamSynchronize(c->stream), "sync before bubble reset");
     free_bubbles(c);
     c->bins_valid = false;
@@ -516,65 +536,15 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
 
 int lbm_step(lbm_ctx* c, int nsteps) {
     if (!c || nsteps < 0) return LBM_ERR_ARG;
+    adjoint_free(c);
     int rc = ensure_device(c);
     if (rc) return rc;
     if (c->unstable) return fail(c, LBM_ERR_UNSTABLE, "liquid solver is unstable (sticky)");
-    const Geo g = geo_of(c);
-    const CollideParams cp = collide_params(c);
-    const BubbleConst bc = bubble_const(c);
-    const bool bubbles = c->bub.nb > 0;
-    const bool two_way = bubbles && c->p.two_way;
     for (int s = 0; s < nsteps; ++s) {
-        if (bubbles) {
-            LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bc, c->flag_d,
-                                    c->use_small ? &c->small : nullptr, c->stream),
-                     "bubble update");
-            if (c->use_small) {
-                c->launches += 1;   // binning fused into the bubble update
-            } else {
-                LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
-                c->launches += 1 + BINNING_LAUNCHES;
-            }
-            c->bins_valid = true;
-        }
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (c->timing) {
-            if (c->events_used == c->events.size()) {
-                cudaEvent_t a, b;
-                LBM_CUDA(cudaEventCreate(&a), "event");
-                LBM_CUDA(cudaEventCreate(&b), "event");
-                c->events.emplace_back(a, b);
-            }
-            e0 = c->events[c->events_used].first;
-            e1 = c->events[c->events_used].second;
-            ++c->events_used;
-            LBM_CUDA(cudaEventRecord(e0, c->stream), "event record");
-        }
-        TileLists tl{};
-        if (c->use_small) tl = TileLists{c->small.start, c->small.count, c->small.items, SMALL_MAX_PAIRS};
-        else tl = TileLists{c->bins.off, c->bins.cnt, c->bins.items, c->bins.cap};
-        LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
-                                       two_way ? &tl : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
-                                       c->stream),
-                 "collide-stream");
-        if (c->timing) LBM_CUDA(cudaEventRecord(e1, c->stream), "event record");
-        c->launches += 1;
-        c->cur ^= 1;
+        rc = enqueue_one_step(c);
+        if (rc) return rc;
     }
-    LBM_CUDA(cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int), cudaMemcpyDeviceToHost,
-                             c->stream), "read flag");
-    LBM_CUDA(cudaStreamSynchronize(c->stream), "step");
-    if (*c->flag_h) {
-        c->unstable = true;
-        return fail(c, LBM_ERR_UNSTABLE, "non-finite value or |u| >= 0.3 in the liquid");
-    }
-    if (c->bins_valid) {
-        int ov = 0;
-        LBM_CUDA(cudaMemcpy(&ov, c->use_small ? c->small.overflow : c->bins.overflow, sizeof(int),
-                            cudaMemcpyDeviceToHost), "overflow");
-        if (ov) return fail(c, LBM_ERR_STATE, "tile list capacity exceeded");
-    }
-    return LBM_OK;
+    return finish_steps(c);
 }
 
 int lbm_get_fields(lbm_ctx* c, double* rho, double* u3) {

@@ -1,0 +1,80 @@
+// Host-side definition of the context shared by the C-ABI translation units
+// (lbm_capi.cu, lbm_adjoint.cu).  Not part of the public interface.
+#pragma once
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+struct AdjointTape;   // lbm_adjoint.cu
+
+using lbm::Bins;
+using lbm::BubbleDev;
+using lbm::SmallBins;
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    unsigned walls = 0;
+    double omega = 1.0;
+    int storage = LBM_STORE_F32;
+    double scale = 1.0;
+    lbm_params p{};
+    cudaStream_t stream = nullptr;
+    lbm_alloc_fn af = nullptr;
+    lbm_free_fn ff = nullptr;
+    void* au = nullptr;
+
+    bool dev_ready = false;
+    int device = 0;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    int* flag_d = nullptr;
+    int* flag_h = nullptr;       // pinned
+    bool unstable = false;
+
+    // bubbles
+    BubbleDev bub{};
+    int nb_cap = 0;
+    // bins: the large path (count, scan, fill, sort) or, for few pairs, the
+    // single-launch small path
+    Bins bins{};
+    SmallBins small{};
+    bool use_small = false;
+    bool bins_valid = false;
+
+    // timing of the collide-stream launches
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    size_t events_used = 0;
+
+    long long launches = 0;      // kernels enqueued by this context
+
+    AdjointTape* adj = nullptr;   // forward record of lbm_adj_forward
+
+    std::vector<std::pair<void*, size_t>> allocs;
+    std::string err;
+};
+
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what);
+void* dalloc(lbm_ctx* c, size_t bytes);
+void dfree(lbm_ctx* c, void* p);
+size_t elem_size(int storage);
+lbm::Geo geo_of(const lbm_ctx* c);
+lbm::CollideParams collide_params(const lbm_ctx* c);
+lbm::BubbleConst bubble_const(const lbm_ctx* c);
+int ensure_device(lbm_ctx* c);
+// One coupled step on the context stream (the body of lbm_step's loop).
+int enqueue_one_step(lbm_ctx* c);
+int finish_steps(lbm_ctx* c);
+void adjoint_free(lbm_ctx* c);
+
+#define LBM_CUDA(call, what)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)

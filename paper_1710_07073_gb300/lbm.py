@@ -98,6 +98,8 @@ def lib():
         "lbm_set_kernel_timing": (i, [vp, i]),
         "lbm_get_kernel_time": (i, [vp, P(d), P(i)]),
         "lbm_launch_count": (ll, [vp]),
+        "lbm_adj_forward": (i, [vp, i, i, i, d, P(d)]),
+        "lbm_adj_backward": (i, [vp, d, P(d), P(d), P(d)]),
         "lbm_batch_create": (i, [i, P(i), P(d), P(u), i, d, P(vp)]),
         "lbm_batch_destroy": (None, [vp]),
         "lbm_batch_set_stream": (i, [vp, vp]),
@@ -306,6 +308,26 @@ def lbm_get_kernel_time(ctx):
     n = ctypes.c_int(0)
     _check(ctx, lib().lbm_get_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def lbm_adj_forward(ctx, nsteps, checkpoint_every, window, target):
+    """Forward record of nsteps steps; returns L = (ubar - target)^2."""
+    loss = ctypes.c_double(0.0)
+    _check(ctx, lib().lbm_adj_forward(ctx, int(nsteps), int(checkpoint_every), int(window),
+                                      float(target), ctypes.byref(loss)))
+    return loss.value
+
+
+def lbm_adj_backward(ctx, dloss=1.0, want_u0=True):
+    """Adjoint sweep: (dL/ds_D, dL/dd_b[n], dL/du0[3S] or None), scaled by dloss."""
+    n = ctypes.c_int(0)
+    _check(ctx, lib().lbm_get_bubbles(ctx, 0, ctypes.byref(n), None, None, None, None, None))
+    g_sd = ctypes.c_double(0.0)
+    g_d = np.zeros(n.value)
+    g_u0 = np.zeros(3 * lbm_sites(ctx)) if want_u0 else None
+    _check(ctx, lib().lbm_adj_backward(ctx, float(dloss), ctypes.byref(g_sd), _dptr(g_d),
+                                       _dptr(g_u0)))
+    return g_sd.value, g_d, g_u0
 
 
 LBM_NOALLOC_MAX_TILES = 262144
