@@ -308,6 +308,74 @@ def run_batch(args, wl):
     return 0
 
 
+def run_adjoint(args):
+    """Adjoint of 1000 coupled steps of a 128x128x256 column (checkpoint every 50),
+    gradients of the terminal-velocity mismatch, checked by central differences."""
+    import torch
+    from paper_1710_07073_gb300 import lbm, workloads as wlm
+    from paper_1710_07073_gb300.adjoint import TerminalVelocityProblem
+
+    torch.cuda.set_device(0)
+    lbm.lib()
+    dims = (128, 128, 256)
+    prob = TerminalVelocityProblem(dims=dims, omega=1.6, positions=np.array([[64.0, 64.0, 32.0]]),
+                                   steps=1000, checkpoint_every=50, window=200, target=8e-5,
+                                   g=1e-5)
+    P = wlm.gaussian_velocity_perturbation(dims, seed=4, amp=1e-4)
+    S = int(np.prod(dims))
+
+    def loss_only(sd, d, eps):
+        col = prob.column(sd, d, eps * P)
+        loss = lbm.lbm_adj_forward(col.ctx, prob.steps, prob.checkpoint_every, prob.window,
+                                   prob.target)
+        col.close()
+        return loss
+
+    col = prob.column(1.0, 2.5, P)
+    lbm.lbm_adj_forward(col.ctx, 50, 50, 10, prob.target)   # warm-up
+    lbm.lbm_adj_backward(col.ctx, 1.0, want_u0=False)
+    col.close()
+    col = prob.column(1.0, 2.5, P)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = lbm.lbm_adj_forward(col.ctx, prob.steps, prob.checkpoint_every, prob.window, prob.target)
+    t1 = time.perf_counter()
+    lbm.lbm_set_kernel_timing(col.ctx, True)
+    g_sd, g_d, g_u0 = lbm.lbm_adj_backward(col.ctx, 1.0, want_u0=True)
+    t2 = time.perf_counter()
+    k_ms, k_n = lbm.lbm_get_kernel_time(col.ctx)
+    col.close()
+    g_e = float((g_u0 * P.reshape(-1)).sum())
+    h, he = 1e-3, 0.05
+    fd_sd = (loss_only(1.0 + h, 2.5, 1.0) - loss_only(1.0 - h, 2.5, 1.0)) / (2 * h)
+    fd_d = (loss_only(1.0, 2.5 + h, 1.0) - loss_only(1.0, 2.5 - h, 1.0)) / (2 * h)
+    fd_e = (loss_only(1.0, 2.5, 1.0 + he) - loss_only(1.0, 2.5, 1.0 - he)) / (2 * he)
+    fwd_s, bwd_s = t1 - t0, t2 - t1
+    value = S * prob.steps / (fwd_s + bwd_s) / 1e6
+    achieved = 3 * 19 * 4 * S / (k_ms / max(1, k_n) * 1e-3) / 1e9
+    peak, peak_kind = measured_peak()
+    line = {
+        "metric": "adjoint of the coupled step: forward + reverse MLUPS", "value": round(value, 2),
+        "unit": "MLUPS", "n_gpus": 1, "steps": prob.steps, "warmup": 1,
+        "ms_per_step": round((fwd_s + bwd_s) * 1e3 / prob.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint: 128x128x256 column, omega 1.6, d 2.5, 1000 steps, "
+                               "checkpoint every 50, loss over the last 200 steps",
+                   "forward_s": round(fwd_s, 4), "backward_s": round(bwd_s, 4), "loss": loss},
+        "gradients": {"drag_scale": [g_sd, fd_sd, abs(g_sd / fd_sd - 1)],
+                      "diameter": [float(g_d[0]), fd_d, abs(g_d[0] / fd_d - 1)],
+                      "u0_direction": [g_e, fd_e, abs(g_e / fd_e - 1)],
+                      "format": "[adjoint, central FD of the FP32 forward, relative difference]"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_adj_liquid",
+                     "algorithmic_bytes_per_launch": 3 * 19 * 4 * S,
+                     "avg_launch_ms": round(k_ms / max(1, k_n), 5), "launches": k_n,
+                     "peak_kind": peak_kind},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args, wl):
     import torch
     from paper_1710_07073_gb300 import lbm
@@ -450,7 +518,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("gb300", "reference"), default="gb300")
-    ap.add_argument("--workload", choices=("single_large", "swarm", "batch"), default="single_large")
+    ap.add_argument("--workload", choices=("single_large", "swarm", "batch", "adjoint"),
+                    default="single_large")
     ap.add_argument("--storage", choices=tuple(STORAGES), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dims", default=None,
@@ -458,6 +527,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     wl = workload(args.workload)
     if args.dims:
         from paper_1710_07073_gb300 import workloads as wlm

@@ -222,7 +222,9 @@ int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
  * backward the context is back at the state the forward ended in.  Any call
  * that changes the state between the two (lbm_step, lbm_set_*) discards the
  * record; lbm_adj_backward then returns LBM_ERR_STATE.  Memory: one state per
- * checkpoint plus checkpoint_every states during the backward. */
+ * checkpoint plus checkpoint_every states during the backward.  With kernel
+ * timing on (lbm_set_kernel_timing), lbm_adj_backward times each launch of
+ * the per-node adjoint sweep instead of the forward collide-stream. */
 int lbm_adj_forward(lbm_ctx* ctx, int nsteps, int checkpoint_every, int window, double target,
                     double* loss);
 int lbm_adj_backward(lbm_ctx* ctx, double dloss, double* grad_drag_scale, double* grad_diam,

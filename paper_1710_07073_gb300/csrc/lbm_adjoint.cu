@@ -653,6 +653,9 @@ extern "C" int lbm_adj_forward(lbm_ctx* c, int nsteps, int checkpoint_every, int
         return LBM_ERR_ARG;
     int rc = ensure_device(c);
     if (rc) return rc;
+    const bool timing = c->timing;   // forward launches are not timed
+    c->timing = false;
+    struct Restore { lbm_ctx* c; bool t; ~Restore() { c->timing = t; } } restore_timing{c, timing};
     if (c->storage != LBM_STORE_F32)
         return fail(c, LBM_ERR_STATE, "the adjoint needs FP32 population storage");
     const int nb = c->bub.nb;
@@ -800,7 +803,20 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
             const float* fn = (const float*)seg_f[n - n0];
             const BubbleSnap* pre = seg_pre + (size_t)(n - n0) * nb;
             const BubbleSnap* post = seg_post + (size_t)(n - n0) * nb;
+            cudaEvent_t e1 = nullptr;
+            if (c->timing) {
+                if (c->events_used == c->events.size()) {
+                    cudaEvent_t ea, eb;
+                    step_rc(cudaEventCreate(&ea), "event");
+                    step_rc(cudaEventCreate(&eb), "event");
+                    c->events.emplace_back(ea, eb);
+                }
+                step_rc(cudaEventRecord(c->events[c->events_used].first, s), "event");
+                e1 = c->events[c->events_used].second;
+                ++c->events_used;
+            }
             k_adj_liquid<<<blocks, 128, 0, s>>>(fn, lam[lc], lam[lc ^ 1], g, cp, post, nb, ac.two_way);
+            if (e1) step_rc(cudaEventRecord(e1, s), "event");
             const double ls = n >= N - t->window ? seed : 0.0;
             k_adj_bubbles<<<1, ADJ_THREADS, 0, s>>>(fn, lam[lc], lam[lc ^ 1], g, cp, pre, post, c->bub.d,
                                                      nb, ac, adj, grads, grads + 1, ls);
