@@ -160,6 +160,22 @@ class ClockSampler:
                 "samples": len(mhz), "window": window}
 
 
+def max_over_ranks(value, world, device=None):
+    """Largest value over the ranks of the job (the slowest rank's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(world, sites_per_rank, steps, ms_max):
+    """Whole-job throughput: all ranks' site updates over the slowest rank's time."""
+    return world * sites_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -272,15 +288,12 @@ def run_batch(args, wl):
     k_ms, k_n = lbm.lbm_batch_get_kernel_time(b.h)
     lbm.lbm_batch_set_kernel_timing(b.h, False)
     b.close()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, "cuda")
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
-    value = world * S * args.steps / (ms * 1e-3) / 1e6
+    value = aggregate_mlups(world, S, args.steps, ms)
     bytes_per_site = 2 * 19 * (4 if storage == "f32" else 2)
     avg_kernel_s = (k_ms / max(1, k_n)) * 1e-3
     achieved = bytes_per_site * S / avg_kernel_s / 1e9
@@ -428,11 +441,8 @@ def run_gpu(args, wl):
         time.sleep(0.2 if sampler.proc else 0.0)
         clocks = sampler.stop()
 
-        if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * S * args.steps / (ms * 1e-3) / 1e6
+        ms = max_over_ranks(ms, world, "cuda")
+        value = aggregate_mlups(world, S, args.steps, ms)
 
         # End to end through the public API with host buffers: upload the
         # initial fields and bubbles from pinned memory, step, read the bubbles
@@ -459,11 +469,8 @@ def run_gpu(args, wl):
         lbm.lbm_get_fields(ctx, out_rho=rho_o, out_u=u_o)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e_value = world * S * args.steps / e2e_s / 1e6
+        e2e_s = max_over_ranks(e2e_s, world, "cuda")
+        e2e_value = aggregate_mlups(world, S, args.steps, e2e_s * 1e3)
         h2d = (4 * 8 * S + 7 * 8 * nb) / args.steps
         d2h = (4 * 8 * S) / args.steps + (12 * 8 + 4) * nb
         col.close()

@@ -773,6 +773,10 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     ac.substeps = c->p.substeps;
     ac.two_way = c->p.two_way;
     const double seed = dloss * 2.0 * (t->ubar - t->target) / ((double)t->window * nb);
+    // Kernel timing covers the adjoint sweep only, not the recomputed forward.
+    const bool time_adjoint = c->timing;
+    c->timing = false;
+    struct Restore { lbm_ctx* c; bool t; ~Restore() { c->timing = t; } } restore_timing{c, time_adjoint};
     int lc = 0;   // lam[lc] holds Lambda^{n+1}
     int rc = LBM_OK;
     auto step_rc = [&](cudaError_t e, const char* what) {
@@ -804,7 +808,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
             const BubbleSnap* pre = seg_pre + (size_t)(n - n0) * nb;
             const BubbleSnap* post = seg_post + (size_t)(n - n0) * nb;
             cudaEvent_t e1 = nullptr;
-            if (c->timing) {
+            if (time_adjoint) {
                 if (c->events_used == c->events.size()) {
                     cudaEvent_t ea, eb;
                     step_rc(cudaEventCreate(&ea), "event");
