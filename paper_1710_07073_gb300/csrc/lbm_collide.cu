@@ -638,21 +638,23 @@ int pair_min_blocks(int storage) {
 // ---------------------------------------------------------------------------
 // TMA-staged sweep for 16-bit storage (nx a multiple of 8).
 //
-// Persistent CTAs walk the 32 x 4 x 4 tiles (one binning tile each).  For a
-// tile, one thread issues 19 bulk tensor copies -- one box per plane j, the
-// tile shifted by -c_j -- into a shared-memory stage and the CTA computes from
-// shared memory while the next tile's boxes are in flight (two stages, one
-// mbarrier each).  A TMA box must start on a 16-byte boundary in x, so planes
+// Persistent CTAs walk tiles of 128 x 4 x 1 nodes.  For a tile, one thread
+// issues 19 bulk tensor copies -- one box per plane j, the tile shifted by
+// -c_j -- into a shared-memory stage and the CTA computes from shared memory
+// while the next tile's boxes are in flight (two stages, one mbarrier each).  A TMA box must start on a 16-byte boundary in x, so planes
 // that cross x are fetched 48 wide starting 8 nodes to the left.  Boxes that
 // reach outside the box domain come back zero-filled; nodes on the domain
 // faces therefore take their populations from the general pull instead.
 // Waits on an mbarrier are bounded: on timeout the kernel sets bit 4 of the
 // status flag, waits (bounded) for the copies it issued, and stops.
 // ---------------------------------------------------------------------------
-constexpr int TMA_THREADS = PX * TY * TZ;          // 16 x 4 x 4: one x-pair per thread
-constexpr int TMA_NARROW = TX;                      // box width of planes with c_x = 0
-constexpr int TMA_WIDE = TX + 16;                   // box width of planes crossing x
-constexpr int TMA_ROW_NODES = TY * TZ;
+// A TMA tile is TMA_BX x TY x 1 nodes (4 binning tiles along x): boxes of
+// TY rows of 256-288 bytes keep the number of row requests per node low.
+constexpr int TMA_BX = 4 * TX;                     // 128 nodes along x
+constexpr int TMA_THREADS = (TMA_BX / 2) * TY;     // one x-pair per thread: 64 x 4
+constexpr int TMA_NARROW = TMA_BX;                 // box width of planes with c_x = 0
+constexpr int TMA_WIDE = TMA_BX + 16;              // box width of planes crossing x
+constexpr int TMA_ROW_NODES = TY;
 constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;       // ~0.1-1 s of polling
 
 __host__ __device__ constexpr int tma_width(int j) { return cx(j) == 0 ? TMA_NARROW : TMA_WIDE; }
@@ -664,8 +666,8 @@ constexpr int TMA_STAGE_BYTES = TMA_STAGE_ELEMS * 2;
 static_assert(TMA_STAGE_BYTES % 128 == 0, "stages stay 128-byte aligned");
 
 struct TmaMaps {
-    CUtensorMap narrow;   // box TMA_NARROW x TY x TZ x 1
-    CUtensorMap wide;     // box TMA_WIDE x TY x TZ x 1
+    CUtensorMap narrow;   // box TMA_NARROW x TY x 1 x 1
+    CUtensorMap wide;     // box TMA_WIDE x TY x 1 x 1
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
@@ -710,11 +712,11 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map
         : "memory");
 }
 
-// Issue the 19 boxes of tile (bx, by, bz) into one stage (thread 0 only).
+// Issue the 19 boxes of TMA tile (bx, by, z) into one stage (thread 0 only).
 __device__ __forceinline__ void tma_issue_tile(const TmaMaps& maps, unsigned stage, unsigned bar,
                                                int bx, int by, int bz) {
     mbar_expect_tx(bar, (unsigned)TMA_STAGE_BYTES);
-    const int x0 = bx * TX, y0 = by * TY, z0 = bz * TZ;
+    const int x0 = bx * TMA_BX, y0 = by * TY, z0 = bz;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         const CUtensorMap* map = cx(j) == 0 ? &maps.narrow : &maps.wide;
@@ -726,10 +728,9 @@ __device__ __forceinline__ void tma_issue_tile(const TmaMaps& maps, unsigned sta
 
 // Raw values of direction J for the pair (x0 + 2 tx, +1) from a stage.
 template <int ST, int J>
-__device__ __forceinline__ float2 stage_pair(const typename Store<ST>::T* st, int tx, int ty,
-                                             int tz) {
+__device__ __forceinline__ float2 stage_pair(const typename Store<ST>::T* st, int tx, int ty) {
     using T = typename Store<ST>::T;
-    const T* row = st + tma_plane_offset(J) + (tz * TY + ty) * tma_width(J);
+    const T* row = st + tma_plane_offset(J) + ty * tma_width(J);
     auto h2 = [&](int e) {
         return Vec2<ST>::load_shared(row + e);
     };
@@ -754,12 +755,11 @@ k_collide_stream_tma(const __grid_constant__ TmaMaps maps,
     extern __shared__ __align__(1024) unsigned char smem[];
     T* stages = reinterpret_cast<T*>(smem);                        // 2 stages
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + 2 * TMA_STAGE_BYTES);
-    BubbleRec* srec = reinterpret_cast<BubbleRec*>(smem + 2 * TMA_STAGE_BYTES + 16);
-    int& s_abort = *reinterpret_cast<int*>(smem + 2 * TMA_STAGE_BYTES + 16 +
-                                           sizeof(BubbleRec) * TMA_THREADS);
+    int& s_abort = *reinterpret_cast<int*>(smem + 2 * TMA_STAGE_BYTES + 16);
     const int tid = threadIdx.x;
-    const int tx = tid % PX, ty = (tid / PX) % TY, tz = tid / (PX * TY);
-    const int ntiles = g.ntx * g.nty * g.ntz;
+    const int tx = tid % (TMA_BX / 2), ty = tid / (TMA_BX / 2);
+    const int nbx = (g.nx + TMA_BX - 1) / TMA_BX;
+    const int ntiles = nbx * g.nty * g.nz;
     const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
     const unsigned stage0 = smem_addr(stages), stage1 = stage0 + TMA_STAGE_BYTES;
     if (tid == 0) {
@@ -771,15 +771,15 @@ k_collide_stream_tma(const __grid_constant__ TmaMaps maps,
     __syncthreads();
     int t = blockIdx.x;
     if (tid == 0 && t < ntiles)
-        tma_issue_tile(maps, stage0, bar0, t % g.ntx, (t / g.ntx) % g.nty, t / (g.ntx * g.nty));
+        tma_issue_tile(maps, stage0, bar0, t % nbx, (t / nbx) % g.nty, t / (nbx * g.nty));
     int issued = t < ntiles ? 1 : 0, waited = 0;
     for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
         const int s = i & 1;
-        const int bx = t % g.ntx, by = (t / g.ntx) % g.nty, bz = t / (g.ntx * g.nty);
+        const int bx = t % nbx, by = (t / nbx) % g.nty, z = t / (nbx * g.nty);
         const int tn = t + gridDim.x;
         if (tid == 0 && tn < ntiles) {
-            tma_issue_tile(maps, s ? stage0 : stage1, s ? bar0 : bar1, tn % g.ntx,
-                           (tn / g.ntx) % g.nty, tn / (g.ntx * g.nty));
+            tma_issue_tile(maps, s ? stage0 : stage1, s ? bar0 : bar1, tn % nbx,
+                           (tn / nbx) % g.nty, tn / (nbx * g.nty));
             ++issued;
         }
         // Bounded wait for this tile's boxes.
@@ -792,32 +792,25 @@ k_collide_stream_tma(const __grid_constant__ TmaMaps maps,
         ++waited;
         const T* st = stages + (s ? TMA_STAGE_ELEMS : 0);
 
-        const int x0 = bx * TX + 2 * tx, y = by * TY + ty, z = bz * TZ + tz;
-        const bool active = (x0 < g.nx) && (y < g.ny) && (z < g.nz);
-        float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
-        bool forced = false;
-        if (tile_count != nullptr) {
-            const int n_t = tile_count[t];
-            if (n_t > 0) {
-                forced = true;
-                const int beg = tile_start[t];
-                const int end = min(beg + n_t, cap);
-                for (int c0 = beg; c0 < end; c0 += TMA_THREADS) {
-                    const int cnt = min(TMA_THREADS, end - c0);
-                    __syncthreads();
-                    if (tid < cnt) {
-                        const int id = items[c0 + tid];
-                        if (id >= 0 && id < nb) srec[tid] = recs[id];
-                        else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int x0 = bx * TMA_BX + 2 * tx, y = by * TY + ty;
+        const bool active = (x0 < g.nx) && (y < g.ny);
+        if (active) {
+            // Force from the bubbles binned to this node pair's tile (Eq. 21).
+            float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
+            bool forced = false;
+            if (tile_count != nullptr) {
+                const int bt = ((z / TZ) * g.nty + by) * g.ntx + x0 / TX;
+                const int n_t = tile_count[bt];
+                if (n_t > 0) {
+                    forced = true;
+                    const int beg = tile_start[bt];
+                    const int end = min(beg + n_t, cap);
+                    for (int k = beg; k < end; ++k) {
+                        const int id = items[k];
+                        if (id >= 0 && id < nb) add_bubble_force_pair(recs[id], g, x0, y, z, Fx, Fy, Fz);
                     }
-                    __syncthreads();
-                    if (active)
-                        for (int k = 0; k < cnt; ++k)
-                            add_bubble_force_pair(srec[k], g, x0, y, z, Fx, Fy, Fz);
                 }
             }
-        }
-        if (active) {
             const unsigned S = (unsigned)g.S;
             const unsigned site0 = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx +
                                    (unsigned)x0;
@@ -825,7 +818,7 @@ k_collide_stream_tma(const __grid_constant__ TmaMaps maps,
             const bool face = x0 == 0 || x0 + 2 >= g.nx || y == 0 || y == g.ny - 1 || z == 0 ||
                               z == g.nz - 1;
             if (!face) {
-#define LBM_SP(J) rv[J] = stage_pair<ST, J>(st, tx, ty, tz)
+#define LBM_SP(J) rv[J] = stage_pair<ST, J>(st, tx, ty)
                 LBM_SP(0); LBM_SP(1); LBM_SP(2); LBM_SP(3); LBM_SP(4);
                 LBM_SP(5); LBM_SP(6); LBM_SP(7); LBM_SP(8); LBM_SP(9);
                 LBM_SP(10); LBM_SP(11); LBM_SP(12); LBM_SP(13); LBM_SP(14);
@@ -888,8 +881,8 @@ static bool make_tma_maps(const void* f, const Geo& g, TmaMaps& maps) {
     const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 2, (cuuint64_t)g.nx * g.ny * 2,
                                    (cuuint64_t)g.S * 2};
     const cuuint32_t elem[4] = {1, 1, 1, 1};
-    const cuuint32_t box_n[4] = {TMA_NARROW, TY, TZ, 1};
-    const cuuint32_t box_w[4] = {TMA_WIDE, TY, TZ, 1};
+    const cuuint32_t box_n[4] = {TMA_NARROW, TY, 1, 1};
+    const cuuint32_t box_w[4] = {TMA_WIDE, TY, 1, 1};
     void* base = const_cast<void*>(f);
     if (enc(&maps.narrow, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box_n, elem,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -909,8 +902,8 @@ static cudaError_t launch_tma(const TmaMaps& maps, const void* fin, void* fout, 
                               cudaStream_t st) {
     using T = typename Store<ST>::T;
     // Stages first (the dynamic window starts the CTA's shared memory, so the
-    // TMA destinations are aligned), then the mbarriers, records and a flag.
-    const size_t smem = 2 * TMA_STAGE_BYTES + 16 + sizeof(BubbleRec) * TMA_THREADS + 16;
+    // TMA destinations are aligned), then the two mbarriers and a flag.
+    const size_t smem = 2 * TMA_STAGE_BYTES + 16 + 16;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_collide_stream_tma<ST>,
@@ -923,7 +916,7 @@ static cudaError_t launch_tma(const TmaMaps& maps, const void* fin, void* fout, 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream_tma<ST>, TMA_THREADS,
                                                   smem);
-    const int ntiles = g.ntx * g.nty * g.ntz;
+    const int ntiles = ((g.nx + TMA_BX - 1) / TMA_BX) * g.nty * g.nz;
     const int grid = std::max(1, std::min(ntiles, sms * std::max(per_sm, 1)));
     k_collide_stream_tma<ST><<<grid, TMA_THREADS, smem, st>>>(maps, (const T*)fin, (T*)fout, g, cp,
                                                                start, count, items, cap, recs, nb,
