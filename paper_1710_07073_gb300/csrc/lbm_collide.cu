@@ -14,19 +14,9 @@
 // short: nodes away from the box faces address their 19 sources with one
 // 32-bit offset each, tiles without bubbles skip the forcing terms, and each
 // pair of opposite directions shares its equilibrium terms.
-#include <cuda.h>
-
-#include <algorithm>
-
 #include "lbm_device.cuh"
 
 namespace lbm {
-
-// The TMA-staged sweep is used for 16-bit storage when the layout allows it;
-// set_tma_sweep(false) selects the two-nodes-per-thread sweep instead.
-static bool g_use_tma = true;
-bool use_tma_sweep() { return g_use_tma; }
-void set_tma_sweep(bool on) { g_use_tma = on; }
 
 // Force Phi at node (x,y,z) from one bubble record: tensor product of cell
 // integrals (Eq. 19) times psi_b / normalisation.
@@ -276,9 +266,6 @@ template <> struct Vec2<0> {
     static __device__ __forceinline__ float2 load(const float* p) {
         return __ldg(reinterpret_cast<const float2*>(p));
     }
-    static __device__ __forceinline__ float2 load_shared(const float* p) {
-        return *reinterpret_cast<const float2*>(p);
-    }
     static __device__ __forceinline__ void store(float* p, float2 v) {
         __stcs(reinterpret_cast<float2*>(p), v);
     }
@@ -287,9 +274,6 @@ template <> struct Vec2<1> {
     static __device__ __forceinline__ float2 load(const __half* p) {
         return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
     }
-    static __device__ __forceinline__ float2 load_shared(const __half* p) {
-        return __half22float2(*reinterpret_cast<const __half2*>(p));
-    }
     static __device__ __forceinline__ void store(__half* p, float2 v) {
         __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(v.x, v.y));
     }
@@ -297,9 +281,6 @@ template <> struct Vec2<1> {
 template <> struct Vec2<2> {
     static __device__ __forceinline__ float2 load(const __nv_bfloat16* p) {
         return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
-    }
-    static __device__ __forceinline__ float2 load_shared(const __nv_bfloat16* p) {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
     }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float2 v) {
         __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(v.x, v.y));
@@ -635,295 +616,6 @@ int pair_min_blocks(int storage) {
     return storage == 0 ? PairOccupancy<0>::kMinBlocks : PairOccupancy<1>::kMinBlocks;
 }
 
-// ---------------------------------------------------------------------------
-// TMA-staged sweep for 16-bit storage (nx a multiple of 8).
-//
-// Persistent CTAs walk tiles of 128 x 4 x 1 nodes.  For a tile, one thread
-// issues 19 bulk tensor copies -- one box per plane j, the tile shifted by
-// -c_j -- into a shared-memory stage and the CTA computes from shared memory
-// while the next tile's boxes are in flight (two stages, one mbarrier each).  A TMA box must start on a 16-byte boundary in x, so planes
-// that cross x are fetched 48 wide starting 8 nodes to the left.  Boxes that
-// reach outside the box domain come back zero-filled; nodes on the domain
-// faces therefore take their populations from the general pull instead.
-// Waits on an mbarrier are bounded: on timeout the kernel sets bit 4 of the
-// status flag, waits (bounded) for the copies it issued, and stops.
-// ---------------------------------------------------------------------------
-// A TMA tile is TMA_BX x TY x 1 nodes (4 binning tiles along x): boxes of
-// TY rows of 256-288 bytes keep the number of row requests per node low.
-constexpr int TMA_BX = 4 * TX;                     // 128 nodes along x
-constexpr int TMA_THREADS = (TMA_BX / 2) * TY;     // one x-pair per thread: 64 x 4
-constexpr int TMA_NARROW = TMA_BX;                 // box width of planes with c_x = 0
-constexpr int TMA_WIDE = TMA_BX + 16;              // box width of planes crossing x
-constexpr int TMA_ROW_NODES = TY;
-constexpr unsigned TMA_WAIT_LIMIT = 1u << 22;       // ~0.1-1 s of polling
-
-__host__ __device__ constexpr int tma_width(int j) { return cx(j) == 0 ? TMA_NARROW : TMA_WIDE; }
-__host__ __device__ constexpr int tma_plane_offset(int j) {   // in elements
-    return j == 0 ? 0 : tma_plane_offset(j - 1) + tma_width(j - 1) * TMA_ROW_NODES;
-}
-constexpr int TMA_STAGE_ELEMS = tma_plane_offset(Q);
-constexpr int TMA_STAGE_BYTES = TMA_STAGE_ELEMS * 2;
-static_assert(TMA_STAGE_BYTES % 128 == 0, "stages stay 128-byte aligned");
-
-struct TmaMaps {
-    CUtensorMap narrow;   // box TMA_NARROW x TY x 1 x 1
-    CUtensorMap wide;     // box TMA_WIDE x TY x 1 x 1
-};
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-    for (unsigned it = 0; it < TMA_WAIT_LIMIT; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (it > 64) __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int x, int y,
-                                            int z, int w, unsigned bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
-        : "memory");
-}
-
-// Issue the 19 boxes of TMA tile (bx, by, z) into one stage (thread 0 only).
-__device__ __forceinline__ void tma_issue_tile(const TmaMaps& maps, unsigned stage, unsigned bar,
-                                               int bx, int by, int bz) {
-    mbar_expect_tx(bar, (unsigned)TMA_STAGE_BYTES);
-    const int x0 = bx * TMA_BX, y0 = by * TY, z0 = bz;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        const CUtensorMap* map = cx(j) == 0 ? &maps.narrow : &maps.wide;
-        const int xs = cx(j) == 0 ? x0 : x0 - 8;   // 16-byte aligned start in x
-        tma_load_4d(stage + 2u * (unsigned)tma_plane_offset(j), map, xs, y0 - cy(j), z0 - cz(j), j,
-                    bar);
-    }
-}
-
-// Raw values of direction J for the pair (x0 + 2 tx, +1) from a stage.
-template <int ST, int J>
-__device__ __forceinline__ float2 stage_pair(const typename Store<ST>::T* st, int tx, int ty) {
-    using T = typename Store<ST>::T;
-    const T* row = st + tma_plane_offset(J) + ty * tma_width(J);
-    auto h2 = [&](int e) {
-        return Vec2<ST>::load_shared(row + e);
-    };
-    if (cx(J) == 0) return h2(2 * tx);
-    if (cx(J) == 1) {   // box starts at x0 - 8: node x receives x - 1 -> element 2tx + 7, 2tx + 8
-        const float2 a = h2(2 * tx + 6), b = h2(2 * tx + 8);
-        return make_float2(a.y, b.x);
-    }
-    const float2 a = h2(2 * tx + 8), b = h2(2 * tx + 10);   // x + 1 -> 2tx + 9, 2tx + 10
-    return make_float2(a.y, b.x);
-}
-
-template <int ST>
-__global__ void __launch_bounds__(TMA_THREADS, 3)
-k_collide_stream_tma(const __grid_constant__ TmaMaps maps,
-                     const typename Store<ST>::T* __restrict__ fin,
-                     typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
-                     const int* __restrict__ tile_start, const int* __restrict__ tile_count,
-                     const int* __restrict__ items, int cap, const BubbleRec* __restrict__ recs,
-                     int nb, int* __restrict__ flag) {
-    using T = typename Store<ST>::T;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    T* stages = reinterpret_cast<T*>(smem);                        // 2 stages
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem + 2 * TMA_STAGE_BYTES);
-    int& s_abort = *reinterpret_cast<int*>(smem + 2 * TMA_STAGE_BYTES + 16);
-    const int tid = threadIdx.x;
-    const int tx = tid % (TMA_BX / 2), ty = tid / (TMA_BX / 2);
-    const int nbx = (g.nx + TMA_BX - 1) / TMA_BX;
-    const int ntiles = nbx * g.nty * g.nz;
-    const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
-    const unsigned stage0 = smem_addr(stages), stage1 = stage0 + TMA_STAGE_BYTES;
-    if (tid == 0) {
-        mbar_init(bar0, 1);
-        mbar_init(bar1, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
-    }
-    __syncthreads();
-    int t = blockIdx.x;
-    if (tid == 0 && t < ntiles)
-        tma_issue_tile(maps, stage0, bar0, t % nbx, (t / nbx) % g.nty, t / (nbx * g.nty));
-    int issued = t < ntiles ? 1 : 0, waited = 0;
-    for (int i = 0; t < ntiles; ++i, t += gridDim.x) {
-        const int s = i & 1;
-        const int bx = t % nbx, by = (t / nbx) % g.nty, z = t / (nbx * g.nty);
-        const int tn = t + gridDim.x;
-        if (tid == 0 && tn < ntiles) {
-            tma_issue_tile(maps, s ? stage0 : stage1, s ? bar0 : bar1, tn % nbx,
-                           (tn / nbx) % g.nty, tn / (nbx * g.nty));
-            ++issued;
-        }
-        // Bounded wait for this tile's boxes.
-        if (tid == 0) s_abort = mbar_wait_bounded(s ? bar1 : bar0, (unsigned)((i >> 1) & 1)) ? 0 : 1;
-        __syncthreads();
-        if (s_abort) {
-            if (tid == 0) atomicOr(flag, 4);
-            break;
-        }
-        ++waited;
-        const T* st = stages + (s ? TMA_STAGE_ELEMS : 0);
-
-        const int x0 = bx * TMA_BX + 2 * tx, y = by * TY + ty;
-        const bool active = (x0 < g.nx) && (y < g.ny);
-        if (active) {
-            // Force from the bubbles binned to this node pair's tile (Eq. 21).
-            float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
-            bool forced = false;
-            if (tile_count != nullptr) {
-                const int bt = ((z / TZ) * g.nty + by) * g.ntx + x0 / TX;
-                const int n_t = tile_count[bt];
-                if (n_t > 0) {
-                    forced = true;
-                    const int beg = tile_start[bt];
-                    const int end = min(beg + n_t, cap);
-                    for (int k = beg; k < end; ++k) {
-                        const int id = items[k];
-                        if (id >= 0 && id < nb) add_bubble_force_pair(recs[id], g, x0, y, z, Fx, Fy, Fz);
-                    }
-                }
-            }
-            const unsigned S = (unsigned)g.S;
-            const unsigned site0 = ((unsigned)z * (unsigned)g.ny + (unsigned)y) * (unsigned)g.nx +
-                                   (unsigned)x0;
-            float2 rv[Q];
-            const bool face = x0 == 0 || x0 + 2 >= g.nx || y == 0 || y == g.ny - 1 || z == 0 ||
-                              z == g.nz - 1;
-            if (!face) {
-#define LBM_SP(J) rv[J] = stage_pair<ST, J>(st, tx, ty)
-                LBM_SP(0); LBM_SP(1); LBM_SP(2); LBM_SP(3); LBM_SP(4);
-                LBM_SP(5); LBM_SP(6); LBM_SP(7); LBM_SP(8); LBM_SP(9);
-                LBM_SP(10); LBM_SP(11); LBM_SP(12); LBM_SP(13); LBM_SP(14);
-                LBM_SP(15); LBM_SP(16); LBM_SP(17); LBM_SP(18);
-#undef LBM_SP
-            } else {
-#define LBM_PA(J) rv[J] = pull_pair_any<ST, J>(fin, g, x0, y, z)
-                LBM_PA(0); LBM_PA(1); LBM_PA(2); LBM_PA(3); LBM_PA(4);
-                LBM_PA(5); LBM_PA(6); LBM_PA(7); LBM_PA(8); LBM_PA(9);
-                LBM_PA(10); LBM_PA(11); LBM_PA(12); LBM_PA(13); LBM_PA(14);
-                LBM_PA(15); LBM_PA(16); LBM_PA(17); LBM_PA(18);
-#undef LBM_PA
-            }
-            if (forced) collide_store_pair<ST, true>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, true);
-            else collide_store_pair<ST, false>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, true);
-        }
-        __syncthreads();   // this stage is free for the tile after next
-    }
-    // Never leave copies in flight: wait (bounded) for any issued but unwaited stage.
-    if (tid == 0) {
-        for (int k = waited; k < issued; ++k) {
-            const int s = k & 1;
-            if (!mbar_wait_bounded(s ? bar1 : bar0, (unsigned)((k >> 1) & 1))) {
-                atomicOr(flag, 4);
-                break;
-            }
-        }
-    }
-    __syncthreads();
-}
-
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_tiled() {
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
-// Tensor maps over a 16-bit population buffer as a 4-D array
-// (x, y, z, plane); false if the layout does not allow TMA.
-static bool make_tma_maps(const void* f, const Geo& g, TmaMaps& maps) {
-    EncodeTiledFn enc = encode_tiled();
-    if (!enc || (g.nx % 8) != 0 || ((unsigned long long)f % 16) != 0) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)Q};
-    const cuuint64_t strides[3] = {(cuuint64_t)g.nx * 2, (cuuint64_t)g.nx * g.ny * 2,
-                                   (cuuint64_t)g.S * 2};
-    const cuuint32_t elem[4] = {1, 1, 1, 1};
-    const cuuint32_t box_n[4] = {TMA_NARROW, TY, 1, 1};
-    const cuuint32_t box_w[4] = {TMA_WIDE, TY, 1, 1};
-    void* base = const_cast<void*>(f);
-    if (enc(&maps.narrow, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box_n, elem,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    if (enc(&maps.wide, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, dims, strides, box_w, elem,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return false;
-    return true;
-}
-
-template <int ST>
-static cudaError_t launch_tma(const TmaMaps& maps, const void* fin, void* fout, const Geo& g,
-                              const CollideParams& cp, const int* start, const int* count,
-                              const int* items, int cap, const BubbleRec* recs, int nb, int* flag,
-                              cudaStream_t st) {
-    using T = typename Store<ST>::T;
-    // Stages first (the dynamic window starts the CTA's shared memory, so the
-    // TMA destinations are aligned), then the two mbarriers and a flag.
-    const size_t smem = 2 * TMA_STAGE_BYTES + 16 + 16;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_collide_stream_tma<ST>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_collide_stream_tma<ST>, TMA_THREADS,
-                                                  smem);
-    const int ntiles = ((g.nx + TMA_BX - 1) / TMA_BX) * g.nty * g.nz;
-    const int grid = std::max(1, std::min(ntiles, sms * std::max(per_sm, 1)));
-    k_collide_stream_tma<ST><<<grid, TMA_THREADS, smem, st>>>(maps, (const T*)fin, (T*)fout, g, cp,
-                                                               start, count, items, cap, recs, nb,
-                                                               flag);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, cudaStream_t st) {
@@ -931,14 +623,6 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
     const int* count = tl ? tl->count : nullptr;
     const int* items = tl ? tl->items : nullptr;
     const int cap = tl ? tl->cap : 0;
-    if (storage != 0 && use_tma_sweep()) {
-        TmaMaps maps;
-        if (make_tma_maps(fin, g, maps)) {
-            return storage == 1
-                ? launch_tma<1>(maps, fin, fout, g, cp, start, count, items, cap, recs, nb, flag, st)
-                : launch_tma<2>(maps, fin, fout, g, cp, start, count, items, cap, recs, nb, flag, st);
-        }
-    }
     if ((g.nx & 1) == 0) {
         // Even rows: two nodes per thread with aligned vector accesses.
         dim3 block(PX, TY, PZ);

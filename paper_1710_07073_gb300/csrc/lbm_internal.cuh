@@ -190,8 +190,6 @@ cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* 
 cudaError_t launch_bubble_constants_batch(const BubbleDev& b, const BubbleConst& bc,
                                           const double* col_nu, const int* bubble_col,
                                           cudaStream_t st);
-bool use_tma_sweep();
-void set_tma_sweep(bool on);
 int batch_block_threads();
 int batch_z_block();
 int pair_min_blocks(int storage);

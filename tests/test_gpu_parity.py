@@ -75,8 +75,8 @@ def test_one_step_random_populations(omega, walls, dims):
                                                (lbm.LBM_STORE_BF16, 1.0, 2.0 ** -8)])
 @pytest.mark.parametrize("dims", [(37, 9, 11), (38, 9, 11), (40, 9, 11), (32, 8, 8), (64, 12, 9)])
 def test_one_step_16bit_from_representable_input(storage, scale, tol, dims):
-    # nx odd: one node per thread; nx even: two nodes per thread; nx a multiple
-    # of 8: the TMA-staged sweep (ragged tiles in x, y and z included).
+    # nx odd: one node per thread; nx even: two nodes per thread (ragged tiles
+    # in x, y and z included).
     # Both sweeps in 16-bit storage: from populations the format holds exactly,
     # one step differs from the FP64 step by FP32 arithmetic plus one rounding
     # of each stored value (half an ulp, relative to f - w rho0).
