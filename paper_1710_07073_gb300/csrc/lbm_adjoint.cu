@@ -794,6 +794,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
         c->cur = cur;
         step_rc(cudaMemcpyAsync(c->f[cur], t->ck_f[seg], fb, cudaMemcpyDeviceToDevice, s), "restore");
         k_restore<<<sb, 128, 0, s>>>(c->bub, t->ck_b[seg]);
+        c->cover_valid = false;
         for (int n = n0; n < n1 && rc == LBM_OK; ++n) {
             step_rc(cudaMemcpyAsync(seg_f[n - n0], c->f[c->cur], fb, cudaMemcpyDeviceToDevice, s),
                     "segment state");
@@ -843,6 +844,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     c->cur = t->final_cur;
     step_rc(cudaMemcpyAsync(c->f[c->cur], t->final_f, fb, cudaMemcpyDeviceToDevice, s), "final");
     k_restore<<<sb, 128, 0, s>>>(c->bub, t->final_b);
+    c->cover_valid = false;
     step_rc(cudaStreamSynchronize(s), "adjoint");
     release();
     if (rc) return rc;

@@ -338,10 +338,13 @@ int run_steps(lbm_batch* b, int nsteps) {
 void free_bubbles(lbm_batch* b) {
     void* ptrs[] = {b->bub.k, b->bub.x, b->bub.u, b->bub.d, b->bub.n, b->bub.ulprev, b->bub.ul,
                     b->bub.psi, b->bub.has_prev, b->bub.active, b->bub.spread, b->bub.cell,
-                    b->bub.rec, b->bubble_col_d};
+                    b->bub.rec, b->bubble_col_d, b->small.part, b->small.arrive};
     for (void* ptr : ptrs) bfree(b, ptr);
     b->bub = BubbleDev{};
     b->bubble_col_d = nullptr;
+    b->small.part = nullptr;
+    b->small.arrive = nullptr;
+    b->small.parts = 0;
 }
 
 int axis_tile_bound(double n, int T) {
@@ -512,8 +515,11 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     B.cell = (int*)balloc(b, i1);
     B.rec = (BubbleRec*)balloc(b, sizeof(BubbleRec) * (size_t)n);
     b->bubble_col_d = (int*)balloc(b, i1);
+    sb.parts = window_parts(hwmax);
+    sb.part = (float*)balloc(b, sizeof(float) * 3 * WINDOW_CHUNKS_MAX * (size_t)n);
+    sb.arrive = (int*)balloc(b, i1);
     if (!B.k || !B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
-        !B.active || !B.spread || !B.cell || !B.rec || !b->bubble_col_d) {
+        !B.active || !B.spread || !B.cell || !B.rec || !b->bubble_col_d || !sb.part || !sb.arrive) {
         free_bubbles(b);
         return bfail(b, LBM_ERR_ALLOC, "bubble state");
     }
@@ -534,6 +540,7 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     LBM_BCUDA(cudaMemcpyAsync(B.cell, minus.data(), i1, cudaMemcpyHostToDevice, s), "cell");
     LBM_BCUDA(cudaMemcpyAsync(b->bubble_col_d, col_of.data(), i1, cudaMemcpyHostToDevice, s), "col");
     LBM_BCUDA(cudaMemsetAsync(B.rec, 0, sizeof(BubbleRec) * (size_t)n, s), "rec");
+    LBM_BCUDA(cudaMemsetAsync(sb.arrive, 0, i1, s), "arrive");
     LBM_BCUDA(launch_bubble_constants_batch(B, batch_bubble_const(b), b->col_nu_d, b->bubble_col_d, s),
               "bubble constants");
     LBM_BCUDA(cudaStreamSynchronize(s), "bubble upload");

@@ -1,13 +1,21 @@
 // Bubble side of the coupled step and the field utilities.
 //
-//  k_bubbles      one warp per bubble: forward coupling (Eq. 19-20) of the bare
-//                 Eq. 10 liquid velocity, Table 1 forces, sub-stepped Newton
-//                 update (Eq. 4, Table 2), reaction psi_b = -mean F_D
-//                 (Algorithm 1 step 6) and the spreading record for the sweep.
-//  binning        bubble windows to lattice tiles (Algorithm 1 step 2):
-//                 integer counting sort, then each tile's list in bubble order.
-//  field kernels  initialisation to f^eq (Eq. 6), population I/O, Eq. 10
-//                 moments and FP64 totals.
+//  k_bubbles_binned  few bubbles: the window of each bubble is reduced by one
+//                    or more CTAs (gathered Eq. 10 velocity, Eq. 19-20); the
+//                    CTA completing a bubble does the Table 1 forces, the
+//                    sub-stepped Newton update (Eq. 4, Table 2), the reaction
+//                    psi_b = -mean F_D (Algorithm 1 step 6) and the spreading
+//                    record; the last one bins all bubbles.
+//  k_moments_tiles,  many bubbles: Eq. 10 velocity of the covered tiles, then
+//  k_bubbles_warp    one warp per bubble with the same tail.
+//  binning           bubble windows to lattice tiles (Algorithm 1 step 2):
+//                    integer counting sort, then each tile's list in bubble
+//                    order.
+//  field kernels     initialisation to f^eq (Eq. 6), population I/O, Eq. 10
+//                    moments and FP64 totals.
+#include <algorithm>
+#include <cmath>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -28,17 +36,65 @@ __device__ __forceinline__ float axis_norm(double xa, float inv_n, int L, bool p
     return (b - a) * (p4 * 0.2f - (b2 + ab + a2) * (2.0f / 3.0f) + 1.0f);
 }
 
-__device__ __forceinline__ void make_record(const double* xb, float inv_n, const Geo& g,
+// ---- positions in two floats ------------------------------------------------
+// A position is carried through the sub-steps as hi + lo, two floats with
+// |lo| <= ulp(hi)/2 (about 48 significant bits), so the 10 sub-steps use the
+// FP32 pipe: FP64 issue is slow on this GPU and the bubble update is one
+// serial thread.  Sums use Knuth's TwoSum; the product error of u dt_b comes
+// from one FMA (the exact-product property of fused multiply-add).
+struct F2 {
+    float h, l;
+};
+
+__device__ __forceinline__ F2 f2_from(double v) {
+    const float h = (float)v;
+    return F2{h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ double f2_to(F2 a) { return (double)a.h + (double)a.l; }
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return F2{s, (a - (s - bb)) + (b - bb)};
+}
+
+// (a.h + a.l) + (bh + bl)
+__device__ __forceinline__ F2 f2_add(F2 a, float bh, float bl) {
+    const F2 s = two_sum(a.h, bh);
+    return two_sum(s.h, s.l + (a.l + bl));
+}
+
+__device__ __forceinline__ bool f2_lt(F2 a, F2 b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+
+// floor of hi + lo and the fraction (hi + lo) - floor in [0, 1].
+__device__ __forceinline__ int f2_floor(F2 a, float& frac) {
+    float f = floorf(a.h);
+    if (f == a.h && a.l < 0.0f) f -= 1.0f;
+    frac = (a.h - f) + a.l;
+    return (int)f;
+}
+
+// axis_norm of a two-float coordinate.
+__device__ __forceinline__ float axis_norm2(F2 xa, float inv_n, int L, bool periodic) {
+    if (periodic) return 16.0f / 15.0f;
+    const float lo = (-xa.h - xa.l) * inv_n, hi = (((float)L - xa.h) - xa.l) * inv_n;
+    const float a = fmaxf(lo, -1.0f), b = fminf(hi, 1.0f);
+    if (!(b > a)) return 0.0f;
+    const float a2 = a * a, b2 = b * b, ab = a * b;
+    const float p4 = b2 * b2 + b2 * ab + ab * ab + ab * a2 + a2 * a2;
+    return (b - a) * (p4 * 0.2f - (b2 + ab + a2) * (2.0f / 3.0f) + 1.0f);
+}
+
+__device__ __forceinline__ void make_record(const F2* xb, float inv_n, const Geo& g,
                                             const float* psi, BubbleRec& r) {
     int anc[3];
     float fr[3];
     float norm = 1.0f;
     const int L[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
-        const double fl = floor(xb[a]);
-        anc[a] = (int)fl;
-        fr[a] = (float)(xb[a] - fl);
-        norm *= axis_norm(xb[a], inv_n, L[a], !(g.walls & (1u << (2 * a))));
+        anc[a] = f2_floor(xb[a], fr[a]);
+        norm *= axis_norm2(xb[a], inv_n, L[a], !(g.walls & (1u << (2 * a))));
     }
     const float inv_norm = 1.0f / norm;
     r.ax = anc[0];
@@ -55,49 +111,53 @@ __device__ __forceinline__ void make_record(const double* xb, float inv_n, const
     r.pz = psi[2] * inv_norm;
 }
 
-// One CTA of BUBBLE_THREADS threads per bubble: the threads stride over the
-// window's nodes for the forward coupling, thread 0 integrates the bubble.
-//
+// Bare Eq. 10 velocity u = sum_j c_j g_j / (rho0 + sum_j g_j) of shifted
+// pre-collision populations.
+__device__ __forceinline__ void node_velocity(const float gv[Q], const CollideParams& cp,
+                                              float u[3]) {
+    float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        drho += gv[q];
+        if (cx(q) != 0) jx += (float)cx(q) * gv[q];
+        if (cy(q) != 0) jy += (float)cy(q) * gv[q];
+        if (cz(q) != 0) jz += (float)cz(q) * gv[q];
+    }
+    const float inv_rho = 1.0f / (cp.rho0 + drho);
+    u[0] = jx * inv_rho;
+    u[1] = jy * inv_rho;
+    u[2] = jz * inv_rho;
+}
+
 // Precision: positions are integrated in FP64 (they reach hundreds of lattice
 // units and move by 1e-5 per sub-step); velocities, forces and the mapping
 // weights are FP32.  FP64 latency on this GPU is long, so only the position
 // update, the window bounds and the wall tests use it.
 constexpr int BUBBLE_THREADS = 256;
 
-template <int ST>
-__device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const Geo& g,
-                              const CollideParams& cp, const BubbleDev& B, const BubbleConst& bc,
-                              int* __restrict__ flag, int b, float (*red)[BUBBLE_THREADS / 32]) {
-    const int tid = threadIdx.x;
-    if (b >= B.nb) return;
-    if (!B.active[b]) {
-        if (tid == 0) {
-            B.spread[b] = 0;
-            B.cell[b] = -1;
-        }
-        return;
-    }
-    const int L[3] = {g.nx, g.ny, g.nz};
-    double xb[3] = {B.x[3 * b], B.x[3 * b + 1], B.x[3 * b + 2]};
-    const double n = B.n[b];
-    const BubbleK K = B.k[b];
-    if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) {
-        // A non-finite centre can only come from an unstable liquid: stop
-        // coupling this bubble and report the instability.
-        if (tid == 0) {
-            B.active[b] = 0;
-            B.spread[b] = 0;
-            B.cell[b] = -1;
-            atomicOr(flag, 2);
-        }
-        return;
-    }
-
-    // Window cells per axis (Algorithm 1 step 2): cells overlapping (x - n, x + n).
-    const float inv_n = K.inv_nf, hh = 0.5f * K.inv_nf;
+// The interpolation window of one bubble (Algorithm 1 step 2): the cells
+// overlapping (x - n, x + n) per axis, the anchor cell and fraction of the
+// centre, and the in-domain weight sum used to renormalise.
+struct Window {
     int lo[3], cnt[3], anc[3];
     float fr[3];
-    float norm = 1.0f;
+    float norm;
+    int M;   // nodes in the window
+};
+
+enum { BUBBLE_LIVE = 0, BUBBLE_IDLE = 1, BUBBLE_NONFINITE = 2 };
+
+__device__ int bubble_window(const Geo& g, const BubbleDev& B, int b, Window& w) {
+    // All loads first (one round trip), then the decisions.
+    const int active = B.active[b];
+    const double xb[3] = {B.x[3 * b], B.x[3 * b + 1], B.x[3 * b + 2]};
+    const double n = B.n[b];
+    const float inv_n = B.k[b].inv_nf;
+    if (!active) return BUBBLE_IDLE;
+    const int L[3] = {g.nx, g.ny, g.nz};
+    // A non-finite centre can only come from an unstable liquid.
+    if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) return BUBBLE_NONFINITE;
+    w.norm = 1.0f;
     for (int a = 0; a < 3; ++a) {
         const bool periodic = !(g.walls & (1u << (2 * a)));
         int l = (int)floor(xb[a] - n);
@@ -106,81 +166,149 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
             l = max(l, 0);
             h = min(h, L[a] - 1);
         }
-        lo[a] = l;
-        cnt[a] = min(max(h - l + 1, 0), 2 * (int)MAX_HALF_WIDTH + 2);
+        w.lo[a] = l;
+        w.cnt[a] = min(max(h - l + 1, 0), WINDOW_CELLS_MAX);
         const double fl = floor(xb[a]);
-        anc[a] = (int)fl;
-        fr[a] = (float)(xb[a] - fl);
-        norm *= axis_norm(xb[a], inv_n, L[a], periodic);
+        w.anc[a] = (int)fl;
+        w.fr[a] = (float)(xb[a] - fl);
+        w.norm *= axis_norm(xb[a], inv_n, L[a], periodic);
     }
+    w.M = w.cnt[0] * w.cnt[1] * w.cnt[2];
+    return BUBBLE_LIVE;
+}
 
-    // Forward coupling (Eq. 20): threads stride over the window's nodes and
-    // weight the bare Eq. 10 velocity of the current populations.
-    float ax = 0.0f, ay = 0.0f, az = 0.0f;
-    const int M = cnt[0] * cnt[1] * cnt[2];
-    for (int m = tid; m < M; m += BUBBLE_THREADS) {
-        const int ix = m % cnt[0];
-        const int rest = m / cnt[0];
-        const int iy = rest % cnt[1];
-        const int iz = rest / cnt[1];
-        const int i = lo[0] + ix, j = lo[1] + iy, k = lo[2] + iz;
-        const float w = cell_poly(((float)(i - anc[0]) + 0.5f - fr[0]) * inv_n, hh) *
-                        cell_poly(((float)(j - anc[1]) + 0.5f - fr[1]) * inv_n, hh) *
-                        cell_poly(((float)(k - anc[2]) + 0.5f - fr[2]) * inv_n, hh);
-        const int iw = (i % g.nx + g.nx) % g.nx;
-        const int jw = (j % g.ny + g.ny) % g.ny;
-        const int kw = (k % g.nz + g.nz) % g.nz;
-        float gv[Q];
-        gather<ST>(f, g, cp, iw, jw, kw, gv);
-        float drho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            drho += gv[q];
-            if (cx(q) != 0) jx += (float)cx(q) * gv[q];
-            if (cy(q) != 0) jy += (float)cy(q) * gv[q];
-            if (cz(q) != 0) jz += (float)cz(q) * gv[q];
-        }
-        const float inv_rho = 1.0f / (cp.rho0 + drho);
-        ax = fmaf(w, jx * inv_rho, ax);
-        ay = fmaf(w, jy * inv_rho, ay);
-        az = fmaf(w, jz * inv_rho, az);
+// Weight and wrapped lattice coordinates of window node m (x fastest).
+__device__ __forceinline__ float window_node(const Geo& g, const Window& w, float inv_n, int m,
+                                             int& iw, int& jw, int& kw) {
+    const float hh = 0.5f * inv_n;
+    const int ix = m % w.cnt[0];
+    const int rest = m / w.cnt[0];
+    const int iy = rest % w.cnt[1];
+    const int iz = rest / w.cnt[1];
+    const int i = w.lo[0] + ix, j = w.lo[1] + iy, k = w.lo[2] + iz;
+    iw = (i % g.nx + g.nx) % g.nx;
+    jw = (j % g.ny + g.ny) % g.ny;
+    kw = (k % g.nz + g.nz) % g.nz;
+    return cell_poly(((float)(i - w.anc[0]) + 0.5f - w.fr[0]) * inv_n, hh) *
+           cell_poly(((float)(j - w.anc[1]) + 0.5f - w.fr[1]) * inv_n, hh) *
+           cell_poly(((float)(k - w.anc[2]) + 0.5f - w.fr[2]) * inv_n, hh);
+}
+
+// Eq. 20 partial sums of one chunk: nodes m0 + tid and m0 + tid + nt (below
+// m1), both gathered before either is used so their loads overlap.
+template <int ST>
+__device__ __forceinline__ void chunk_sum2(const typename Store<ST>::T* __restrict__ f,
+                                           const Geo& g, const CollideParams& cp, const Window& w,
+                                           float inv_n, int m0, int m1, int tid, int nt, float& ax,
+                                           float& ay, float& az) {
+    const int ma = m0 + tid, mb = ma + nt;
+    const bool ha = ma < m1, hb = mb < m1;
+    int ia, ja, ka, ib, jb, kb;
+    const float wa = window_node(g, w, inv_n, ha ? ma : m0, ia, ja, ka);
+    const float wb = window_node(g, w, inv_n, hb ? mb : m0, ib, jb, kb);
+    typename Store<ST>::T ra[Q], rb[Q];
+    gather_issue<ST>(f, g, ia, ja, ka, ra);
+    gather_issue<ST>(f, g, ib, jb, kb, rb);
+    float ga[Q], gb[Q];
+    gather_finish<ST>(ra, cp, ga);
+    gather_finish<ST>(rb, cp, gb);
+    float ua[3], ub[3];
+    node_velocity(ga, cp, ua);
+    node_velocity(gb, cp, ub);
+    if (ha) {
+        ax = fmaf(wa, ua[0], ax);
+        ay = fmaf(wa, ua[1], ay);
+        az = fmaf(wa, ua[2], az);
     }
+    if (hb) {
+        ax = fmaf(wb, ub[0], ax);
+        ay = fmaf(wb, ub[1], ay);
+        az = fmaf(wb, ub[2], az);
+    }
+}
+
+// Eq. 20 partial sums over the window nodes tid, tid + nt, ... from the
+// precomputed Eq. 10 velocities `mom` (three planes of S floats).
+__device__ __forceinline__ void window_sum_mom(const float* __restrict__ mom, const Geo& g,
+                                               const Window& w, float inv_n, int tid, int nt,
+                                               float& ax, float& ay, float& az) {
+    for (int m = tid; m < w.M; m += nt) {
+        int iw, jw, kw;
+        const float wt = window_node(g, w, inv_n, m, iw, jw, kw);
+        const size_t node = (size_t)site_index(g, iw, jw, kw);
+        ax = fmaf(wt, __ldg(mom + node), ax);
+        ay = fmaf(wt, __ldg(mom + (size_t)g.S + node), ay);
+        az = fmaf(wt, __ldg(mom + 2 * (size_t)g.S + node), az);
+    }
+}
+
+__device__ __forceinline__ void warp_sum3(float& ax, float& ay, float& az) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
         az += __shfl_xor_sync(0xffffffffu, az, o);
     }
+}
+
+// Sum of (ax, ay, az) over the CTA's BUBBLE_THREADS threads, in thread 0
+// (fixed order: warp shuffles, then warps in order).
+__device__ __forceinline__ void block_sum3(float& ax, float& ay, float& az,
+                                           float (*red)[BUBBLE_THREADS / 32]) {
+    warp_sum3(ax, ay, az);
+    const int tid = threadIdx.x;
     if ((tid & 31) == 0) {
         red[0][tid >> 5] = ax;
         red[1][tid >> 5] = ay;
         red[2][tid >> 5] = az;
     }
     __syncthreads();
-    if (tid != 0) return;
-    ax = ay = az = 0.0f;
-    for (int w = 0; w < BUBBLE_THREADS / 32; ++w) {
-        ax += red[0][w];
-        ay += red[1][w];
-        az += red[2][w];
+    if (tid == 0) {
+        ax = ay = az = 0.0f;
+        for (int k = 0; k < BUBBLE_THREADS / 32; ++k) {
+            ax += red[0][k];
+            ay += red[1][k];
+            az += red[2][k];
+        }
     }
+}
 
-    const float inv_norm = 1.0f / norm;
+// One thread: everything after the window sums (ax, ay, az) of bubble b.
+// An idle bubble leaves the coupling; a non-finite one is deactivated and
+// flags the instability; a live one takes the Table 1 forces and the Newton
+// update of Eq. 4 with the added mass on the left (m_eff), sub-stepped with
+// dt_b (Table 2), then its reaction psi (Algorithm 1) and spreading record.
+__device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst& bc,
+                            int* __restrict__ flag, int b, int state, const Window& w, float ax,
+                            float ay, float az) {
+    if (state != BUBBLE_LIVE) {
+        if (state == BUBBLE_NONFINITE) {
+            B.active[b] = 0;
+            atomicOr(flag, 2);
+        }
+        B.spread[b] = 0;
+        B.cell[b] = -1;
+        return;
+    }
+    const int L[3] = {g.nx, g.ny, g.nz};
+    F2 xb[3] = {f2_from(B.x[3 * b]), f2_from(B.x[3 * b + 1]), f2_from(B.x[3 * b + 2])};
+    const BubbleK K = B.k[b];
+    const float inv_norm = 1.0f / w.norm;
     const float ul[3] = {ax * inv_norm, ay * inv_norm, az * inv_norm};
     float fvm[3] = {0.0f, 0.0f, 0.0f};   // C_A rho_l V_b D_t u_l
     if (B.has_prev[b]) {
         for (int a = 0; a < 3; ++a)
             fvm[a] = K.fvm_coef_dt * (ul[a] - (float)B.ulprev[3 * b + a]);
     }
-
-    // Table 1 forces and the Newton update of Eq. 4 with the added mass on
-    // the left (m_eff), sub-stepped with dt_b (Table 2).
-    const double dt_b = bc.dt_b;
-    const double r = K.r;
+    const F2 dt_b = f2_from(bc.dt_b);
+    const F2 r = f2_from(K.r);
+    F2 top[3];   // L - r
+    for (int a = 0; a < 3; ++a) top[a] = f2_add(F2{(float)L[a], 0.0f}, -r.h, -r.l);
     const float sn_coeff = (float)bc.sn_coeff, sn_exp = (float)bc.sn_exp;
     const float fb[3] = {0.0f, 0.0f, K.fb};
     float u[3] = {(float)B.u[3 * b], (float)B.u[3 * b + 1], (float)B.u[3 * b + 2]};
     float fd_sum[3] = {0.0f, 0.0f, 0.0f};
+    bool wrap_far = false;   // a periodic coordinate left [-L, 2L): folded through FP64 below
     for (int k = 0; k < bc.substeps; ++k) {
         const float v0 = u[0] - ul[0], v1 = u[1] - ul[1], v2 = u[2] - ul[2];
         const float speed = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
@@ -192,33 +320,48 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
         for (int a = 0; a < 3; ++a) {
             fd_sum[a] += fd[a];
             u[a] = fmaf(fb[a] + fd[a] + fvm[a], K.kdt, u[a]);
-            xb[a] = fma((double)u[a], dt_b, xb[a]);
+            // x += u dt_b: the product as hi + lo (FMA error term), then TwoSum.
+            const float ph = u[a] * dt_b.h;
+            const float pl = fmaf(u[a], dt_b.h, -ph) + u[a] * dt_b.l;
+            xb[a] = f2_add(xb[a], ph, pl);
             if (g.walls & (1u << (2 * a))) {
-                if (xb[a] < r) {
+                if (f2_lt(xb[a], r)) {
                     xb[a] = r;
                     u[a] = fmaxf(u[a], 0.0f);
                 }
-                if (xb[a] > (double)L[a] - r) {
-                    xb[a] = (double)L[a] - r;
+                if (f2_lt(top[a], xb[a])) {
+                    xb[a] = top[a];
                     u[a] = fminf(u[a], 0.0f);
                 }
             } else {
-                xb[a] = __dsub_rn(xb[a], __dmul_rn((double)L[a], floor(xb[a] / (double)L[a])));
+                const float La = (float)L[a];
+                if (f2_lt(xb[a], F2{0.0f, 0.0f})) xb[a] = f2_add(xb[a], La, 0.0f);
+                else if (!f2_lt(xb[a], F2{La, 0.0f})) xb[a] = f2_add(xb[a], -La, 0.0f);
+                if (!(xb[a].h >= 0.0f && xb[a].h <= La)) wrap_far = true;
             }
+        }
+    }
+    if (wrap_far) {
+        // Only reachable with runaway or non-finite velocities: fold in FP64.
+        for (int a = 0; a < 3; ++a) {
+            if (g.walls & (1u << (2 * a))) continue;
+            double v = f2_to(xb[a]);
+            v = __dsub_rn(v, __dmul_rn((double)L[a], floor(v / (double)L[a])));
+            xb[a] = f2_from(v);
         }
     }
     float psi[3];
     const float inv_sub = 1.0f / (float)bc.substeps;
     for (int a = 0; a < 3; ++a) {
         psi[a] = -fd_sum[a] * inv_sub;
-        B.x[3 * b + a] = xb[a];
+        B.x[3 * b + a] = f2_to(xb[a]);
         B.u[3 * b + a] = u[a];
         B.ul[3 * b + a] = ul[a];
         B.ulprev[3 * b + a] = ul[a];
         B.psi[3 * b + a] = psi[a];
     }
     B.has_prev[b] = 1;
-    if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]) && isfinite(u[0]) &&
+    if (!(isfinite(xb[0].h) && isfinite(xb[1].h) && isfinite(xb[2].h) && isfinite(u[0]) &&
           isfinite(u[1]) && isfinite(u[2]) && isfinite(psi[0]) && isfinite(psi[1]) &&
           isfinite(psi[2]))) {
         B.active[b] = 0;
@@ -229,19 +372,97 @@ __device__ void bubble_update(const typename Store<ST>::T* __restrict__ f, const
     }
     B.spread[b] = 1;
     int ci[3];
-    for (int a = 0; a < 3; ++a) ci[a] = min(max((int)floor(xb[a]), 0), L[a] - 1);
+    for (int a = 0; a < 3; ++a) {
+        float fr;
+        ci[a] = min(max(f2_floor(xb[a], fr), 0), L[a] - 1);
+    }
     B.cell[b] = (ci[2] * g.ny + ci[1]) * g.nx + ci[0];
-    make_record(xb, inv_n, g, psi, B.rec[b]);
+    make_record(xb, K.inv_nf, g, psi, B.rec[b]);
     // Algorithm 1: the bubble stops once it reaches the top of the liquid.
-    if ((g.walls & 0x20) && xb[2] >= (double)g.nz - r) B.active[b] = 0;
+    if ((g.walls & 0x20) && !f2_lt(xb[2], top[2])) B.active[b] = 0;
 }
 
+// Many bubbles: one warp per bubble, window velocities from the moments of
+// the covered tiles.
+constexpr int WARP_BUBBLE_THREADS = 128;   // four bubbles per CTA
+
 template <int ST>
-__global__ void __launch_bounds__(BUBBLE_THREADS)
-k_bubbles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp, BubbleDev B,
-          BubbleConst bc, int* __restrict__ flag) {
-    __shared__ float red[3][BUBBLE_THREADS / 32];
-    bubble_update<ST>(f, g, cp, B, bc, flag, blockIdx.x, red);
+__global__ void __launch_bounds__(WARP_BUBBLE_THREADS)
+k_bubbles_warp(const typename Store<ST>::T* __restrict__ f, const float* __restrict__ mom, Geo g,
+               CollideParams cp, BubbleDev B, BubbleConst bc, int* __restrict__ flag) {
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (b >= B.nb) return;
+    const int lane = threadIdx.x & 31;
+    Window w;
+    const int state = bubble_window(g, B, b, w);
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+    if (state == BUBBLE_LIVE)
+        window_sum_mom(mom, g, w, B.k[b].inv_nf, lane, 32, ax, ay, az);
+    warp_sum3(ax, ay, az);
+    if (lane == 0) bubble_tail(g, B, bc, flag, b, state, w, ax, ay, az);
+}
+
+// Eq. 10 velocity of every node of the tiles some bubble window covers
+// (count > 0); other tiles are skipped.  One CTA per tile, TX x TY threads
+// looping over the tile's TZ planes.
+template <int ST>
+__global__ void __launch_bounds__(TX * TY)
+k_moments_tiles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
+                const int* __restrict__ tile_count, float* __restrict__ mom) {
+    const int t = blockIdx.x;
+    if (tile_count[t] == 0) return;
+    const int bx = t % g.ntx, by = (t / g.ntx) % g.nty, bz = t / (g.ntx * g.nty);
+    const int x = bx * TX + threadIdx.x, y = by * TY + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int zend = min(bz * TZ + TZ, g.nz);
+    for (int z = bz * TZ; z < zend; z += 2) {   // two planes per pass: 38 loads in flight
+        const bool two = z + 1 < zend;
+        typename Store<ST>::T ra[Q], rb[Q];
+        gather_issue<ST>(f, g, x, y, z, ra);
+        gather_issue<ST>(f, g, x, y, two ? z + 1 : z, rb);
+        float gv[Q], u[3];
+        gather_finish<ST>(ra, cp, gv);
+        node_velocity(gv, cp, u);
+        size_t node = (size_t)site_index(g, x, y, z);
+        mom[node] = u[0];
+        mom[(size_t)g.S + node] = u[1];
+        mom[2 * (size_t)g.S + node] = u[2];
+        if (two) {
+            gather_finish<ST>(rb, cp, gv);
+            node_velocity(gv, cp, u);
+            node += (size_t)g.nx * g.ny;
+            mom[node] = u[0];
+            mom[(size_t)g.S + node] = u[1];
+            mom[2 * (size_t)g.S + node] = u[2];
+        }
+    }
+}
+
+cudaError_t launch_bubbles_many(int storage, const void* f, float* mom, const Geo& g,
+                                const CollideParams& cp, const BubbleDev& b, const BubbleConst& bc,
+                                const int* tile_count, int* flag, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    const int T = g.ntx * g.nty * g.ntz;
+    const int blocks = (b.nb * 32 + WARP_BUBBLE_THREADS - 1) / WARP_BUBBLE_THREADS;
+    dim3 tb(TX, TY);
+    switch (storage) {
+        case 0:
+            k_moments_tiles<0><<<T, tb, 0, st>>>((const float*)f, g, cp, tile_count, mom);
+            k_bubbles_warp<0><<<blocks, WARP_BUBBLE_THREADS, 0, st>>>((const float*)f, mom, g, cp, b,
+                                                                      bc, flag);
+            break;
+        case 1:
+            k_moments_tiles<1><<<T, tb, 0, st>>>((const __half*)f, g, cp, tile_count, mom);
+            k_bubbles_warp<1><<<blocks, WARP_BUBBLE_THREADS, 0, st>>>((const __half*)f, mom, g, cp,
+                                                                      b, bc, flag);
+            break;
+        default:
+            k_moments_tiles<2><<<T, tb, 0, st>>>((const __nv_bfloat16*)f, g, cp, tile_count, mom);
+            k_bubbles_warp<2><<<blocks, WARP_BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, mom,
+                                                                      g, cp, b, bc, flag);
+            break;
+    }
+    return cudaGetLastError();
 }
 
 // Table 1 / Eq. 3 constants of each bubble (FP64).
@@ -307,9 +528,9 @@ __device__ int axis_tiles(double xa, double n, int L, bool periodic, int T,
 }
 
 template <bool FILL>
-__global__ void k_bin(Geo g, BubbleDev B, Bins bins) {
+__global__ void k_bin(Geo g, BubbleDev B, Bins bins, const int* __restrict__ select) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B.nb || !B.spread[b]) return;
+    if (b >= B.nb || !select[b]) return;
     const int L[3] = {g.nx, g.ny, g.nz};
     const int T[3] = {TX, TY, TZ};
     int tl[3][MAX_AXIS_TILES];
@@ -422,20 +643,33 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_add(int* off, int T, const 
         if (base + k < T) off[base + k] += add;
 }
 
-cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st) {
+cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st,
+                           const int* select) {
+    if (!select) select = b.spread;
     cudaError_t e = cudaMemsetAsync(bins.cnt, 0, sizeof(int) * (size_t)bins.T, st);
     if (e != cudaSuccess) return e;
     const int tb = 128;
     const int bb = (b.nb + tb - 1) / tb;
-    if (b.nb > 0) k_bin<false><<<bb, tb, 0, st>>>(g, b, bins);
+    if (b.nb > 0) k_bin<false><<<bb, tb, 0, st>>>(g, b, bins, select);
     k_scan_local<<<bins.nblocks, SCAN_BLOCK, 0, st>>>(bins.cnt, bins.off, bins.T, bins.block_sums);
     k_scan_sums<<<1, SCAN_BLOCK, 0, st>>>(bins.block_sums, bins.nblocks, bins.off, bins.T);
     k_scan_add<<<bins.nblocks, SCAN_BLOCK, 0, st>>>(bins.off, bins.T, bins.block_sums);
     e = cudaMemsetAsync(bins.cnt, 0, sizeof(int) * (size_t)bins.T, st);
     if (e != cudaSuccess) return e;
-    if (b.nb > 0) k_bin<true><<<bb, tb, 0, st>>>(g, b, bins);
+    if (b.nb > 0) k_bin<true><<<bb, tb, 0, st>>>(g, b, bins, select);
     k_bin_sort<<<(bins.T + 127) / 128, 128, 0, st>>>(bins);
     return cudaGetLastError();
+}
+
+// The per-tile counts of the previous binning back to zero (only the tiles it
+// listed), so that the counts stay valid between calls without a sweep over
+// all tiles.
+__device__ void clear_prev_tiles(const SmallBins& sb) {
+    const int prev = min(max(__ldcg(sb.prev_n), 0), SMALL_MAX_PAIRS);
+    for (int i = threadIdx.x; i < prev; i += blockDim.x) {
+        const int t = __ldcg(sb.prev_tiles + i);
+        if (t >= 0 && t < sb.T) sb.count[t] = 0;
+    }
 }
 
 // Few pairs: one CTA enumerates every (tile, bubble) pair, sorts the keys
@@ -450,11 +684,6 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
                                 const BatchColumn* cols = nullptr,
                                 const int* bubble_col = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int prev = min(max(__ldcg(sb.prev_n), 0), SMALL_MAX_PAIRS);
-    for (int i = tid; i < prev; i += nt) {
-        const int t = __ldcg(sb.prev_tiles + i);
-        if (t >= 0 && t < sb.T) sb.count[t] = 0;
-    }
     if (tid == 0) *s_n = 0;
     __syncthreads();
     const int T[3] = {TX, TY, TZ};
@@ -511,107 +740,142 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
     if (tid == 0) *sb.prev_n = n;
 }
 
-// Bubble update with the few-pair binning fused behind it: every CTA updates
-// its bubble, then counts itself done; the CTA that finds all others done
-// (no waiting: it is simply the last to arrive) bins all bubbles.
+// Bubble update with the few-pair binning fused behind it.
+//
+// The window of a bubble is cut into chunks of WINDOW_CHUNK nodes (node m of
+// chunk k is m = k WINDOW_CHUNK + thread or + thread + BUBBLE_THREADS), and
+// sb.parts CTAs share a bubble, CTA p taking chunks p, p + parts, ...  Each
+// chunk is reduced in a fixed order and the chunk sums are added in chunk
+// order, so the result does not depend on `parts`: a bubble gives the same
+// bits in a column of its own and in a batch.  The CTA that completes a
+// bubble's chunks (the last to arrive; nothing waits) integrates it; the CTA
+// that completes the last bubble bins all bubbles.  CTA 0 first clears the
+// previous binning's tile counts; that is ordered before the new binning by
+// the same arrive / done counters.  With `cols` set (a batch), bubble b lives
+// in column bubble_col[b].
 template <int ST>
-__global__ void __launch_bounds__(BUBBLE_THREADS)
+__global__ void __launch_bounds__(BUBBLE_THREADS, 1)
 k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
-                 BubbleDev B, BubbleConst bc, int* __restrict__ flag, SmallBins sb) {
+                 BubbleDev B, BubbleConst bc, int* __restrict__ flag, SmallBins sb,
+                 const BatchColumn* __restrict__ cols, const int* __restrict__ bubble_col) {
     __shared__ float red[3][BUBBLE_THREADS / 32];
     __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
     __shared__ int s_n, s_last;
-    bubble_update<ST>(f, g, cp, B, bc, flag, blockIdx.x, red);
-    __syncthreads();
+    const int parts = sb.parts;
+    const int b = blockIdx.x / parts, p = blockIdx.x - b * parts;
+    if (blockIdx.x == 0) {
+        clear_prev_tiles(sb);
+        __threadfence();
+    }
+    if (cols) {
+        const BatchColumn& col = cols[bubble_col[b]];
+        f += col.pop_offset;
+        g = col.g;
+        cp = col.cp;
+    }
+    Window w;
+    const int state = bubble_window(g, B, b, w);
+    const int nchunks = state == BUBBLE_LIVE ? (w.M + WINDOW_CHUNK - 1) / WINDOW_CHUNK : 0;
+    const float inv_n = B.k[b].inv_nf;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;   // thread 0: running sum over this CTA's chunks
+    for (int k = p; k < nchunks; k += parts) {
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        const int m0 = k * WINDOW_CHUNK;
+        chunk_sum2<ST>(f, g, cp, w, inv_n, m0, min(m0 + WINDOW_CHUNK, w.M), threadIdx.x,
+                       BUBBLE_THREADS, ax, ay, az);
+        block_sum3(ax, ay, az, red);
+        if (threadIdx.x == 0) {
+            if (parts == 1) {
+                sx += ax;
+                sy += ay;
+                sz += az;
+            } else {
+                float* slot = sb.part + 3 * ((size_t)b * WINDOW_CHUNKS_MAX + k);
+                slot[0] = ax;
+                slot[1] = ay;
+                slot[2] = az;
+            }
+        }
+        __syncthreads();   // `red` is reused by the next chunk
+    }
+    __syncthreads();       // CTA 0's clearing is complete before thread 0 arrives
+    const bool alone = gridDim.x == 1;   // one bubble, one CTA: nothing to publish
     if (threadIdx.x == 0) {
-        __threadfence();                                 // publish this bubble's state
-        s_last = atomicAdd(sb.done, 1) == (int)gridDim.x - 1;
+        bool mine = true;
+        if (parts > 1) {
+            __threadfence();                                 // publish this CTA's chunk sums
+            mine = atomicAdd(sb.arrive + b, 1) == parts - 1;
+            if (mine) {
+                __threadfence();
+                const float* q = sb.part + 3 * (size_t)b * WINDOW_CHUNKS_MAX;
+                for (int k = 0; k < nchunks; ++k) {
+                    sx += __ldcg(q + 3 * k);
+                    sy += __ldcg(q + 3 * k + 1);
+                    sz += __ldcg(q + 3 * k + 2);
+                }
+                sb.arrive[b] = 0;                            // ready for the next launch
+            }
+        }
+        s_last = 0;
+        if (mine) {
+            bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz);
+            if (alone) {
+                s_last = 1;
+            } else {
+                __threadfence();                             // publish this bubble's state
+                s_last = atomicAdd(sb.done, 1) == B.nb - 1;
+            }
+        }
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
-    bin_small_block(g, B, sb, keys, &s_n);
-    if (threadIdx.x == 0) *sb.done = 0;                  // ready for the next launch
+    if (!alone) __threadfence();
+    bin_small_block(g, B, sb, keys, &s_n, cols, bubble_col);
+    if (threadIdx.x == 0 && !alone) *sb.done = 0;        // ready for the next launch
 }
+
+int window_parts(double max_half_width) {
+    const int cells = std::min((int)std::ceil(2.0 * max_half_width) + 1, WINDOW_CELLS_MAX);
+    const int nodes = cells * cells * cells;
+    return std::max(1, std::min((nodes + WINDOW_CHUNK - 1) / WINDOW_CHUNK, WINDOW_CHUNKS_MAX));
+}
+
+namespace {
+template <int ST>
+void launch_binned(const void* f, const Geo& g, const CollideParams& cp, const BubbleDev& b,
+                   const BubbleConst& bc, int* flag, const SmallBins& sb, const BatchColumn* cols,
+                   const int* bubble_col, cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    k_bubbles_binned<ST><<<b.nb * sb.parts, BUBBLE_THREADS, 0, st>>>(
+        (const T*)f, g, cp, b, bc, flag, sb, cols, bubble_col);
+}
+}  // namespace
 
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag,
-                           const SmallBins* fused, cudaStream_t st) {
+                           const SmallBins& sb, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
-    if (fused) {
-        switch (storage) {
-            case 0:
-                k_bubbles_binned<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, g, cp, b, bc,
-                                                                     flag, *fused);
-                break;
-            case 1:
-                k_bubbles_binned<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, g, cp, b, bc,
-                                                                     flag, *fused);
-                break;
-            default:
-                k_bubbles_binned<2><<<b.nb, BUBBLE_THREADS, 0, st>>>(
-                    (const __nv_bfloat16*)f, g, cp, b, bc, flag, *fused);
-                break;
-        }
-        return cudaGetLastError();
-    }
+    if (sb.parts < 1 || sb.parts > WINDOW_CHUNKS_MAX) return cudaErrorInvalidValue;
     switch (storage) {
-        case 0:
-            k_bubbles<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, g, cp, b, bc, flag);
-            break;
-        case 1:
-            k_bubbles<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, g, cp, b, bc, flag);
-            break;
-        default:
-            k_bubbles<2><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, g, cp, b, bc,
-                                                          flag);
-            break;
+        case 0: launch_binned<0>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, st); break;
+        case 1: launch_binned<1>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, st); break;
+        default: launch_binned<2>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, st); break;
     }
     return cudaGetLastError();
-}
-
-// Bubble update of a batch: bubble b moves in column bubble_col[b]; the
-// few-pair binning of all columns is fused behind it as for one column.
-template <int ST>
-__global__ void __launch_bounds__(BUBBLE_THREADS)
-k_bubbles_batch(const typename Store<ST>::T* __restrict__ f, const BatchColumn* __restrict__ cols,
-                const int* __restrict__ bubble_col, BubbleDev B, BubbleConst bc,
-                int* __restrict__ flag, SmallBins sb) {
-    __shared__ float red[3][BUBBLE_THREADS / 32];
-    __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
-    __shared__ int s_n, s_last;
-    const int b = blockIdx.x;
-    const BatchColumn& col = cols[bubble_col[b]];
-    bubble_update<ST>(f + col.pop_offset, col.g, col.cp, B, bc, flag, b, red);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(sb.done, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    bin_small_block(col.g, B, sb, keys, &s_n, cols, bubble_col);
-    if (threadIdx.x == 0) *sb.done = 0;
 }
 
 cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* cols,
                                  const int* bubble_col, const BubbleDev& b, const BubbleConst& bc,
                                  int* flag, const SmallBins& sb, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
+    if (sb.parts < 1 || sb.parts > WINDOW_CHUNKS_MAX) return cudaErrorInvalidValue;
+    // Geometry and relaxation come from each bubble's column.
+    const Geo g0{};
+    const CollideParams cp0{};
     switch (storage) {
-        case 0:
-            k_bubbles_batch<0><<<b.nb, BUBBLE_THREADS, 0, st>>>((const float*)f, cols, bubble_col,
-                                                                b, bc, flag, sb);
-            break;
-        case 1:
-            k_bubbles_batch<1><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __half*)f, cols, bubble_col,
-                                                                b, bc, flag, sb);
-            break;
-        default:
-            k_bubbles_batch<2><<<b.nb, BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, cols,
-                                                                bubble_col, b, bc, flag, sb);
-            break;
+        case 0: launch_binned<0>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, st); break;
+        case 1: launch_binned<1>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, st); break;
+        default: launch_binned<2>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, st); break;
     }
     return cudaGetLastError();
 }

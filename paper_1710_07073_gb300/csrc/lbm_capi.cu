@@ -153,8 +153,10 @@ void free_bubbles(lbm_ctx* c) {
     SmallBins& sb = c->small;
     void* ptrs[] = {b.k, b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
                     b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items, sb.prev_tiles,
-                    sb.prev_n, sb.overflow, sb.done};
+                    sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, c->mom};
     for (void* p : ptrs) dfree(c, p);
+    c->mom = nullptr;
+    c->cover_valid = false;
     b = BubbleDev{};
     sb = SmallBins{};
     c->bins.items = nullptr;
@@ -171,14 +173,24 @@ int enqueue_one_step(lbm_ctx* c) {
     const bool bubbles = c->bub.nb > 0;
     const bool two_way = bubbles && c->p.two_way;
     if (bubbles) {
-        LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c), c->flag_d,
-                                c->use_small ? &c->small : nullptr, c->stream),
-                 "bubble update");
         if (c->use_small) {
+            LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
+                                    c->flag_d, c->small, c->stream),
+                     "bubble update");
             c->launches += 1;   // binning fused into the bubble update
         } else {
+            // The tiles holding the windows of the current centres: left by
+            // the previous step's binning, else binned here from `active`.
+            if (!c->cover_valid) {
+                LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream, c->bub.active), "cover");
+                c->launches += BINNING_LAUNCHES;
+            }
+            LBM_CUDA(launch_bubbles_many(c->storage, c->f[c->cur], c->mom, g, cp, c->bub,
+                                         bubble_const(c), c->bins.cnt, c->flag_d, c->stream),
+                     "bubble update");
             LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
-            c->launches += 1 + BINNING_LAUNCHES;
+            c->launches += 2 + BINNING_LAUNCHES;
+            c->cover_valid = true;
         }
         c->bins_valid = true;
     }
@@ -491,12 +503,16 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sb.prev_n = (int*)dalloc(c, sizeof(int));
         sb.overflow = (int*)dalloc(c, sizeof(int));
         sb.done = (int*)dalloc(c, sizeof(int));
+        sb.parts = window_parts(hwmax);
+        sb.part = (float*)dalloc(c, sizeof(float) * 3 * WINDOW_CHUNKS_MAX * (size_t)n);
+        sb.arrive = (int*)dalloc(c, sizeof(int) * (size_t)n);
         lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow &&
-                   sb.done;
+                   sb.done && sb.part && sb.arrive;
     } else {
         c->bins.cap = (int)cap;
         c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
-        lists_ok = c->bins.items != nullptr;
+        c->mom = (float*)dalloc(c, sizeof(float) * 3 * (size_t)c->nx * c->ny * c->nz);
+        lists_ok = c->bins.items != nullptr && c->mom != nullptr;
     }
     if (!B.k || !B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
         !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
@@ -509,6 +525,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         LBM_CUDA(cudaMemsetAsync(sb.prev_n, 0, sizeof(int), c->stream), "prev_n");
         LBM_CUDA(cudaMemsetAsync(sb.overflow, 0, sizeof(int), c->stream), "overflow");
         LBM_CUDA(cudaMemsetAsync(sb.done, 0, sizeof(int), c->stream), "done");
+        LBM_CUDA(cudaMemsetAsync(sb.arrive, 0, sizeof(int) * (size_t)n, c->stream), "arrive");
     }
     B.nb = n;
     std::vector<double> hn(n), zeros(3 * (size_t)n, 0.0);

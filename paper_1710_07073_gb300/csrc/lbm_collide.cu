@@ -470,33 +470,9 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     const int xa = active ? x0 : 0;
     const int ya = min(y, g.ny - 1), za = min(z, g.nz - 1);
 
-    float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
-    bool forced = false;   // uniform over the CTA (one tile)
-    if (tile_count != nullptr) {
-        const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
-        const int n_t = tile_count[t];
-        if (n_t > 0) {
-            forced = true;
-            const int beg = tile_start[t];
-            const int end = min(beg + n_t, cap);
-            const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
-            constexpr int NT = PX * TY * PZ;
-            for (int c0 = beg; c0 < end; c0 += NT) {
-                const int cnt = min(NT, end - c0);
-                __syncthreads();
-                if (tid < cnt) {
-                    const int id = items[c0 + tid];
-                    if (id >= 0 && id < nb) srec[tid] = recs[id];
-                    else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                }
-                __syncthreads();
-                if (active)
-                    for (int k = 0; k < cnt; ++k)
-                        add_bubble_force_pair(srec[k], g, x0, y, z, Fx, Fy, Fz);
-            }
-            __syncthreads();   // srec is reused by the CTA's next block
-        }
-    }
+    const int n_t = tile_count != nullptr
+                        ? tile_count[(((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx]
+                        : 0;
 
     const unsigned S = (unsigned)g.S;
     const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
@@ -518,6 +494,33 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
         LBM_PA(15); LBM_PA(16); LBM_PA(17); LBM_PA(18);
 #undef LBM_PA
     }
+    // The force gather (Eq. 21) runs after the population loads are issued,
+    // so the tile-list lookup does not delay them.
+    float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
+    bool forced = false;   // uniform over the CTA (one tile)
+    if (n_t > 0) {
+        forced = true;
+        const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
+        const int beg = tile_start[t];
+        const int end = min(beg + n_t, cap);
+        const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
+        constexpr int NT = PX * TY * PZ;
+        for (int c0 = beg; c0 < end; c0 += NT) {
+            const int cnt = min(NT, end - c0);
+            __syncthreads();
+            if (tid < cnt) {
+                const int id = items[c0 + tid];
+                if (id >= 0 && id < nb) srec[tid] = recs[id];
+                else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            }
+            __syncthreads();
+            if (active)
+                for (int k = 0; k < cnt; ++k)
+                    add_bubble_force_pair(srec[k], g, x0, y, z, Fx, Fy, Fz);
+        }
+        __syncthreads();   // srec is reused by the CTA's next block
+    }
+
     if (forced) collide_store_pair<ST, true>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
     else collide_store_pair<ST, false>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
 }

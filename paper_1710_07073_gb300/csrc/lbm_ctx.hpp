@@ -44,6 +44,10 @@ struct lbm_ctx {
     SmallBins small{};
     bool use_small = false;
     bool bins_valid = false;
+    // Large path: Eq. 10 velocity of the covered tiles (3 planes of S floats)
+    // and whether bins.cnt marks the windows of the current centres.
+    float* mom = nullptr;
+    bool cover_valid = false;
 
     // timing of the collide-stream launches
     bool timing = false;

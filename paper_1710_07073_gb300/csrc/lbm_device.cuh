@@ -17,6 +17,9 @@ template <int ST> struct Store;
 template <> struct Store<0> {
     using T = float;
     static constexpr bool kScaled = false;
+    static __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+    template <int J>
+    static __device__ __forceinline__ float widen(T v, const CollideParams&) { return v; }
     static __device__ __forceinline__ float load_raw(const T* p) { return __ldg(p); }
     static __device__ __forceinline__ void store_raw(T* p, float v) { __stcs(p, v); }
     template <int J>
@@ -38,6 +41,11 @@ template <> struct Store<0> {
 template <> struct Store<1> {
     using T = __half;
     static constexpr bool kScaled = true;
+    static __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+    template <int J>
+    static __device__ __forceinline__ float widen(T v, const CollideParams& cp) {
+        return __half2float(v) * (wf(J) * cp.inv_scale);
+    }
     static __device__ __forceinline__ float load_raw(const T* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void store_raw(T* p, float v) {
         __stcs(p, __float2half_rn(v));
@@ -61,6 +69,11 @@ template <> struct Store<1> {
 template <> struct Store<2> {
     using T = __nv_bfloat16;
     static constexpr bool kScaled = true;
+    static __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+    template <int J>
+    static __device__ __forceinline__ float widen(T v, const CollideParams& cp) {
+        return __bfloat162float(v) * (wf(J) * cp.inv_scale);
+    }
     static __device__ __forceinline__ float load_raw(const T* p) {
         return __bfloat162float(__ldg(p));
     }
@@ -117,15 +130,61 @@ __device__ __forceinline__ void pull_source(const Geo& g, int x, int y, int z, i
     }
 }
 
-template <int ST, int J>
-__device__ __forceinline__ float pull_one(const typename Store<ST>::T* __restrict__ f,
-                                          const Geo& g, const CollideParams& cp, int x, int y,
-                                          int z) {
-    int plane, idx;
-    pull_source<J>(g, x, y, z, plane, idx);
+// Element offset (plane j S + site) of the population j arriving at node
+// (x,y,z) under Eq. 16, with the wrap and the half-way bounce-back of
+// pull_source written as selects: no branches, so that a gather can compute
+// all 19 offsets, then issue all 19 loads, then use them.
+template <int J>
+__device__ __forceinline__ unsigned pull_offset(const Geo& g, int x, int y, int z) {
+    int sx = x - cx(J), sy = y - cy(J), sz = z - cz(J);
+    bool bounce = false;
+    if (cx(J) != 0) {
+        const bool out = (unsigned)sx >= (unsigned)g.nx;
+        bounce = bounce || (out && (g.walls & 0x01));
+        sx = out ? (sx < 0 ? sx + g.nx : sx - g.nx) : sx;
+    }
+    if (cy(J) != 0) {
+        const bool out = (unsigned)sy >= (unsigned)g.ny;
+        bounce = bounce || (out && (g.walls & 0x04));
+        sy = out ? (sy < 0 ? sy + g.ny : sy - g.ny) : sy;
+    }
+    if (cz(J) != 0) {
+        const bool out = (unsigned)sz >= (unsigned)g.nz;
+        bounce = bounce || (out && (g.walls & 0x10));
+        sz = out ? (sz < 0 ? sz + g.nz : sz - g.nz) : sz;
+    }
+    const unsigned S = (unsigned)g.S;
+    const unsigned own = (unsigned)site_index(g, x, y, z);
+    const unsigned src = (unsigned)site_index(g, sx, sy, sz);
     // The stored scale of a bounced population is that of its own plane; the
     // 16-bit formats share w_j between opposite directions, so J's scale holds.
-    return Store<ST>::template load<J>(f + (size_t)plane * (size_t)g.S + idx, cp);
+    return bounce ? (unsigned)opp(J) * S + own : (unsigned)J * S + src;
+}
+
+// Stored pre-collision values at one node: the 19 loads, issued together.
+template <int ST>
+__device__ __forceinline__ void gather_issue(const typename Store<ST>::T* __restrict__ f,
+                                             const Geo& g, int x, int y, int z,
+                                             typename Store<ST>::T raw[Q]) {
+    unsigned o[Q];
+#define LBM_OFF(J) o[J] = pull_offset<J>(g, x, y, z)
+    LBM_OFF(0); LBM_OFF(1); LBM_OFF(2); LBM_OFF(3); LBM_OFF(4); LBM_OFF(5); LBM_OFF(6);
+    LBM_OFF(7); LBM_OFF(8); LBM_OFF(9); LBM_OFF(10); LBM_OFF(11); LBM_OFF(12); LBM_OFF(13);
+    LBM_OFF(14); LBM_OFF(15); LBM_OFF(16); LBM_OFF(17); LBM_OFF(18);
+#undef LBM_OFF
+#pragma unroll
+    for (int q = 0; q < Q; ++q) raw[q] = Store<ST>::ld(f + o[q]);
+}
+
+// Stored values to shifted populations f_j - w_j rho0.
+template <int ST>
+__device__ __forceinline__ void gather_finish(const typename Store<ST>::T raw[Q],
+                                              const CollideParams& cp, float gv[Q]) {
+#define LBM_WID(J) gv[J] = Store<ST>::template widen<J>(raw[J], cp)
+    LBM_WID(0); LBM_WID(1); LBM_WID(2); LBM_WID(3); LBM_WID(4); LBM_WID(5); LBM_WID(6);
+    LBM_WID(7); LBM_WID(8); LBM_WID(9); LBM_WID(10); LBM_WID(11); LBM_WID(12); LBM_WID(13);
+    LBM_WID(14); LBM_WID(15); LBM_WID(16); LBM_WID(17); LBM_WID(18);
+#undef LBM_WID
 }
 
 // Pre-collision populations f_j(x, t) - w_j rho0 at one node (Eq. 16 pull).
@@ -133,25 +192,9 @@ template <int ST>
 __device__ __forceinline__ void gather(const typename Store<ST>::T* __restrict__ f, const Geo& g,
                                        const CollideParams& cp, int x, int y, int z,
                                        float gv[Q]) {
-    gv[0] = pull_one<ST, 0>(f, g, cp, x, y, z);
-    gv[1] = pull_one<ST, 1>(f, g, cp, x, y, z);
-    gv[2] = pull_one<ST, 2>(f, g, cp, x, y, z);
-    gv[3] = pull_one<ST, 3>(f, g, cp, x, y, z);
-    gv[4] = pull_one<ST, 4>(f, g, cp, x, y, z);
-    gv[5] = pull_one<ST, 5>(f, g, cp, x, y, z);
-    gv[6] = pull_one<ST, 6>(f, g, cp, x, y, z);
-    gv[7] = pull_one<ST, 7>(f, g, cp, x, y, z);
-    gv[8] = pull_one<ST, 8>(f, g, cp, x, y, z);
-    gv[9] = pull_one<ST, 9>(f, g, cp, x, y, z);
-    gv[10] = pull_one<ST, 10>(f, g, cp, x, y, z);
-    gv[11] = pull_one<ST, 11>(f, g, cp, x, y, z);
-    gv[12] = pull_one<ST, 12>(f, g, cp, x, y, z);
-    gv[13] = pull_one<ST, 13>(f, g, cp, x, y, z);
-    gv[14] = pull_one<ST, 14>(f, g, cp, x, y, z);
-    gv[15] = pull_one<ST, 15>(f, g, cp, x, y, z);
-    gv[16] = pull_one<ST, 16>(f, g, cp, x, y, z);
-    gv[17] = pull_one<ST, 17>(f, g, cp, x, y, z);
-    gv[18] = pull_one<ST, 18>(f, g, cp, x, y, z);
+    typename Store<ST>::T raw[Q];
+    gather_issue<ST>(f, g, x, y, z, raw);
+    gather_finish<ST>(raw, cp, gv);
 }
 
 // Integral of the mapping function over [s - h, s + h] in units of the

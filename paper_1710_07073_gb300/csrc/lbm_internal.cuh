@@ -135,6 +135,13 @@ struct TileLists {
 // (tile, bubble) in shared memory; only the tiles touched by the previous step
 // are cleared, so no work scales with the tile count.
 constexpr int SMALL_MAX_PAIRS = 4096;
+// A bubble window is reduced in chunks of WINDOW_CHUNK nodes (two per thread
+// of a 256-thread bubble CTA): at most (2 MAX_HALF_WIDTH + 2)^3 / WINDOW_CHUNK
+// rounded up.
+constexpr int WINDOW_CELLS_MAX = 2 * (int)MAX_HALF_WIDTH + 2;
+constexpr int WINDOW_CHUNK = 512;
+constexpr int WINDOW_CHUNKS_MAX =
+    (WINDOW_CELLS_MAX * WINDOW_CELLS_MAX * WINDOW_CELLS_MAX + WINDOW_CHUNK - 1) / WINDOW_CHUNK;
 struct SmallBins {
     int T;
     int* start;        // [T]
@@ -143,7 +150,10 @@ struct SmallBins {
     int* prev_tiles;   // [SMALL_MAX_PAIRS] tile of each pair of the last binning
     int* prev_n;       // [1] number of pairs of the last binning
     int* overflow;     // [1]
-    int* done;         // [1] CTAs of the bubble update that have finished (0 between launches)
+    int* done;         // [1] bubbles the update has finished (0 between launches)
+    int parts;         // CTAs per bubble in the update, 1..WINDOW_CHUNKS_MAX
+    float* part;       // [nb * WINDOW_CHUNKS_MAX * 3] chunk sums (parts > 1)
+    int* arrive;       // [nb] CTAs of a bubble that have finished (0 between launches)
 };
 
 // One column of a batch: its geometry and relaxation, where its populations
@@ -162,14 +172,26 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
 
-// Bubble update; with `fused` the few-pair binning runs in the same launch.
+// Bubble update with the few-pair binning in the same launch (sb.parts CTAs
+// per bubble).
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag,
-                           const SmallBins* fused, cudaStream_t st);
+                           const SmallBins& sb, cudaStream_t st);
+// CTAs per bubble for windows of half-width up to max_half_width: one per
+// 256-node chunk of the largest window.
+int window_parts(double max_half_width);
 cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st);
+// Many bubbles: Eq. 10 velocity of the covered tiles into mom[3*S], then one
+// warp per bubble interpolating from it.  tile_count: the binning of the
+// current centres (count > 0 marks a covered tile).
+cudaError_t launch_bubbles_many(int storage, const void* f, float* mom, const Geo& g,
+                                const CollideParams& cp, const BubbleDev& b, const BubbleConst& bc,
+                                const int* tile_count, int* flag, cudaStream_t st);
 // Kernels launched by one launch_binning call (count, 3-pass scan, fill, sort).
+// Bubbles b with select[b] != 0 are binned; select defaults to b.spread.
 constexpr int BINNING_LAUNCHES = 6;
-cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st);
+cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, cudaStream_t st,
+                           const int* select = nullptr);
 cudaError_t launch_fields(int storage, const void* f, const Geo& g, const CollideParams& cp,
                           double* rho, double* u, cudaStream_t st);
 cudaError_t launch_get_populations(int storage, const void* f, const Geo& g,
