@@ -147,13 +147,33 @@ struct Window {
 
 enum { BUBBLE_LIVE = 0, BUBBLE_IDLE = 1, BUBBLE_NONFINITE = 2 };
 
-__device__ int bubble_window(const Geo& g, const BubbleDev& B, int b, Window& w) {
-    // All loads first (one round trip), then the decisions.
-    const int active = B.active[b];
-    const double xb[3] = {B.x[3 * b], B.x[3 * b + 1], B.x[3 * b + 2]};
-    const double n = B.n[b];
-    const float inv_n = B.k[b].inv_nf;
-    if (!active) return BUBBLE_IDLE;
+// The state of one bubble that an update reads, loaded in one round trip at
+// the start of the kernel (the integration part only by the thread that will
+// integrate, `full`).
+struct BubbleIn {
+    double x[3], n;
+    BubbleK k;
+    double u[3], ulprev[3];
+    int active, has_prev;
+};
+
+__device__ __forceinline__ void load_bubble(const BubbleDev& B, int b, bool full, BubbleIn& in) {
+    in.active = B.active[b];
+    for (int a = 0; a < 3; ++a) in.x[a] = B.x[3 * b + a];
+    in.n = B.n[b];
+    in.k = B.k[b];
+    in.has_prev = full ? B.has_prev[b] : 0;
+    for (int a = 0; a < 3; ++a) {
+        in.u[a] = full ? B.u[3 * b + a] : 0.0;
+        in.ulprev[a] = full ? B.ulprev[3 * b + a] : 0.0;
+    }
+}
+
+__device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w) {
+    const double* xb = in.x;
+    const double n = in.n;
+    const float inv_n = in.k.inv_nf;
+    if (!in.active) return BUBBLE_IDLE;
     const int L[3] = {g.nx, g.ny, g.nz};
     // A non-finite centre can only come from an unstable liquid.
     if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) return BUBBLE_NONFINITE;
@@ -280,7 +300,7 @@ __device__ __forceinline__ void block_sum3(float& ax, float& ay, float& az,
 // dt_b (Table 2), then its reaction psi (Algorithm 1) and spreading record.
 __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst& bc,
                             int* __restrict__ flag, int b, int state, const Window& w, float ax,
-                            float ay, float az) {
+                            float ay, float az, const BubbleIn& in) {
     if (state != BUBBLE_LIVE) {
         if (state == BUBBLE_NONFINITE) {
             B.active[b] = 0;
@@ -291,14 +311,13 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
         return;
     }
     const int L[3] = {g.nx, g.ny, g.nz};
-    F2 xb[3] = {f2_from(B.x[3 * b]), f2_from(B.x[3 * b + 1]), f2_from(B.x[3 * b + 2])};
-    const BubbleK K = B.k[b];
+    F2 xb[3] = {f2_from(in.x[0]), f2_from(in.x[1]), f2_from(in.x[2])};
+    const BubbleK& K = in.k;
     const float inv_norm = 1.0f / w.norm;
     const float ul[3] = {ax * inv_norm, ay * inv_norm, az * inv_norm};
     float fvm[3] = {0.0f, 0.0f, 0.0f};   // C_A rho_l V_b D_t u_l
-    if (B.has_prev[b]) {
-        for (int a = 0; a < 3; ++a)
-            fvm[a] = K.fvm_coef_dt * (ul[a] - (float)B.ulprev[3 * b + a]);
+    if (in.has_prev) {
+        for (int a = 0; a < 3; ++a) fvm[a] = K.fvm_coef_dt * (ul[a] - (float)in.ulprev[a]);
     }
     const F2 dt_b = f2_from(bc.dt_b);
     const F2 r = f2_from(K.r);
@@ -306,7 +325,7 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
     for (int a = 0; a < 3; ++a) top[a] = f2_add(F2{(float)L[a], 0.0f}, -r.h, -r.l);
     const float sn_coeff = (float)bc.sn_coeff, sn_exp = (float)bc.sn_exp;
     const float fb[3] = {0.0f, 0.0f, K.fb};
-    float u[3] = {(float)B.u[3 * b], (float)B.u[3 * b + 1], (float)B.u[3 * b + 2]};
+    float u[3] = {(float)in.u[0], (float)in.u[1], (float)in.u[2]};
     float fd_sum[3] = {0.0f, 0.0f, 0.0f};
     bool wrap_far = false;   // a periodic coordinate left [-L, 2L): folded through FP64 below
     for (int k = 0; k < bc.substeps; ++k) {
@@ -393,13 +412,14 @@ k_bubbles_warp(const typename Store<ST>::T* __restrict__ f, const float* __restr
     const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (b >= B.nb) return;
     const int lane = threadIdx.x & 31;
+    BubbleIn in;
+    load_bubble(B, b, lane == 0, in);
     Window w;
-    const int state = bubble_window(g, B, b, w);
+    const int state = bubble_window(g, in, w);
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
-    if (state == BUBBLE_LIVE)
-        window_sum_mom(mom, g, w, B.k[b].inv_nf, lane, 32, ax, ay, az);
+    if (state == BUBBLE_LIVE) window_sum_mom(mom, g, w, in.k.inv_nf, lane, 32, ax, ay, az);
     warp_sum3(ax, ay, az);
-    if (lane == 0) bubble_tail(g, B, bc, flag, b, state, w, ax, ay, az);
+    if (lane == 0) bubble_tail(g, B, bc, flag, b, state, w, ax, ay, az, in);
 }
 
 // Eq. 10 velocity of every node of the tiles some bubble window covers
@@ -665,8 +685,12 @@ cudaError_t launch_binning(const Geo& g, const BubbleDev& b, const Bins& bins, c
 // listed), so that the counts stay valid between calls without a sweep over
 // all tiles.
 __device__ void clear_prev_tiles(const SmallBins& sb) {
+    // The first entries are read together with the count (one round trip);
+    // prev_tiles holds SMALL_MAX_PAIRS entries, so the read is in bounds.
+    const int first = (int)threadIdx.x < SMALL_MAX_PAIRS ? __ldcg(sb.prev_tiles + threadIdx.x) : -1;
     const int prev = min(max(__ldcg(sb.prev_n), 0), SMALL_MAX_PAIRS);
-    for (int i = threadIdx.x; i < prev; i += blockDim.x) {
+    if ((int)threadIdx.x < prev && first >= 0 && first < sb.T) sb.count[first] = 0;
+    for (int i = threadIdx.x + blockDim.x; i < prev; i += blockDim.x) {
         const int t = __ldcg(sb.prev_tiles + i);
         if (t >= 0 && t < sb.T) sb.count[t] = 0;
     }
@@ -763,9 +787,12 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
     __shared__ int s_n, s_last;
     const int parts = sb.parts;
     const int b = blockIdx.x / parts, p = blockIdx.x - b * parts;
+    const bool alone = gridDim.x == 1;   // one bubble, one CTA: nothing to publish
+    BubbleIn in;
+    load_bubble(B, b, threadIdx.x == 0, in);
     if (blockIdx.x == 0) {
         clear_prev_tiles(sb);
-        __threadfence();
+        if (!alone) __threadfence();
     }
     if (cols) {
         const BatchColumn& col = cols[bubble_col[b]];
@@ -774,9 +801,9 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
         cp = col.cp;
     }
     Window w;
-    const int state = bubble_window(g, B, b, w);
+    const int state = bubble_window(g, in, w);
     const int nchunks = state == BUBBLE_LIVE ? (w.M + WINDOW_CHUNK - 1) / WINDOW_CHUNK : 0;
-    const float inv_n = B.k[b].inv_nf;
+    const float inv_n = in.k.inv_nf;
     float sx = 0.0f, sy = 0.0f, sz = 0.0f;   // thread 0: running sum over this CTA's chunks
     for (int k = p; k < nchunks; k += parts) {
         float ax = 0.0f, ay = 0.0f, az = 0.0f;
@@ -799,7 +826,6 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
         __syncthreads();   // `red` is reused by the next chunk
     }
     __syncthreads();       // CTA 0's clearing is complete before thread 0 arrives
-    const bool alone = gridDim.x == 1;   // one bubble, one CTA: nothing to publish
     if (threadIdx.x == 0) {
         bool mine = true;
         if (parts > 1) {
@@ -818,7 +844,7 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
         }
         s_last = 0;
         if (mine) {
-            bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz);
+            bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz, in);
             if (alone) {
                 s_last = 1;
             } else {

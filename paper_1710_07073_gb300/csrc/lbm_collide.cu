@@ -360,43 +360,74 @@ __device__ __forceinline__ float2 pull_pair_any(const typename Store<ST>::T* __r
     return make_float2(pull_raw_any<ST, J>(f, g, x0, y, z), pull_raw_any<ST, J>(f, g, x0 + 1, y, z));
 }
 
-template <int ST, int J, bool FORCED>
-__device__ __forceinline__ void relax_pair2(typename Store<ST>::T* __restrict__ fout, unsigned S,
-                                            unsigned site0, const float2 rv[Q], float2 base,
-                                            float2 rho, float2 ux, float2 uy, float2 uz,
-                                            float2 Fx, float2 Fy, float2 Fz, float2 uF,
-                                            const CollideParams& cp, bool store) {
-    const float C = Store<ST>::kScaled ? cp.scale : wf(J);
-    float2 cu = f2(0.0f);
-    if (cx(J) != 0) cu = fma2(f2((float)cx(J)), ux, cu);
-    if (cy(J) != 0) cu = fma2(f2((float)cy(J)), uy, cu);
-    if (cz(J) != 0) cu = fma2(f2((float)cz(J)), uz, cu);
-    const float2 rcu = mul2(rho, cu);
-    float2 even = mul2(f2(cp.omega), fma2(mul2(f2(4.5f), rcu), cu, base));
-    float2 odd = mul2(f2(3.0f * cp.omega), rcu);
-    if (FORCED) {
-        float2 cF = f2(0.0f);
-        if (cx(J) != 0) cF = fma2(f2((float)cx(J)), Fx, cF);
-        if (cy(J) != 0) cF = fma2(f2((float)cy(J)), Fy, cF);
-        if (cz(J) != 0) cF = fma2(f2((float)cz(J)), Fz, cF);
-        even = fma2(f2(cp.pref), fma2(mul2(f2(9.0f), cu), cF, mul2(f2(-3.0f), uF)), even);
-        odd = fma2(f2(3.0f * cp.pref), cF, odd);
-    }
-    const float2 om1 = f2(1.0f - cp.omega);
-    const float2 a = fma2(om1, rv[J], mul2(f2(C), add2(even, odd)));
-    const float2 b = fma2(om1, rv[J + 1], mul2(f2(C), sub2(even, odd)));
-    if (store) {
-        Vec2<ST>::store(fout + ((unsigned)J * S + site0), a);
-        Vec2<ST>::store(fout + ((unsigned)(J + 1) * S + site0), b);
-    }
+// c_j . v for direction J (J odd; J + 1 is its opposite), written with adds
+// only: no multiply by +-1.
+template <int J>
+__device__ __forceinline__ float2 c_dot(float2 vx, float2 vy, float2 vz) {
+    constexpr int X = cx(J), Y = cy(J), Z = cz(J);
+    static_assert((J & 1) && (X == 1 || (X == 0 && Y == 1) || (X == 0 && Y == 0 && Z == 1)),
+                  "odd directions lead with a +1 component");
+    if (Y == 0 && Z == 0) return vx;                    // J = 1 (+x)
+    if (X == 0 && Z == 0) return vy;                    // J = 3 (+y)
+    if (X == 0 && Y == 0) return vz;                    // J = 5 (+z)
+    if (Z == 0) return Y > 0 ? add2(vx, vy) : sub2(vx, vy);
+    if (Y == 0) return Z > 0 ? add2(vx, vz) : sub2(vx, vz);
+    return Z > 0 ? add2(vy, vz) : sub2(vy, vz);
 }
 
-template <int ST, bool FORCED>
-__device__ __forceinline__ void collide_store_pair(typename Store<ST>::T* __restrict__ fout,
-                                                   unsigned S, unsigned site0, const float2 rv[Q],
-                                                   float2 Fx, float2 Fy, float2 Fz,
-                                                   const CollideParams& cp, int* flag,
-                                                   bool store) {
+// Per-class coefficients of the relaxation in stored units: with K = C omega
+// (C = w_j for FP32, the storage scale for 16 bits), the post-collision value
+// of J and of its opposite is
+//   (1 - omega) r_{J or J+1} + K base + 4.5 K rho (c.u)^2  +-  3 K rho (c.u)
+// (Eq. 6 and 14 with f^eq - w rho0 written around base = drho - 1.5 rho u^2).
+struct RelaxK {
+    float2 base, r45, r3;
+};
+
+__device__ __forceinline__ RelaxK relax_k(float K, float2 base, float2 rho) {
+    return RelaxK{mul2(f2(K), base), mul2(f2(4.5f * K), rho), mul2(f2(3.0f * K), rho)};
+}
+
+// Where a collided pair goes: the pair kernel stores it (2-wide, plane J at
+// site0); the four-node kernel keeps the first pair packed and stores both
+// pairs together.
+template <int ST>
+struct PairStore {
+    typename Store<ST>::T* fout;
+    unsigned S, site0;
+    bool store;
+    template <int J>
+    __device__ __forceinline__ void put(float2 v) const {
+        if (store) Vec2<ST>::store(fout + ((unsigned)J * S + site0), v);
+    }
+};
+
+template <int ST, int J, bool FORCED, class Sink>
+__device__ __forceinline__ void relax_pair2(Sink& sink, const float2 rv[Q], const RelaxK& k,
+                                            float2 ux, float2 uy, float2 uz, float2 Fx, float2 Fy,
+                                            float2 Fz, float2 uF, const CollideParams& cp) {
+    const float2 cu = c_dot<J>(ux, uy, uz);
+    float2 even = fma2(mul2(k.r45, cu), cu, k.base);
+    float2 odd = mul2(k.r3, cu);
+    if (FORCED) {
+        // Guo term (Eq. 15), (1 - omega/2) w_j [3 (c - u) + 9 (c.u) c] . F
+        const float C = Store<ST>::kScaled ? cp.scale : wf(J);
+        const float2 cF = c_dot<J>(Fx, Fy, Fz);
+        even = fma2(f2(C * cp.pref), fma2(mul2(f2(9.0f), cu), cF, mul2(f2(-3.0f), uF)), even);
+        odd = fma2(f2(3.0f * C * cp.pref), cF, odd);
+    }
+    const float2 om1 = f2(1.0f - cp.omega);
+    sink.template put<J>(fma2(om1, rv[J], add2(even, odd)));
+    sink.template put<J + 1>(fma2(om1, rv[J + 1], sub2(even, odd)));
+}
+
+// Collision of one x-pair of nodes (Eq. 13, 6, 14, 12, 15) from its
+// pre-collision values rv (stored units); `live` pairs take part in the
+// stability flag.
+template <int ST, bool FORCED, class Sink>
+__device__ __forceinline__ void collide_pair(Sink& sink, const float2 rv[Q], float2 Fx, float2 Fy,
+                                             float2 Fz, const CollideParams& cp, int* flag,
+                                             bool live) {
     const float2 s_axis = add2(add2(add2(rv[1], rv[2]), add2(rv[3], rv[4])), add2(rv[5], rv[6]));
     const float2 s_edge = add2(add2(add2(add2(rv[7], rv[8]), add2(rv[9], rv[10])),
                                     add2(add2(rv[11], rv[12]), add2(rv[13], rv[14]))),
@@ -435,17 +466,20 @@ __device__ __forceinline__ void collide_store_pair(typename Store<ST>::T* __rest
         uz = mul2(jz, inv_rho);
     }
     const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
-    if (store && !(usq.x < 0.09f && usq.y < 0.09f)) atomicOr(flag, 1);
+    if (live && !(usq.x < 0.09f && usq.y < 0.09f)) atomicOr(flag, 1);
     const float2 uF = FORCED ? fma2(ux, Fx, fma2(uy, Fy, mul2(uz, Fz))) : f2(0.0f);
     const float2 base = fma2(mul2(f2(-1.5f), rho), usq, drho);
     float2 e0 = mul2(f2(cp.omega), base);
     if (FORCED) e0 = fma2(f2(-3.0f * cp.pref), uF, e0);
     const float C0 = Store<ST>::kScaled ? cp.scale : wf(0);
-    const float2 r0 = fma2(f2(1.0f - cp.omega), rv[0], mul2(f2(C0), e0));
-    if (store) Vec2<ST>::store(fout + site0, r0);
-#define LBM_PAIR2(J) relax_pair2<ST, J, FORCED>(fout, S, site0, rv, base, rho, ux, uy, uz, Fx, Fy, Fz, uF, cp, store)
-    LBM_PAIR2(1); LBM_PAIR2(3); LBM_PAIR2(5); LBM_PAIR2(7); LBM_PAIR2(9);
-    LBM_PAIR2(11); LBM_PAIR2(13); LBM_PAIR2(15); LBM_PAIR2(17);
+    sink.template put<0>(fma2(f2(1.0f - cp.omega), rv[0], mul2(f2(C0), e0)));
+    // One coefficient class for the 16-bit formats (C = scale); FP32 has
+    // the axis and the diagonal weights.
+    const RelaxK ka = relax_k((Store<ST>::kScaled ? cp.scale : wf(1)) * cp.omega, base, rho);
+    const RelaxK ke = Store<ST>::kScaled ? ka : relax_k(wf(7) * cp.omega, base, rho);
+#define LBM_PAIR2(J, K) relax_pair2<ST, J, FORCED>(sink, rv, K, ux, uy, uz, Fx, Fy, Fz, uF, cp)
+    LBM_PAIR2(1, ka); LBM_PAIR2(3, ka); LBM_PAIR2(5, ka); LBM_PAIR2(7, ke); LBM_PAIR2(9, ke);
+    LBM_PAIR2(11, ke); LBM_PAIR2(13, ke); LBM_PAIR2(15, ke); LBM_PAIR2(17, ke);
 #undef LBM_PAIR2
 }
 
@@ -521,8 +555,9 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
         __syncthreads();   // srec is reused by the CTA's next block
     }
 
-    if (forced) collide_store_pair<ST, true>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
-    else collide_store_pair<ST, false>(fout, S, site0, rv, Fx, Fy, Fz, cp, flag, active);
+    PairStore<ST> sink{fout, S, site0, active};
+    if (forced) collide_pair<ST, true>(sink, rv, Fx, Fy, Fz, cp, flag, active);
+    else collide_pair<ST, false>(sink, rv, Fx, Fy, Fz, cp, flag, active);
 }
 
 template <int ST>
