@@ -40,6 +40,7 @@ constexpr int ADJ_MAX_SUB = 64;
 // after it (ul = u_l of the step, psi, x', u', rec = spreading record).
 struct BubbleSnap {
     double x[3], u[3], q[3], ul[3], psi[3];
+    float xh[3], xl[3];   // the centre as stored (x = xh + xl), for an exact restore
     int h, active;
     BubbleRec rec;
 };
@@ -61,7 +62,9 @@ __global__ void k_snapshot(BubbleDev B, BubbleSnap* out, int post) {
     if (b >= B.nb) return;
     BubbleSnap& s = out[b];
     for (int a = 0; a < 3; ++a) {
-        s.x[a] = B.x[3 * b + a];
+        s.xh[a] = B.xh[3 * b + a];
+        s.xl[a] = B.xl[3 * b + a];
+        s.x[a] = join_f2(s.xh[a], s.xl[a]);
         s.u[a] = B.u[3 * b + a];
         if (post) {
             s.ul[a] = B.ul[3 * b + a];
@@ -84,9 +87,10 @@ __global__ void k_restore(BubbleDev B, const BubbleSnap* in) {
     if (b >= B.nb) return;
     const BubbleSnap& s = in[b];
     for (int a = 0; a < 3; ++a) {
-        B.x[3 * b + a] = s.x[a];
-        B.u[3 * b + a] = s.u[a];
-        B.ulprev[3 * b + a] = s.q[a];
+        B.xh[3 * b + a] = s.xh[a];
+        B.xl[3 * b + a] = s.xl[a];
+        B.u[3 * b + a] = (float)s.u[a];
+        B.ulprev[3 * b + a] = (float)s.q[a];
     }
     B.has_prev[b] = s.h;
     B.active[b] = s.active;

@@ -131,6 +131,7 @@ BubbleConst batch_bubble_const(const lbm_batch* b) {
     bc.nu = 0.0;   // per column
     bc.dt_l = 1.0;
     bc.dt_b = 1.0 / b->p.substeps;
+    split_f2(bc.dt_b, bc.dt_bh, bc.dt_bl);
     bc.substeps = b->p.substeps;
     return bc;
 }
@@ -336,7 +337,7 @@ int run_steps(lbm_batch* b, int nsteps) {
 }
 
 void free_bubbles(lbm_batch* b) {
-    void* ptrs[] = {b->bub.k, b->bub.x, b->bub.u, b->bub.d, b->bub.n, b->bub.ulprev, b->bub.ul,
+    void* ptrs[] = {b->bub.k, b->bub.xh, b->bub.xl, b->bub.u, b->bub.d, b->bub.n, b->bub.ulprev, b->bub.ul,
                     b->bub.psi, b->bub.has_prev, b->bub.active, b->bub.spread, b->bub.cell,
                     b->bub.rec, b->bubble_col_d, b->small.part, b->small.arrive};
     for (void* ptr : ptrs) bfree(b, ptr);
@@ -499,16 +500,17 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     LBM_BCUDA(cudaMemsetAsync(sb.prev_n, 0, sizeof(int), s), "prev_n");
     if (n == 0) return LBM_OK;
     BubbleDev& B = b->bub;
-    const size_t v3 = sizeof(double) * 3 * (size_t)n, v1 = sizeof(double) * (size_t)n,
+    const size_t f3 = sizeof(float) * 3 * (size_t)n, v1 = sizeof(double) * (size_t)n,
                  i1 = sizeof(int) * (size_t)n;
     B.k = (BubbleK*)balloc(b, sizeof(BubbleK) * (size_t)n);
-    B.x = (double*)balloc(b, v3);
-    B.u = (double*)balloc(b, v3);
+    B.xh = (float*)balloc(b, f3);
+    B.xl = (float*)balloc(b, f3);
+    B.u = (float*)balloc(b, f3);
     B.d = (double*)balloc(b, v1);
     B.n = (double*)balloc(b, v1);
-    B.ulprev = (double*)balloc(b, v3);
-    B.ul = (double*)balloc(b, v3);
-    B.psi = (double*)balloc(b, v3);
+    B.ulprev = (float*)balloc(b, f3);
+    B.ul = (float*)balloc(b, f3);
+    B.psi = (float*)balloc(b, f3);
     B.has_prev = (int*)balloc(b, i1);
     B.active = (int*)balloc(b, i1);
     B.spread = (int*)balloc(b, i1);
@@ -518,22 +520,19 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     sb.parts = window_parts(hwmax);
     sb.part = (float*)balloc(b, sizeof(float) * 3 * WINDOW_CHUNKS_MAX * (size_t)n);
     sb.arrive = (int*)balloc(b, i1);
-    if (!B.k || !B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
-        !B.active || !B.spread || !B.cell || !B.rec || !b->bubble_col_d || !sb.part || !sb.arrive) {
+    if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi ||
+        !B.has_prev || !B.active || !B.spread || !B.cell || !B.rec || !b->bubble_col_d ||
+        !sb.part || !sb.arrive) {
         free_bubbles(b);
         return bfail(b, LBM_ERR_ALLOC, "bubble state");
     }
     B.nb = n;
-    std::vector<double> hn(n), zeros(3 * (size_t)n, 0.0);
+    std::vector<double> hn(n);
     for (int k = 0; k < n; ++k) hn[k] = b->p.width_factor * diam[k];
     std::vector<int> ones(n, 1), izero(n, 0), minus(n, -1);
-    LBM_BCUDA(cudaMemcpyAsync(B.x, pos3, v3, cudaMemcpyHostToDevice, s), "pos");
-    LBM_BCUDA(cudaMemcpyAsync(B.u, vel3 ? vel3 : zeros.data(), v3, cudaMemcpyHostToDevice, s), "vel");
+    LBM_BCUDA(upload_bubble_state(B, n, pos3, vel3, s), "bubbles");
     LBM_BCUDA(cudaMemcpyAsync(B.d, diam, v1, cudaMemcpyHostToDevice, s), "diam");
     LBM_BCUDA(cudaMemcpyAsync(B.n, hn.data(), v1, cudaMemcpyHostToDevice, s), "n");
-    LBM_BCUDA(cudaMemcpyAsync(B.ulprev, zeros.data(), v3, cudaMemcpyHostToDevice, s), "ulprev");
-    LBM_BCUDA(cudaMemcpyAsync(B.ul, zeros.data(), v3, cudaMemcpyHostToDevice, s), "ul");
-    LBM_BCUDA(cudaMemcpyAsync(B.psi, zeros.data(), v3, cudaMemcpyHostToDevice, s), "psi");
     LBM_BCUDA(cudaMemcpyAsync(B.has_prev, izero.data(), i1, cudaMemcpyHostToDevice, s), "has_prev");
     LBM_BCUDA(cudaMemcpyAsync(B.active, ones.data(), i1, cudaMemcpyHostToDevice, s), "active");
     LBM_BCUDA(cudaMemcpyAsync(B.spread, izero.data(), i1, cudaMemcpyHostToDevice, s), "spread");
@@ -568,7 +567,7 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out)
     const size_t fbytes = (size_t)b->total_elems * elem_bytes(b->storage);
     void* f_save = balloc(b, fbytes);
     const int n = b->bub.nb;
-    const size_t bub_bytes = (size_t)n * (sizeof(double) * 15 + sizeof(int) * 4 + sizeof(BubbleRec));
+    const size_t bub_bytes = (size_t)n * (sizeof(float) * 18 + sizeof(int) * 4 + sizeof(BubbleRec));
     const size_t bin_bytes = sizeof(int) * ((size_t)b->small.T * 2 + 2 * SMALL_MAX_PAIRS + 1);
     char* aux = (char*)balloc(b, bub_bytes + bin_bytes + 16);
     if (!f_save || !aux) {
@@ -580,9 +579,10 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out)
     const BubbleDev& B = b->bub;
     const SmallBins& sb = b->small;
     const Blob blobs[] = {
-        {B.x, sizeof(double) * 3 * (size_t)n}, {B.u, sizeof(double) * 3 * (size_t)n},
-        {B.ulprev, sizeof(double) * 3 * (size_t)n}, {B.ul, sizeof(double) * 3 * (size_t)n},
-        {B.psi, sizeof(double) * 3 * (size_t)n}, {B.has_prev, sizeof(int) * (size_t)n},
+        {B.xh, sizeof(float) * 3 * (size_t)n}, {B.xl, sizeof(float) * 3 * (size_t)n},
+        {B.u, sizeof(float) * 3 * (size_t)n}, {B.ulprev, sizeof(float) * 3 * (size_t)n},
+        {B.ul, sizeof(float) * 3 * (size_t)n}, {B.psi, sizeof(float) * 3 * (size_t)n},
+        {B.has_prev, sizeof(int) * (size_t)n},
         {B.active, sizeof(int) * (size_t)n}, {B.spread, sizeof(int) * (size_t)n},
         {B.cell, sizeof(int) * (size_t)n}, {B.rec, sizeof(BubbleRec) * (size_t)n},
         {sb.start, sizeof(int) * (size_t)sb.T}, {sb.count, sizeof(int) * (size_t)sb.T},
@@ -699,11 +699,7 @@ int lbm_batch_get_bubbles(lbm_batch* b, int cap, int* n, double* pos3, double* v
     const int k = nb < cap ? nb : cap;
     if (k == 0) return LBM_OK;
     cudaStream_t s = b->stream;
-    const size_t v3 = sizeof(double) * 3 * (size_t)k;
-    if (pos3) LBM_BCUDA(cudaMemcpyAsync(pos3, b->bub.x, v3, cudaMemcpyDeviceToHost, s), "pos");
-    if (vel3) LBM_BCUDA(cudaMemcpyAsync(vel3, b->bub.u, v3, cudaMemcpyDeviceToHost, s), "vel");
-    if (ul3) LBM_BCUDA(cudaMemcpyAsync(ul3, b->bub.ul, v3, cudaMemcpyDeviceToHost, s), "ul");
-    if (psi3) LBM_BCUDA(cudaMemcpyAsync(psi3, b->bub.psi, v3, cudaMemcpyDeviceToHost, s), "psi");
+    LBM_BCUDA(download_bubble_state(b->bub, k, pos3, vel3, ul3, psi3, s), "bubbles");
     if (active)
         LBM_BCUDA(cudaMemcpyAsync(active, b->bub.active, sizeof(int) * (size_t)k,
                                   cudaMemcpyDeviceToHost, s), "active");

@@ -15,6 +15,7 @@
 //                    moments and FP64 totals.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "lbm_device.cuh"
 
@@ -23,18 +24,6 @@ namespace lbm {
 // ---------------------------------------------------------------------------
 // Bubble update
 // ---------------------------------------------------------------------------
-
-// Window normalisation along one axis: the integral of the mapping over the
-// in-box part of [-n, n] (without 15/16); the full 16/15 on a periodic axis.
-__device__ __forceinline__ float axis_norm(double xa, float inv_n, int L, bool periodic) {
-    if (periodic) return 16.0f / 15.0f;
-    const float lo = (float)(-xa) * inv_n, hi = (float)((double)L - xa) * inv_n;
-    const float a = fmaxf(lo, -1.0f), b = fminf(hi, 1.0f);
-    if (!(b > a)) return 0.0f;
-    const float a2 = a * a, b2 = b * b, ab = a * b;
-    const float p4 = b2 * b2 + b2 * ab + ab * ab + ab * a2 + a2 * a2;
-    return (b - a) * (p4 * 0.2f - (b2 + ab + a2) * (2.0f / 3.0f) + 1.0f);
-}
 
 // ---- positions in two floats ------------------------------------------------
 // A position is carried through the sub-steps as hi + lo, two floats with
@@ -75,7 +64,23 @@ __device__ __forceinline__ int f2_floor(F2 a, float& frac) {
     return (int)f;
 }
 
-// axis_norm of a two-float coordinate.
+// floor and ceil of hi + lo.  With |lo| <= ulp(hi)/2 the sum can cross an
+// integer only when hi itself is one, so lo decides only then.
+__device__ __forceinline__ int f2_floor_int(F2 a) {
+    float f = floorf(a.h);
+    if (f == a.h && a.l < 0.0f) f -= 1.0f;
+    return (int)f;
+}
+
+__device__ __forceinline__ int f2_ceil_int(F2 a) {
+    float c = ceilf(a.h);
+    if (c == a.h && a.l > 0.0f) c += 1.0f;
+    return (int)c;
+}
+
+// Window normalisation along one axis: the integral of the mapping over the
+// in-box part of [-n, n] (without 15/16), for the two-float coordinate xa; the
+// full 16/15 on a periodic axis.
 __device__ __forceinline__ float axis_norm2(F2 xa, float inv_n, int L, bool periodic) {
     if (periodic) return 16.0f / 15.0f;
     const float lo = (-xa.h - xa.l) * inv_n, hi = (((float)L - xa.h) - xa.l) * inv_n;
@@ -151,47 +156,51 @@ enum { BUBBLE_LIVE = 0, BUBBLE_IDLE = 1, BUBBLE_NONFINITE = 2 };
 // the start of the kernel (the integration part only by the thread that will
 // integrate, `full`).
 struct BubbleIn {
-    double x[3], n;
+    F2 x[3];
     BubbleK k;
-    double u[3], ulprev[3];
+    float u[3], ulprev[3];
     int active, has_prev;
 };
 
 __device__ __forceinline__ void load_bubble(const BubbleDev& B, int b, bool full, BubbleIn& in) {
     in.active = B.active[b];
-    for (int a = 0; a < 3; ++a) in.x[a] = B.x[3 * b + a];
-    in.n = B.n[b];
+    for (int a = 0; a < 3; ++a) in.x[a] = F2{B.xh[3 * b + a], B.xl[3 * b + a]};
     in.k = B.k[b];
     in.has_prev = full ? B.has_prev[b] : 0;
     for (int a = 0; a < 3; ++a) {
-        in.u[a] = full ? B.u[3 * b + a] : 0.0;
-        in.ulprev[a] = full ? B.ulprev[3 * b + a] : 0.0;
+        in.u[a] = full ? B.u[3 * b + a] : 0.0f;
+        in.ulprev[a] = full ? B.ulprev[3 * b + a] : 0.0f;
     }
 }
 
+// First and last cell of the support (x - n, x + n) on one axis, before
+// clipping: floor(x - n) and ceil(x + n) - 1, from the two-float centre and
+// half-width.
+__device__ __forceinline__ void support_cells(F2 x, float nh, float nl, int& lo, int& hi) {
+    lo = f2_floor_int(f2_add(x, -nh, -nl));
+    hi = f2_ceil_int(f2_add(x, nh, nl)) - 1;
+}
+
 __device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w) {
-    const double* xb = in.x;
-    const double n = in.n;
+    const F2* xb = in.x;
     const float inv_n = in.k.inv_nf;
     if (!in.active) return BUBBLE_IDLE;
     const int L[3] = {g.nx, g.ny, g.nz};
     // A non-finite centre can only come from an unstable liquid.
-    if (!(isfinite(xb[0]) && isfinite(xb[1]) && isfinite(xb[2]))) return BUBBLE_NONFINITE;
+    if (!(isfinite(xb[0].h) && isfinite(xb[1].h) && isfinite(xb[2].h))) return BUBBLE_NONFINITE;
     w.norm = 1.0f;
     for (int a = 0; a < 3; ++a) {
         const bool periodic = !(g.walls & (1u << (2 * a)));
-        int l = (int)floor(xb[a] - n);
-        int h = (int)ceil(xb[a] + n) - 1;
+        int l, h;
+        support_cells(xb[a], in.k.nh, in.k.nl, l, h);
         if (!periodic) {
             l = max(l, 0);
             h = min(h, L[a] - 1);
         }
         w.lo[a] = l;
         w.cnt[a] = min(max(h - l + 1, 0), WINDOW_CELLS_MAX);
-        const double fl = floor(xb[a]);
-        w.anc[a] = (int)fl;
-        w.fr[a] = (float)(xb[a] - fl);
-        w.norm *= axis_norm(xb[a], inv_n, L[a], periodic);
+        w.anc[a] = f2_floor(xb[a], w.fr[a]);
+        w.norm *= axis_norm2(xb[a], inv_n, L[a], periodic);
     }
     w.M = w.cnt[0] * w.cnt[1] * w.cnt[2];
     return BUBBLE_LIVE;
@@ -311,21 +320,21 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
         return;
     }
     const int L[3] = {g.nx, g.ny, g.nz};
-    F2 xb[3] = {f2_from(in.x[0]), f2_from(in.x[1]), f2_from(in.x[2])};
+    F2 xb[3] = {in.x[0], in.x[1], in.x[2]};
     const BubbleK& K = in.k;
     const float inv_norm = 1.0f / w.norm;
     const float ul[3] = {ax * inv_norm, ay * inv_norm, az * inv_norm};
     float fvm[3] = {0.0f, 0.0f, 0.0f};   // C_A rho_l V_b D_t u_l
     if (in.has_prev) {
-        for (int a = 0; a < 3; ++a) fvm[a] = K.fvm_coef_dt * (ul[a] - (float)in.ulprev[a]);
+        for (int a = 0; a < 3; ++a) fvm[a] = K.fvm_coef_dt * (ul[a] - in.ulprev[a]);
     }
-    const F2 dt_b = f2_from(bc.dt_b);
-    const F2 r = f2_from(K.r);
+    const F2 dt_b{bc.dt_bh, bc.dt_bl};
+    const F2 r{K.rh, K.rl};
     F2 top[3];   // L - r
     for (int a = 0; a < 3; ++a) top[a] = f2_add(F2{(float)L[a], 0.0f}, -r.h, -r.l);
     const float sn_coeff = (float)bc.sn_coeff, sn_exp = (float)bc.sn_exp;
     const float fb[3] = {0.0f, 0.0f, K.fb};
-    float u[3] = {(float)in.u[0], (float)in.u[1], (float)in.u[2]};
+    float u[3] = {in.u[0], in.u[1], in.u[2]};
     float fd_sum[3] = {0.0f, 0.0f, 0.0f};
     bool wrap_far = false;   // a periodic coordinate left [-L, 2L): folded through FP64 below
     for (int k = 0; k < bc.substeps; ++k) {
@@ -373,7 +382,8 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
     const float inv_sub = 1.0f / (float)bc.substeps;
     for (int a = 0; a < 3; ++a) {
         psi[a] = -fd_sum[a] * inv_sub;
-        B.x[3 * b + a] = f2_to(xb[a]);
+        B.xh[3 * b + a] = xb[a].h;
+        B.xl[3 * b + a] = xb[a].l;
         B.u[3 * b + a] = u[a];
         B.ul[3 * b + a] = ul[a];
         B.ulprev[3 * b + a] = ul[a];
@@ -496,6 +506,8 @@ __global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_fac
     BubbleK K;
     K.inv_nf = (float)(1.0 / B.n[b]);
     K.r = r;
+    split_f2(r, K.rh, K.rl);
+    split_f2(B.n[b], K.nh, K.nl);
     K.kdt = (float)(bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol));
     K.fb = (float)((bc.rho_l - bc.rho_b) * vol * bc.g);
     K.drag_pref = (float)(0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale);
@@ -519,10 +531,8 @@ cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, c
 // ---------------------------------------------------------------------------
 
 // Tiles of one axis holding at least one window cell, ascending.
-__device__ int axis_tiles(double xa, double n, int L, bool periodic, int T,
-                          int out[MAX_AXIS_TILES]) {
-    int lo = (int)floor(xa - n);
-    int hi = (int)ceil(xa + n) - 1;
+// lo, hi: the first and last support cell, floor(x - n) and ceil(x + n) - 1.
+__device__ int axis_tiles(int lo, int hi, int L, bool periodic, int T, int out[MAX_AXIS_TILES]) {
     int cnt = 0;
     if (!periodic) {
         lo = max(lo, 0);
@@ -555,9 +565,18 @@ __global__ void k_bin(Geo g, BubbleDev B, Bins bins, const int* __restrict__ sel
     const int T[3] = {TX, TY, TZ};
     int tl[3][MAX_AXIS_TILES];
     int nt[3];
-    const double n = B.n[b];
-    for (int a = 0; a < 3; ++a)
-        nt[a] = axis_tiles(B.x[3 * b + a], n, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
+    for (int a = 0; a < 3; ++a) {
+        int lo, hi;
+        if (B.x) {   // FP64 centres from the caller (binning without a context)
+            const double xa = B.x[3 * b + a], n = B.n[b];
+            lo = (int)floor(xa - n);
+            hi = (int)ceil(xa + n) - 1;
+        } else {
+            const BubbleK& K = B.k[b];
+            support_cells(F2{B.xh[3 * b + a], B.xl[3 * b + a]}, K.nh, K.nl, lo, hi);
+        }
+        nt[a] = axis_tiles(lo, hi, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
+    }
     for (int iz = 0; iz < nt[2]; ++iz)
         for (int iy = 0; iy < nt[1]; ++iy)
             for (int ix = 0; ix < nt[0]; ++ix) {
@@ -718,10 +737,12 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
         const int L[3] = {gb.nx, gb.ny, gb.nz};
         int tl[3][MAX_AXIS_TILES];
         int ntl[3];
-        const double n = __ldcg(B.n + b);
-        for (int a = 0; a < 3; ++a)
-            ntl[a] = axis_tiles(__ldcg(B.x + 3 * b + a), n, L[a], !(gb.walls & (1u << (2 * a))),
-                                T[a], tl[a]);
+        const float nh = __ldcg(&B.k[b].nh), nl = __ldcg(&B.k[b].nl);
+        for (int a = 0; a < 3; ++a) {
+            int lo, hi;
+            support_cells(F2{__ldcg(B.xh + 3 * b + a), __ldcg(B.xl + 3 * b + a)}, nh, nl, lo, hi);
+            ntl[a] = axis_tiles(lo, hi, L[a], !(gb.walls & (1u << (2 * a))), T[a], tl[a]);
+        }
         for (int iz = 0; iz < ntl[2]; ++iz)
             for (int iy = 0; iy < ntl[1]; ++iy)
                 for (int ix = 0; ix < ntl[0]; ++ix) {
@@ -920,6 +941,8 @@ __global__ void k_bubble_constants_batch(BubbleDev B, BubbleConst bc, const doub
     BubbleK K;
     K.inv_nf = (float)(1.0 / B.n[b]);
     K.r = r;
+    split_f2(r, K.rh, K.rl);
+    split_f2(B.n[b], K.nh, K.nl);
     K.kdt = (float)(c.dt_b / ((c.rho_b + c.c_am * c.rho_l) * vol));
     K.fb = (float)((c.rho_l - c.rho_b) * vol * c.g);
     K.drag_pref = (float)(0.5 * c.rho_l * M_PI * r * r * c.drag_scale);
@@ -1157,6 +1180,57 @@ cudaError_t launch_totals(int storage, const void* f, const Geo& g, const Collid
     }
     k_totals_final<<<1, 32, 0, st>>>(partials, npartials, (double)g.S * (double)cp.rho0, out4);
     return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Host conversion of the bubble state between the C ABI's FP64 arrays and the
+// device format (two-float centres, FP32 velocities).
+// ---------------------------------------------------------------------------
+cudaError_t upload_bubble_state(const BubbleDev& B, int n, const double* pos3, const double* vel3,
+                                cudaStream_t st) {
+    const size_t m = 3 * (size_t)n;
+    std::vector<float> xh(m), xl(m), u(m, 0.0f), zeros(m, 0.0f);
+    for (size_t i = 0; i < m; ++i) {
+        split_f2(pos3[i], xh[i], xl[i]);
+        if (vel3) u[i] = (float)vel3[i];
+    }
+    const size_t bytes = sizeof(float) * m;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(B.xh, xh.data(), bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(B.xl, xl.data(), bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(B.u, u.data(), bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(B.ulprev, zeros.data(), bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(B.ul, zeros.data(), bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(B.psi, zeros.data(), bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    // The staging vectors go out of scope: let the copies finish first.
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t download_bubble_state(const BubbleDev& B, int k, double* pos3, double* vel3,
+                                  double* ul3, double* psi3, cudaStream_t st) {
+    const size_t m = 3 * (size_t)k, bytes = sizeof(float) * m;
+    std::vector<float> xh(pos3 ? m : 0), xl(pos3 ? m : 0), u(vel3 ? m : 0), ul(ul3 ? m : 0),
+        psi(psi3 ? m : 0);
+    cudaError_t e;
+    if (pos3) {
+        if ((e = cudaMemcpyAsync(xh.data(), B.xh, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(xl.data(), B.xl, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    }
+    if (vel3 && (e = cudaMemcpyAsync(u.data(), B.u, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if (ul3 && (e = cudaMemcpyAsync(ul.data(), B.ul, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if (psi3 && (e = cudaMemcpyAsync(psi.data(), B.psi, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    for (size_t i = 0; i < m; ++i) {
+        if (pos3) pos3[i] = join_f2(xh[i], xl[i]);
+        if (vel3) vel3[i] = u[i];
+        if (ul3) ul3[i] = ul[i];
+        if (psi3) psi3[i] = psi[i];
+    }
+    return cudaSuccess;
 }
 
 }  // namespace lbm

@@ -95,6 +95,7 @@ BubbleConst bubble_const(const lbm_ctx* c) {
     bc.nu = (2.0 / c->omega - 1.0) / 6.0;     // Eq. 9
     bc.dt_l = 1.0;
     bc.dt_b = 1.0 / c->p.substeps;            // Table 2: dt_b = dt_l / substeps
+    split_f2(bc.dt_b, bc.dt_bh, bc.dt_bl);
     bc.substeps = c->p.substeps;
     return bc;
 }
@@ -151,7 +152,7 @@ int axis_tile_bound(double n, int T) {
 void free_bubbles(lbm_ctx* c) {
     BubbleDev& b = c->bub;
     SmallBins& sb = c->small;
-    void* ptrs[] = {b.k, b.x, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
+    void* ptrs[] = {b.k, b.xh, b.xl, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
                     b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items, sb.prev_tiles,
                     sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, c->mom};
     for (void* p : ptrs) dfree(c, p);
@@ -465,15 +466,16 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     if (n == 0) return LBM_OK;
 
     BubbleDev& B = c->bub;
-    const size_t v3 = sizeof(double) * 3 * (size_t)n, v1 = sizeof(double) * (size_t)n,
+    const size_t f3 = sizeof(float) * 3 * (size_t)n, v1 = sizeof(double) * (size_t)n,
                  i1 = sizeof(int) * (size_t)n;
-    B.x = (double*)dalloc(c, v3);
-    B.u = (double*)dalloc(c, v3);
+    B.xh = (float*)dalloc(c, f3);
+    B.xl = (float*)dalloc(c, f3);
+    B.u = (float*)dalloc(c, f3);
     B.d = (double*)dalloc(c, v1);
     B.n = (double*)dalloc(c, v1);
-    B.ulprev = (double*)dalloc(c, v3);
-    B.ul = (double*)dalloc(c, v3);
-    B.psi = (double*)dalloc(c, v3);
+    B.ulprev = (float*)dalloc(c, f3);
+    B.ul = (float*)dalloc(c, f3);
+    B.psi = (float*)dalloc(c, f3);
     B.has_prev = (int*)dalloc(c, i1);
     B.active = (int*)dalloc(c, i1);
     B.spread = (int*)dalloc(c, i1);
@@ -514,7 +516,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         c->mom = (float*)dalloc(c, sizeof(float) * 3 * (size_t)c->nx * c->ny * c->nz);
         lists_ok = c->bins.items != nullptr && c->mom != nullptr;
     }
-    if (!B.k || !B.x || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
+    if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
         !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
         free_bubbles(c);
         return fail(c, LBM_ERR_ALLOC, "bubble state");
@@ -528,18 +530,13 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         LBM_CUDA(cudaMemsetAsync(sb.arrive, 0, sizeof(int) * (size_t)n, c->stream), "arrive");
     }
     B.nb = n;
-    std::vector<double> hn(n), zeros(3 * (size_t)n, 0.0);
+    std::vector<double> hn(n);
     for (int b = 0; b < n; ++b) hn[b] = c->p.width_factor * diam[b];
     std::vector<int> ones(n, 1), izero(n, 0), minus(n, -1);
     cudaStream_t s = c->stream;
-    LBM_CUDA(cudaMemcpyAsync(B.x, pos3, v3, cudaMemcpyHostToDevice, s), "upload pos");
-    LBM_CUDA(cudaMemcpyAsync(B.u, vel3 ? vel3 : zeros.data(), v3, cudaMemcpyHostToDevice, s),
-             "upload vel");
+    LBM_CUDA(upload_bubble_state(B, n, pos3, vel3, s), "upload bubbles");
     LBM_CUDA(cudaMemcpyAsync(B.d, diam, v1, cudaMemcpyHostToDevice, s), "upload diam");
     LBM_CUDA(cudaMemcpyAsync(B.n, hn.data(), v1, cudaMemcpyHostToDevice, s), "upload n");
-    LBM_CUDA(cudaMemcpyAsync(B.ulprev, zeros.data(), v3, cudaMemcpyHostToDevice, s), "ulprev");
-    LBM_CUDA(cudaMemcpyAsync(B.ul, zeros.data(), v3, cudaMemcpyHostToDevice, s), "ul");
-    LBM_CUDA(cudaMemcpyAsync(B.psi, zeros.data(), v3, cudaMemcpyHostToDevice, s), "psi");
     LBM_CUDA(cudaMemcpyAsync(B.has_prev, izero.data(), i1, cudaMemcpyHostToDevice, s), "has_prev");
     LBM_CUDA(cudaMemcpyAsync(B.active, ones.data(), i1, cudaMemcpyHostToDevice, s), "active");
     LBM_CUDA(cudaMemcpyAsync(B.spread, izero.data(), i1, cudaMemcpyHostToDevice, s), "spread");
@@ -599,11 +596,7 @@ int lbm_get_bubbles(lbm_ctx* c, int cap, int* n, double* pos3, double* vel3, dou
     const int k = nb < cap ? nb : cap;
     if (k == 0) return LBM_OK;
     cudaStream_t s = c->stream;
-    const size_t v3 = sizeof(double) * 3 * (size_t)k;
-    if (pos3) LBM_CUDA(cudaMemcpyAsync(pos3, c->bub.x, v3, cudaMemcpyDeviceToHost, s), "pos");
-    if (vel3) LBM_CUDA(cudaMemcpyAsync(vel3, c->bub.u, v3, cudaMemcpyDeviceToHost, s), "vel");
-    if (ul3) LBM_CUDA(cudaMemcpyAsync(ul3, c->bub.ul, v3, cudaMemcpyDeviceToHost, s), "ul");
-    if (psi3) LBM_CUDA(cudaMemcpyAsync(psi3, c->bub.psi, v3, cudaMemcpyDeviceToHost, s), "psi");
+    LBM_CUDA(download_bubble_state(c->bub, k, pos3, vel3, ul3, psi3, s), "get bubbles");
     if (active)
         LBM_CUDA(cudaMemcpyAsync(active, c->bub.active, sizeof(int) * (size_t)k,
                                  cudaMemcpyDeviceToHost, s), "active");

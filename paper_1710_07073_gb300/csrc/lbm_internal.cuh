@@ -76,9 +76,13 @@ struct __align__(16) BubbleRec {
 
 // Per-bubble constants of the closures (Table 1) and of the mapping window,
 // derived from the diameter and the parameters whenever either changes.
+// Lengths used against positions come as two floats (hi + lo, |lo| <=
+// ulp(hi)/2), like the positions themselves.
 struct BubbleK {
-    double r;           // d / 2 (wall tests on the FP64 position)
-    float inv_nf;       // 1 / n, n = width_factor * d
+    double r;           // d / 2
+    float rh, rl;       // r as two floats (wall tests)
+    float nh, nl;       // n = width_factor * d as two floats (window bounds)
+    float inv_nf;       // 1 / n
     float kdt;          // dt_b / m_eff, m_eff = (rho_b + C_A rho_l) V_b
     float fb;           // (rho_l - rho_b) V_b g
     float drag_pref;    // 1/2 rho_l pi r^2 * drag_scale
@@ -89,16 +93,24 @@ struct BubbleK {
     float eo_term;      // 8/3 Eo / (Eo + 4)
 };
 
+// Bubble state on the device.  A context keeps the centres as two floats
+// (xh + xl: about 48 significant bits, enough for the 1e-5 moves of a
+// sub-step at positions of hundreds) and velocities, u_l and psi in FP32, so
+// that the per-bubble update runs on the FP32 pipe; the host converts from
+// and to the FP64 arrays of the C ABI.  `x` (FP64 centres) is set only by
+// callers that bin FP64 input directly and is null in a context.
 struct BubbleDev {
     int nb;
     BubbleK* k;       // [nb]
-    double* x;        // [3*nb] interleaved position
-    double* u;        // [3*nb] velocity
+    double* x;        // [3*nb] FP64 centres (binning of caller input only)
+    float* xh;        // [3*nb] interleaved centre, high part
+    float* xl;        // [3*nb] low part
+    float* u;         // [3*nb] velocity
     double* d;        // [nb] diameter
     double* n;        // [nb] window half-width
-    double* ulprev;   // [3*nb] interpolated liquid velocity of the previous step
-    double* ul;       // [3*nb] interpolated liquid velocity of the last step
-    double* psi;      // [3*nb] reaction of the last step
+    float* ulprev;    // [3*nb] interpolated liquid velocity of the previous step
+    float* ul;        // [3*nb] interpolated liquid velocity of the last step
+    float* psi;       // [3*nb] reaction of the last step
     int* has_prev;    // [nb]
     int* active;      // [nb]
     int* spread;      // [nb] 1 if the bubble spread in the last step
@@ -108,8 +120,16 @@ struct BubbleDev {
 
 struct BubbleConst {
     double g, rho_l, rho_b, sigma, c_am, drag_scale, sn_coeff, sn_exp, nu, dt_b, dt_l;
+    float dt_bh, dt_bl;   // dt_b as two floats
     int substeps;
 };
+
+// A double as two floats (h = v rounded, l = the rest rounded) and back.
+__host__ __device__ inline void split_f2(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+__host__ __device__ inline double join_f2(float h, float l) { return (double)h + (double)l; }
 
 struct Bins {
     int T;             // tiles
@@ -181,6 +201,15 @@ cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const Colli
 // 256-node chunk of the largest window.
 int window_parts(double max_half_width);
 cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st);
+// Host: FP64 centres and velocities of n bubbles into the device state
+// (vel3 may be null: at rest); u_l, its previous value and psi are zeroed.
+// Synchronises the stream.
+cudaError_t upload_bubble_state(const BubbleDev& B, int n, const double* pos3, const double* vel3,
+                                cudaStream_t st);
+// Host: the first k bubbles' state as FP64 arrays (null pointers are
+// skipped).  Synchronises the stream.
+cudaError_t download_bubble_state(const BubbleDev& B, int k, double* pos3, double* vel3,
+                                  double* ul3, double* psi3, cudaStream_t st);
 // Many bubbles: Eq. 10 velocity of the covered tiles into mom[3*S], then one
 // warp per bubble interpolating from it.  tile_count: the binning of the
 // current centres (count > 0 marks a covered tile).
