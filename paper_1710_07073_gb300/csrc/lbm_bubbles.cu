@@ -256,18 +256,35 @@ __device__ __forceinline__ void chunk_sum2(const typename Store<ST>::T* __restri
     }
 }
 
-// Eq. 20 partial sums over the window nodes tid, tid + nt, ... from the
-// precomputed Eq. 10 velocities `mom` (three planes of S floats).
-__device__ __forceinline__ void window_sum_mom(const float* __restrict__ mom, const Geo& g,
-                                               const Window& w, float inv_n, int tid, int nt,
-                                               float& ax, float& ay, float& az) {
-    for (int m = tid; m < w.M; m += nt) {
-        int iw, jw, kw;
-        const float wt = window_node(g, w, inv_n, m, iw, jw, kw);
-        const size_t node = (size_t)site_index(g, iw, jw, kw);
-        ax = fmaf(wt, __ldg(mom + node), ax);
-        ay = fmaf(wt, __ldg(mom + (size_t)g.S + node), ay);
-        az = fmaf(wt, __ldg(mom + 2 * (size_t)g.S + node), az);
+// A window coordinate wrapped into [0, L) (windows are narrower than the box).
+__device__ __forceinline__ int wrap_axis(int i, int L) {
+    return i < 0 ? i + L : (i >= L ? i - L : i);
+}
+
+// Eq. 20 partial sums over the window's x-rows (y, z) = tid, tid + nt, ...
+// from the precomputed Eq. 10 velocities `mom` (three planes of S floats).
+// Per row the y and z weights are formed once; along the row only the x
+// weight changes.
+__device__ __forceinline__ void window_sum_rows(const float* __restrict__ mom, const Geo& g,
+                                                const Window& w, float inv_n, int tid, int nt,
+                                                float& ax, float& ay, float& az) {
+    const float hh = 0.5f * inv_n;
+    const int rows = w.cnt[1] * w.cnt[2];
+    const size_t S = (size_t)g.S;
+    for (int r = tid; r < rows; r += nt) {
+        const int iz = r / w.cnt[1], iy = r - iz * w.cnt[1];
+        const int j = w.lo[1] + iy, k = w.lo[2] + iz;
+        const float wyz = cell_poly(((float)(j - w.anc[1]) + 0.5f - w.fr[1]) * inv_n, hh) *
+                          cell_poly(((float)(k - w.anc[2]) + 0.5f - w.fr[2]) * inv_n, hh);
+        const size_t row = ((size_t)wrap_axis(k, g.nz) * g.ny + wrap_axis(j, g.ny)) * g.nx;
+        for (int ix = 0; ix < w.cnt[0]; ++ix) {
+            const int i = w.lo[0] + ix;
+            const float wt = cell_poly(((float)(i - w.anc[0]) + 0.5f - w.fr[0]) * inv_n, hh) * wyz;
+            const size_t node = row + (size_t)wrap_axis(i, g.nx);
+            ax = fmaf(wt, __ldg(mom + node), ax);
+            ay = fmaf(wt, __ldg(mom + S + node), ay);
+            az = fmaf(wt, __ldg(mom + 2 * S + node), az);
+        }
     }
 }
 
@@ -413,23 +430,51 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
 
 // Many bubbles: one warp per bubble, window velocities from the moments of
 // the covered tiles.
-constexpr int WARP_BUBBLE_THREADS = 128;   // four bubbles per CTA
+constexpr int WARP_BUBBLE_THREADS = 128;   // four warps, 32 bubbles each
 
+// Each warp serves 32 consecutive bubbles.  Lane k loads bubble 32 w + k and
+// sets up its window; the warp then sums the 32 windows one after another
+// (each window broadcast from its lane by shuffles), the sum ending with the
+// bubble's own lane; finally all lanes run their bubbles' tails at once.
 template <int ST>
 __global__ void __launch_bounds__(WARP_BUBBLE_THREADS)
 k_bubbles_warp(const typename Store<ST>::T* __restrict__ f, const float* __restrict__ mom, Geo g,
                CollideParams cp, BubbleDev B, BubbleConst bc, int* __restrict__ flag) {
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (b >= B.nb) return;
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const int b0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
+    if (b0 >= B.nb) return;   // uniform over the warp
+    const int b = b0 + lane;
+    const bool have = b < B.nb;
     BubbleIn in;
-    load_bubble(B, b, lane == 0, in);
-    Window w;
-    const int state = bubble_window(g, in, w);
-    float ax = 0.0f, ay = 0.0f, az = 0.0f;
-    if (state == BUBBLE_LIVE) window_sum_mom(mom, g, w, in.k.inv_nf, lane, 32, ax, ay, az);
-    warp_sum3(ax, ay, az);
-    if (lane == 0) bubble_tail(g, B, bc, flag, b, state, w, ax, ay, az, in);
+    Window w{};
+    int state = BUBBLE_IDLE;
+    if (have) {
+        load_bubble(B, b, true, in);
+        state = bubble_window(g, in, w);
+    }
+    const float inv_n = have ? in.k.inv_nf : 0.0f;
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+    for (int j = 0; j < 32; ++j) {
+        if (__shfl_sync(full, state, j) != BUBBLE_LIVE) continue;   // uniform
+        Window wj;
+        for (int a = 0; a < 3; ++a) {
+            wj.lo[a] = __shfl_sync(full, w.lo[a], j);
+            wj.cnt[a] = __shfl_sync(full, w.cnt[a], j);
+            wj.anc[a] = __shfl_sync(full, w.anc[a], j);
+            wj.fr[a] = __shfl_sync(full, w.fr[a], j);
+        }
+        const float inv_nj = __shfl_sync(full, inv_n, j);
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        window_sum_rows(mom, g, wj, inv_nj, lane, 32, ax, ay, az);
+        warp_sum3(ax, ay, az);
+        if (lane == j) {
+            sx = ax;
+            sy = ay;
+            sz = az;
+        }
+    }
+    if (have) bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz, in);
 }
 
 // Eq. 10 velocity of every node of the tiles some bubble window covers
@@ -473,7 +518,7 @@ cudaError_t launch_bubbles_many(int storage, const void* f, float* mom, const Ge
                                 const int* tile_count, int* flag, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
     const int T = g.ntx * g.nty * g.ntz;
-    const int blocks = (b.nb * 32 + WARP_BUBBLE_THREADS - 1) / WARP_BUBBLE_THREADS;
+    const int blocks = (b.nb + WARP_BUBBLE_THREADS - 1) / WARP_BUBBLE_THREADS;   // a bubble per thread
     dim3 tb(TX, TY);
     switch (storage) {
         case 0:
