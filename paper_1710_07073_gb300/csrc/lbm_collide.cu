@@ -258,6 +258,9 @@ template <int ST> struct PairOccupancy {
     static constexpr int kMinBlocks = ST == 0 ? 6 : LBM_PAIR_MINB_16;
 };
 constexpr int PX = TX / 2;   // threads along x
+// Bubbles staged per pass of the sweep's force gather (records and per-axis
+// weight tables in shared memory).
+constexpr int FORCE_CHUNK = 32;
 constexpr int PZ = LBM_PAIR_PZ;   // z-planes per CTA (divides TZ)
 static_assert(TZ % PZ == 0, "a CTA's z-planes must lie in one binning tile");
 
@@ -292,6 +295,19 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// Cell integral of the mapping along one axis for lattice coordinate c, with
+// the record's anchor cell `anc` and offset `fr` (Eq. 19), wrapped on a
+// periodic axis of length L as in add_bubble_force_pair.
+__device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc, float fr, int L,
+                                             bool periodic) {
+    float rc = (float)(c - anc) + 0.5f - fr;
+    if (periodic) {
+        if (rc > 0.5f * L) rc -= (float)L;
+        else if (rc < -0.5f * L) rc += (float)L;
+    }
+    return cell_poly(rc * r.inv_n, r.h);
+}
 
 // Force of one bubble record on the pair (x0, x0 + 1) at (y, z), Eq. 19 and 21.
 __device__ __forceinline__ void add_bubble_force_pair(const BubbleRec& r, const Geo& g, int x0,
@@ -388,9 +404,8 @@ __device__ __forceinline__ RelaxK relax_k(float K, float2 base, float2 rho) {
     return RelaxK{mul2(f2(K), base), mul2(f2(4.5f * K), rho), mul2(f2(3.0f * K), rho)};
 }
 
-// Where a collided pair goes: the pair kernel stores it (2-wide, plane J at
-// site0); the four-node kernel keeps the first pair packed and stores both
-// pairs together.
+// Where a collided pair goes: the pair kernels store it 2-wide in plane J at
+// site0.
 template <int ST>
 struct PairStore {
     typename Store<ST>::T* fout;
@@ -483,10 +498,72 @@ __device__ __forceinline__ void collide_pair(Sink& sink, const float2 rv[Q], flo
 #undef LBM_PAIR2
 }
 
+// Eq. 21 at the pair (x0, x0 + 1), (y, z) of a block whose tile lists n_t > 0
+// bubbles, for long tile lists (many bubbles).  Every thread of the CTA calls
+// it (it synchronises the CTA).
+struct Force2 {
+    float2 x, y, z;
+};
+
+__device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __restrict__ tile_start,
+                                                 const int* __restrict__ items, int cap,
+                                                 const BubbleRec* __restrict__ recs, int nb,
+                                                 int n_t, int bx, int by, int bz, int x0, int y,
+                                                 int z, bool active, BubbleRec* srec) {
+    float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
+    // Chunks of FB bubbles: the CTA first tabulates each bubble's per-axis
+    // cell integrals over the block (TX columns, TY rows, PZ planes), then
+    // every node forms wx (wy wz) from the tables.  Same products, zero test
+    // and order as add_bubble_force_pair.
+    constexpr int FB = FORCE_CHUNK, NAX = TX + TY + PZ;
+    __shared__ float s_w[FB][NAX];   // x: [0, TX), y: [TX, TX + TY), z: the rest
+    const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
+    const int beg = tile_start[t];
+    const int end = min(beg + n_t, cap);
+    const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
+    constexpr int NT = PX * TY * PZ;
+    const int xb0 = bx * TX, yb0 = by * TY, zb0 = bz * PZ;
+    for (int c0 = beg; c0 < end; c0 += FB) {
+        const int cnt = min(FB, end - c0);
+        __syncthreads();
+        if (tid < cnt) {
+            const int id = items[c0 + tid];
+            if (id >= 0 && id < nb) srec[tid] = recs[id];
+            else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
+        __syncthreads();
+        for (int e = tid; e < cnt * NAX; e += NT) {
+            const int k = e / NAX, q = e - k * NAX;
+            const BubbleRec& r = srec[k];
+            if (q < TX)
+                s_w[k][q] = axis_weight(r, xb0 + q, r.ax, r.fx, g.nx, !(g.walls & 0x01));
+            else if (q < TX + TY)
+                s_w[k][q] = axis_weight(r, yb0 + q - TX, r.ay, r.fy, g.ny, !(g.walls & 0x04));
+            else
+                s_w[k][q] = axis_weight(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, !(g.walls & 0x10));
+        }
+        __syncthreads();
+        if (active) {
+            const int xi = 2 * threadIdx.x, yi = TX + threadIdx.y, zi = TX + TY + threadIdx.z;
+            for (int k = 0; k < cnt; ++k) {
+                const float wyz = s_w[k][yi] * s_w[k][zi];
+                if (wyz == 0.0f) continue;
+                const float2 wv = make_float2(s_w[k][xi] * wyz, s_w[k][xi + 1] * wyz);
+                const BubbleRec& r = srec[k];
+                Fx = fma2(wv, f2(r.px), Fx);
+                Fy = fma2(wv, f2(r.py), Fy);
+                Fz = fma2(wv, f2(r.pz), Fz);
+            }
+        }
+    }
+    __syncthreads();   // srec and s_w are reused by the CTA's next block
+    return Force2{Fx, Fy, Fz};
+}
+
 // One CTA's block of the sweep: x-pairs of 32 nodes, TY rows, PZ planes at
 // block coordinates (bx, by, bz).  `srec` is the CTA's staging of bubble
 // records; every thread of the CTA must call this with the same block.
-template <int ST>
+template <int ST, bool TAB>
 __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restrict__ fin,
                                             typename Store<ST>::T* __restrict__ fout,
                                             const Geo& g, const CollideParams& cp,
@@ -531,16 +608,21 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     // The force gather (Eq. 21) runs after the population loads are issued,
     // so the tile-list lookup does not delay them.
     float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
-    bool forced = false;   // uniform over the CTA (one tile)
-    if (n_t > 0) {
-        forced = true;
+    const bool forced = n_t > 0;   // uniform over the CTA (one tile)
+    if (forced && TAB) {
+        const Force2 F = gather_force_tab(g, tile_start, items, cap, recs, nb, n_t, bx, by, bz,
+                                          x0, y, z, active, srec);
+        Fx = F.x;
+        Fy = F.y;
+        Fz = F.z;
+    } else if (forced) {
+        // Few bubbles per tile: each node evaluates its listed bubbles directly.
         const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
         const int beg = tile_start[t];
         const int end = min(beg + n_t, cap);
         const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
-        constexpr int NT = PX * TY * PZ;
-        for (int c0 = beg; c0 < end; c0 += NT) {
-            const int cnt = min(NT, end - c0);
+        for (int c0 = beg; c0 < end; c0 += FORCE_CHUNK) {
+            const int cnt = min(FORCE_CHUNK, end - c0);
             __syncthreads();
             if (tid < cnt) {
                 const int id = items[c0 + tid];
@@ -560,16 +642,17 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     else collide_pair<ST, false>(sink, rv, Fx, Fy, Fz, cp, flag, active);
 }
 
-template <int ST>
+// TAB: the force gather of long tile lists (per-axis weight tables).
+template <int ST, bool TAB>
 __global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
 k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                       typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
                       const int* __restrict__ tile_start, const int* __restrict__ tile_count,
                       const int* __restrict__ items, int cap,
                       const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
-    __shared__ BubbleRec srec[PX * TY * PZ];
-    sweep_block<ST>(fin, fout, g, cp, tile_start, tile_count, items, cap, recs, nb, flag,
-                    blockIdx.x, blockIdx.y, blockIdx.z, srec);
+    __shared__ BubbleRec srec[FORCE_CHUNK];
+    sweep_block<ST, TAB>(fin, fout, g, cp, tile_start, tile_count, items, cap, recs, nb, flag,
+                         blockIdx.x, blockIdx.y, blockIdx.z, srec);
 }
 
 // ---------------------------------------------------------------------------
@@ -589,7 +672,7 @@ k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
                 const int* __restrict__ tile_start, const int* __restrict__ tile_count,
                 const int* __restrict__ items, int cap, const BubbleRec* __restrict__ recs,
                 int nb, int* __restrict__ flag) {
-    __shared__ BubbleRec srec[PX * TY * PZ];
+    __shared__ BubbleRec srec[FORCE_CHUNK];
     __shared__ int s_item_base[MAX_BATCH_COLUMNS + 1];
     __shared__ int s_item;
     const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
@@ -615,7 +698,7 @@ k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
         const int bz0 = (rest / col.g.nty) * depth;
         const int nbz = (col.g.nz + PZ - 1) / PZ;
         for (int bz = bz0; bz < min(bz0 + depth, nbz); ++bz)
-            sweep_block<ST>(fin + col.pop_offset, fout + col.pop_offset, col.g, col.cp,
+            sweep_block<ST, false>(fin + col.pop_offset, fout + col.pop_offset, col.g, col.cp,
                             tile_start + col.tile_base, tile_count + col.tile_base, items, cap,
                             recs, nb, flag, bx, by, bz, srec);
     }
@@ -662,23 +745,27 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
     const int* items = tl ? tl->items : nullptr;
     const int cap = tl ? tl->cap : 0;
     if ((g.nx & 1) == 0) {
-        // Even rows: two nodes per thread with aligned vector accesses.
+        // Even rows: two nodes per thread with aligned vector accesses.  Tile
+        // lists longer than the few-bubble path's (many bubbles per tile)
+        // take the tabulated force gather.
         dim3 block(PX, TY, PZ);
         dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + PZ - 1) / PZ);
-        switch (storage) {
-            case 0:
-                k_collide_stream_pair<0><<<grid, block, 0, st>>>(
-                    (const float*)fin, (float*)fout, g, cp, start, count, items, cap, recs, nb, flag);
-                break;
-            case 1:
-                k_collide_stream_pair<1><<<grid, block, 0, st>>>(
-                    (const __half*)fin, (__half*)fout, g, cp, start, count, items, cap, recs, nb, flag);
-                break;
+        const bool tab = tl != nullptr && tl->cap > SMALL_MAX_PAIRS;
+        switch (storage * 2 + (tab ? 1 : 0)) {
+#define LBM_LAUNCH_PAIR(SI, TB, T)                                                                \
+    case SI * 2 + TB:                                                                             \
+        k_collide_stream_pair<SI, TB><<<grid, block, 0, st>>>(                                    \
+            (const T*)fin, (T*)fout, g, cp, start, count, items, cap, recs, nb, flag);            \
+        break;
+            LBM_LAUNCH_PAIR(0, 0, float)
+            LBM_LAUNCH_PAIR(0, 1, float)
+            LBM_LAUNCH_PAIR(1, 0, __half)
+            LBM_LAUNCH_PAIR(1, 1, __half)
+            LBM_LAUNCH_PAIR(2, 0, __nv_bfloat16)
+            LBM_LAUNCH_PAIR(2, 1, __nv_bfloat16)
+#undef LBM_LAUNCH_PAIR
             default:
-                k_collide_stream_pair<2><<<grid, block, 0, st>>>(
-                    (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, g, cp, start, count, items,
-                    cap, recs, nb, flag);
-                break;
+                return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
     }
