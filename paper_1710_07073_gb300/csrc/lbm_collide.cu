@@ -247,9 +247,11 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
 // ---------------------------------------------------------------------------
 // Resident CTAs per SM the register budget is sized for: FP32 rows move twice
 // the bytes per thread and keep more registers; the 16-bit formats need more
-// warps in flight to cover memory latency (measured on GB300).
+// warps in flight to cover memory latency.  Measured on GB300 (FP16 sweep,
+// 256x256x512): 7 CTAs (72 registers, 48 B spilled) 0.458 ms, 8 CTAs
+// (64 registers, 116 B spilled) 0.463 ms, 6 CTAs 0.471 ms.
 #ifndef LBM_PAIR_MINB_16
-#define LBM_PAIR_MINB_16 8
+#define LBM_PAIR_MINB_16 7
 #endif
 #ifndef LBM_PAIR_PZ
 #define LBM_PAIR_PZ 2

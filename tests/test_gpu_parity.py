@@ -181,6 +181,32 @@ def test_swarm_crop_100_steps(count):
     assert (b["active"] == sim.active).all()
 
 
+@pytest.mark.parametrize("storage,scale,u_tol", [(lbm.LBM_STORE_F16, 256.0, 3e-3),
+                                                 (lbm.LBM_STORE_BF16, 1.0, 3e-2)])
+def test_swarm_crop_16bit_storage(storage, scale, u_tol):
+    # 200 bubbles in 32x32x64 take the many-bubble kernels and the sweep's
+    # tabulated force gather; with 16-bit storage the bars are those of the
+    # storage rounding (about 6e-4 and 8e-3 on a single bubble after 1000
+    # steps, here with a margin), positions to 1e-5.
+    dims = (32, 32, 64)
+    pos, vel, diam = workloads.swarm(dims, 200, seed=1234)
+    p = lbm.lbm_default_params()
+    p.g = 1e-4
+    col = lbm.Column(dims, 1.7, olat.ALL_WALLS, storage, scale)
+    lbm.lbm_set_params(col.ctx, p)
+    lbm.lbm_set_bubbles(col.ctx, pos.reshape(-1), vel.reshape(-1), diam)
+    sim = OracleSim(dims, 1.7, olat.ALL_WALLS, params_for_oracle(p, 1.7))
+    sim.set_bubbles(pos, vel, diam)
+    lbm.lbm_step(col.ctx, 100)
+    sim.run(100)
+    _, u_gpu = col.fields()
+    _, u_or = sim.fields()
+    assert rel_linf(u_gpu, u_or) < u_tol
+    b = lbm.lbm_get_bubbles(col.ctx)
+    assert np.abs(b["pos"] - sim.x).max() < 1e-5 * np.abs(sim.x).max()
+    assert (b["active"] == sim.active).all()
+
+
 @pytest.mark.parametrize("count", [None, 40])
 @pytest.mark.parametrize("walls", [olat.ALL_WALLS, olat.WALL_ZM | olat.WALL_ZP])
 def test_binning_bit_exact(walls, count):
