@@ -207,17 +207,29 @@ __device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w) {
 }
 
 // Weight and wrapped lattice coordinates of window node m (x fastest).
+// m / d for 0 <= m < 2^13 and 1 <= d <= WINDOW_CELLS_MAX, through the float
+// reciprocal: (m + 0.5) / d lies at least 1/(2d) from an integer, far more
+// than the rounding of the product, so the truncation is exact.
+__device__ __forceinline__ int div_small(int m, int d) {
+    return (int)(((float)m + 0.5f) * (1.0f / (float)d));
+}
+
+// A window coordinate wrapped into [0, L) (windows are narrower than the box).
+__device__ __forceinline__ int wrap_axis(int i, int L) {
+    return i < 0 ? i + L : (i >= L ? i - L : i);
+}
+
 __device__ __forceinline__ float window_node(const Geo& g, const Window& w, float inv_n, int m,
                                              int& iw, int& jw, int& kw) {
     const float hh = 0.5f * inv_n;
-    const int ix = m % w.cnt[0];
-    const int rest = m / w.cnt[0];
-    const int iy = rest % w.cnt[1];
-    const int iz = rest / w.cnt[1];
+    const int rest = div_small(m, w.cnt[0]);
+    const int ix = m - rest * w.cnt[0];
+    const int iz = div_small(rest, w.cnt[1]);
+    const int iy = rest - iz * w.cnt[1];
     const int i = w.lo[0] + ix, j = w.lo[1] + iy, k = w.lo[2] + iz;
-    iw = (i % g.nx + g.nx) % g.nx;
-    jw = (j % g.ny + g.ny) % g.ny;
-    kw = (k % g.nz + g.nz) % g.nz;
+    iw = wrap_axis(i, g.nx);
+    jw = wrap_axis(j, g.ny);
+    kw = wrap_axis(k, g.nz);
     return cell_poly(((float)(i - w.anc[0]) + 0.5f - w.fr[0]) * inv_n, hh) *
            cell_poly(((float)(j - w.anc[1]) + 0.5f - w.fr[1]) * inv_n, hh) *
            cell_poly(((float)(k - w.anc[2]) + 0.5f - w.fr[2]) * inv_n, hh);
@@ -254,11 +266,6 @@ __device__ __forceinline__ void chunk_sum2(const typename Store<ST>::T* __restri
         ay = fmaf(wb, ub[1], ay);
         az = fmaf(wb, ub[2], az);
     }
-}
-
-// A window coordinate wrapped into [0, L) (windows are narrower than the box).
-__device__ __forceinline__ int wrap_axis(int i, int L) {
-    return i < 0 ? i + L : (i >= L ? i - L : i);
 }
 
 // Eq. 20 partial sums over the window's x-rows (y, z) = tid, tid + nt, ...
@@ -788,36 +795,44 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
             support_cells(F2{__ldcg(B.xh + 3 * b + a), __ldcg(B.xl + 3 * b + a)}, nh, nl, lo, hi);
             ntl[a] = axis_tiles(lo, hi, L[a], !(gb.walls & (1u << (2 * a))), T[a], tl[a]);
         }
+        // One reservation per bubble; its pairs come out in ascending tile
+        // order (each axis list is ascending).
+        int k = atomicAdd(s_n, ntl[0] * ntl[1] * ntl[2]);
         for (int iz = 0; iz < ntl[2]; ++iz)
             for (int iy = 0; iy < ntl[1]; ++iy)
-                for (int ix = 0; ix < ntl[0]; ++ix) {
+                for (int ix = 0; ix < ntl[0]; ++ix, ++k) {
                     const unsigned t = (unsigned)(base + (tl[2][iz] * gb.nty + tl[1][iy]) * gb.ntx +
                                                   tl[0][ix]);
-                    const int k = atomicAdd(s_n, 1);
                     if (k < SMALL_MAX_PAIRS) keys[k] = ((unsigned long long)t << 32) | (unsigned)b;
                     else atomicOr(sb.overflow, 1);
                 }
     }
     __syncthreads();
     const int n = min(*s_n, SMALL_MAX_PAIRS);
-    int p2 = 1;
-    while (p2 < n) p2 <<= 1;
-    for (int i = n + tid; i < p2; i += nt) keys[i] = ~0ull;
-    __syncthreads();
-    for (int k = 2; k <= p2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < p2; i += nt) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const unsigned long long a = keys[i], c = keys[l];
-                    const bool up = (i & k) == 0;
-                    if ((a > c) == up) {
-                        keys[i] = c;
-                        keys[l] = a;
+    // Keys already in order (one bubble, or bubbles that happened to reserve
+    // in order) skip the sort.
+    int unsorted = 0;
+    for (int i = tid + 1; i < n; i += nt) unsorted |= keys[i - 1] > keys[i];
+    if (__syncthreads_or(unsorted)) {   // uniform over the CTA
+        int p2 = 1;
+        while (p2 < n) p2 <<= 1;
+        for (int i = n + tid; i < p2; i += nt) keys[i] = ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= p2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < p2; i += nt) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const unsigned long long a = keys[i], c = keys[l];
+                        const bool up = (i & k) == 0;
+                        if ((a > c) == up) {
+                            keys[i] = c;
+                            keys[l] = a;
+                        }
                     }
                 }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
     for (int i = tid; i < n; i += nt) {
