@@ -343,6 +343,8 @@ __device__ double block_sum_d(double v, double* sh) {
 struct SubRec {
     double u[3];     // velocity before the sub-step
     double v[3], s, re, cdv, fd[3];
+    double pw;       // Re^sn_exp (FP32 powf, as precise as the FP32 forward)
+    double inv_s;    // 1 / |v| (0 at rest)
     int branch;      // 0: 8/3 Eo/(Eo+4) |v|, 1: 24 nu/d (1 + a Re^e), 2: 48 nu/d
     int xclamp[3], uclamp[3];
 };
@@ -425,6 +427,7 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
             double fvm[3];
             for (int c = 0; c < 3; ++c) fvm[c] = h ? Cf * (ul[c] - q[c]) : 0.0;
             const int L[3] = {g.nx, g.ny, g.nz};
+            const double inv_nu = 1.0 / ac.nu, inv_K = 1.0 / K;
             // forward replay
             double u[3] = {pre[b].u[0], pre[b].u[1], pre[b].u[2]};
             double x[3] = {pre[b].x[0], pre[b].x[1], pre[b].x[2]};
@@ -437,8 +440,12 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                     s2 += sr.v[c] * sr.v[c];
                 }
                 sr.s = sqrt(s2);
-                sr.re = sr.s * d / ac.nu;
-                const double A = A0 * (1.0 + ac.sn_coeff * pow(sr.re, ac.sn_exp));
+                sr.inv_s = sr.s > 0.0 ? 1.0 / sr.s : 0.0;
+                sr.re = sr.s * d * inv_nu;
+                // FP64 pow is a long serial sequence on this GPU; the forward
+                // evaluates Re^e in FP32, so the replay does too.
+                sr.pw = sr.re > 0.0 ? (double)powf((float)sr.re, (float)ac.sn_exp) : 0.0;
+                const double A = A0 * (1.0 + ac.sn_coeff * sr.pw);
                 const double vis = fmin(A, Bv);
                 if (E * sr.s >= vis) {
                     sr.cdv = E * sr.s;
@@ -490,7 +497,7 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                 }
                 double lfd[3];
                 for (int c = 0; c < 3; ++c) {
-                    lfd[c] = lpre[c] * kdt - lpsi[c] / K;
+                    lfd[c] = lpre[c] * kdt - lpsi[c] * inv_K;
                     lfvm[c] += lpre[c] * kdt;
                     lkdt += lpre[c] * ((c == 2 ? fb : 0.0) + sr.fd[c] + fvm[c]);
                     if (c == 2) lfb += lpre[c] * kdt;
@@ -506,17 +513,19 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                     lE += lcdv * sr.s;
                     ls += lcdv * E;
                 } else if (sr.branch == 1) {
-                    lA0 += lcdv * (1.0 + ac.sn_coeff * pow(sr.re, ac.sn_exp));
+                    lA0 += lcdv * (1.0 + ac.sn_coeff * sr.pw);
                     if (sr.re > 0.0) {
-                        const double lre = lcdv * A0 * ac.sn_coeff * ac.sn_exp * pow(sr.re, ac.sn_exp - 1.0);
-                        ls += lre * d / ac.nu;
-                        ld_re += lre * sr.s / ac.nu;
+                        // d(Re^e)/dRe = e Re^e / Re, with 1/Re = nu / (d |v|)
+                        const double lre = lcdv * A0 * ac.sn_coeff * ac.sn_exp * sr.pw *
+                                           (ac.nu / d) * sr.inv_s;
+                        ls += lre * d * inv_nu;
+                        ld_re += lre * sr.s * inv_nu;
                     }
                 } else {
                     lB += lcdv;
                 }
                 if (sr.s > 0.0)
-                    for (int c = 0; c < 3; ++c) lv[c] += ls * sr.v[c] / sr.s;
+                    for (int c = 0; c < 3; ++c) lv[c] += ls * sr.v[c] * sr.inv_s;
                 for (int c = 0; c < 3; ++c) {
                     lu[c] += lv[c];
                     lul[c] -= lv[c];
@@ -793,20 +802,25 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     const int nseg = (N + K - 1) / K;
     for (int seg = nseg - 1; seg >= 0 && rc == LBM_OK; --seg) {
         const int n0 = seg * K, n1 = std::min(N, n0 + K);
-        // Recompute the segment forward from its checkpoint.
-        const int cur = (t->cur0 + n0) & 1;
-        c->cur = cur;
-        step_rc(cudaMemcpyAsync(c->f[cur], t->ck_f[seg], fb, cudaMemcpyDeviceToDevice, s), "restore");
+        // Recompute the segment forward from its checkpoint.  Step n reads its
+        // populations from slot n - n0 and writes slot n - n0 + 1 directly, so
+        // no state is copied per step; the last step writes into a context
+        // buffer, which the final restore overwrites.
+        void* const f_ctx[2] = {c->f[0], c->f[1]};
+        step_rc(cudaMemcpyAsync(seg_f[0], t->ck_f[seg], fb, cudaMemcpyDeviceToDevice, s), "restore");
         k_restore<<<sb, 128, 0, s>>>(c->bub, t->ck_b[seg]);
         c->cover_valid = false;
         for (int n = n0; n < n1 && rc == LBM_OK; ++n) {
-            step_rc(cudaMemcpyAsync(seg_f[n - n0], c->f[c->cur], fb, cudaMemcpyDeviceToDevice, s),
-                    "segment state");
+            c->cur = 0;
+            c->f[0] = seg_f[n - n0];
+            c->f[1] = n + 1 < n1 ? seg_f[n + 1 - n0] : f_ctx[0];
             k_snapshot<<<sb, 128, 0, s>>>(c->bub, seg_pre + (size_t)(n - n0) * nb, 0);
             int r2 = enqueue_one_step(c);
             if (r2) rc = r2;
             k_snapshot<<<sb, 128, 0, s>>>(c->bub, seg_post + (size_t)(n - n0) * nb, 1);
         }
+        c->f[0] = f_ctx[0];
+        c->f[1] = f_ctx[1];
         // Reverse through the segment.
         for (int n = n1 - 1; n >= n0 && rc == LBM_OK; --n) {
             const float* fn = (const float*)seg_f[n - n0];
