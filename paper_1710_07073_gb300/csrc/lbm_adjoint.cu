@@ -207,28 +207,44 @@ __device__ __forceinline__ int node_index(const Geo& g, int i, int j, int k) {
 
 // Adjoint of the post-collision values gathered back through streaming:
 // a_j(y) = Lambda^{n+1} at the node and direction that out_j(y) streams to.
+// Element offset of the adjoint of population J leaving node (x,y,z): plane J
+// at x + c_J, or, when that link crosses a wall, plane opp(J) at the node
+// itself (the adjoint of half-way bounce-back); periodic axes wrap.  Written
+// with selects so that a gather issues all 19 loads before using any.
+template <int J>
+__device__ __forceinline__ unsigned push_offset(const Geo& g, int x, int y, int z) {
+    int tx = x + cx(J), ty = y + cy(J), tz = z + cz(J);
+    bool bounce = false;
+    if (cx(J) != 0) {
+        const bool out = (unsigned)tx >= (unsigned)g.nx;
+        bounce = bounce || (out && (g.walls & 0x01));
+        tx = out ? (tx < 0 ? tx + g.nx : tx - g.nx) : tx;
+    }
+    if (cy(J) != 0) {
+        const bool out = (unsigned)ty >= (unsigned)g.ny;
+        bounce = bounce || (out && (g.walls & 0x04));
+        ty = out ? (ty < 0 ? ty + g.ny : ty - g.ny) : ty;
+    }
+    if (cz(J) != 0) {
+        const bool out = (unsigned)tz >= (unsigned)g.nz;
+        bounce = bounce || (out && (g.walls & 0x10));
+        tz = out ? (tz < 0 ? tz + g.nz : tz - g.nz) : tz;
+    }
+    const unsigned S = (unsigned)g.S;
+    return bounce ? (unsigned)opp(J) * S + (unsigned)node_index(g, x, y, z)
+                  : (unsigned)J * S + (unsigned)node_index(g, tx, ty, tz);
+}
+
 __device__ __forceinline__ void gather_push(const float* __restrict__ lam, const Geo& g, int x,
                                             int y, int z, float a[Q]) {
+    unsigned o[Q];
+#define LBM_PO(J) o[J] = push_offset<J>(g, x, y, z)
+    LBM_PO(0); LBM_PO(1); LBM_PO(2); LBM_PO(3); LBM_PO(4); LBM_PO(5); LBM_PO(6);
+    LBM_PO(7); LBM_PO(8); LBM_PO(9); LBM_PO(10); LBM_PO(11); LBM_PO(12); LBM_PO(13);
+    LBM_PO(14); LBM_PO(15); LBM_PO(16); LBM_PO(17); LBM_PO(18);
+#undef LBM_PO
 #pragma unroll
-    for (int j = 0; j < Q; ++j) {
-        int tx = x + cx(j), ty = y + cy(j), tz = z + cz(j);
-        bool bounce = false;
-        if (cx(j) != 0 && (tx < 0 || tx >= g.nx)) {
-            if (g.walls & 0x01) bounce = true;
-            else tx = tx < 0 ? tx + g.nx : tx - g.nx;
-        }
-        if (cy(j) != 0 && (ty < 0 || ty >= g.ny)) {
-            if (g.walls & 0x04) bounce = true;
-            else ty = ty < 0 ? ty + g.ny : ty - g.ny;
-        }
-        if (cz(j) != 0 && (tz < 0 || tz >= g.nz)) {
-            if (g.walls & 0x10) bounce = true;
-            else tz = tz < 0 ? tz + g.nz : tz - g.nz;
-        }
-        const int dir = bounce ? opp(j) : j;
-        const int node = bounce ? node_index(g, x, y, z) : node_index(g, tx, ty, tz);
-        a[j] = lam[(size_t)dir * g.S + node];
-    }
+    for (int j = 0; j < Q; ++j) a[j] = __ldg(lam + o[j]);
 }
 
 // Force at a node from all spreading records of the step (Eq. 21).
@@ -315,9 +331,11 @@ k_adj_liquid(const float* __restrict__ fn, const float* __restrict__ lam_next,
         sspread[b] = two_way ? post[b].active : 0;
     }
     __syncthreads();
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.S) return;
-    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    const unsigned s = blockIdx.x * blockDim.x + threadIdx.x;   // 19 S < 2^32
+    if (s >= (unsigned)g.S) return;
+    const unsigned xy = s / (unsigned)g.nx;
+    const int x = (int)(s - xy * (unsigned)g.nx), y = (int)(xy % (unsigned)g.ny),
+              z = (int)(xy / (unsigned)g.ny);
     float gv[Q], a[Q], out[Q], F[3], lamF[3];
     gather<0>(fn, g, cp, x, y, z, gv);
     gather_push(lam_next, g, x, y, z, a);
@@ -340,11 +358,12 @@ __device__ double block_sum_d(double v, double* sh) {
     return t;
 }
 
+// One replayed sub-step (FP32, like the forward): slip v = u - u_l, |v|, Re,
+// C_D |v|, the drag, Re^sn_exp and 1/|v|.
 struct SubRec {
-    double u[3];     // velocity before the sub-step
-    double v[3], s, re, cdv, fd[3];
-    double pw;       // Re^sn_exp (FP32 powf, as precise as the FP32 forward)
-    double inv_s;    // 1 / |v| (0 at rest)
+    float v[3], s, re, cdv, fd[3];
+    float pw;        // Re^sn_exp
+    float inv_s;     // 1 / |v| (0 at rest)
     int branch;      // 0: 8/3 Eo/(Eo+4) |v|, 1: 24 nu/d (1 + a Re^e), 2: 48 nu/d
     int xclamp[3], uclamp[3];
 };
@@ -407,7 +426,12 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
         }
         gn = block_sum_d(gn, sh);
 
-        // -- Phase B: reverse of the sub-stepped update (thread 0, FP64) ---------
+        // -- Phase B: reverse of the sub-stepped update (thread 0) ---------------
+        // The closure constants and their d-derivatives are FP64, once per step.
+        // The sub-step replay and the per-sub-step terms of its reverse run in
+        // FP32, the precision of the forward they differentiate, because FP64
+        // issue is slow on this GPU.  The centre (wall clamps) and the adjoint
+        // state carried between sub-steps and steps stay FP64.
         if (tid == 0) {
             const int K = min(ac.substeps, ADJ_MAX_SUB);
             const double r = 0.5 * d, vol = M_PI * d * d * d / 6.0, dvol = 0.5 * M_PI * d * d;
@@ -421,68 +445,74 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
             const double Eo = (ac.rho_l - ac.rho_b) * ac.g * d * d / ac.sigma, dEo = 2.0 * Eo / d;
             const double E = 8.0 / 3.0 * Eo / (Eo + 4.0), dE = 8.0 / 3.0 * 4.0 / ((Eo + 4.0) * (Eo + 4.0)) * dEo;
             const double Cf = ac.c_am * ac.rho_l * vol / ac.dt_l, dCf = ac.c_am * ac.rho_l * dvol / ac.dt_l;
+            const float kdt_f = (float)kdt, fb_f = (float)fb, P_f = (float)P, A0_f = (float)A0,
+                        Bv_f = (float)Bv, E_f = (float)E;
+            const float sn_coeff = (float)ac.sn_coeff, sn_exp = (float)ac.sn_exp;
+            const float re_per_s = (float)(d / ac.nu), nu_over_d = (float)(ac.nu / d),
+                        inv_nu = (float)(1.0 / ac.nu), inv_K = 1.0f / (float)K;
             const double* ul = post[b].ul;
             const double* q = pre[b].q;
             const int h = pre[b].h;
-            double fvm[3];
-            for (int c = 0; c < 3; ++c) fvm[c] = h ? Cf * (ul[c] - q[c]) : 0.0;
+            float ulf[3], fvm[3];
+            for (int c = 0; c < 3; ++c) {
+                ulf[c] = (float)ul[c];
+                fvm[c] = h ? (float)(Cf * (ul[c] - q[c])) : 0.0f;
+            }
             const int L[3] = {g.nx, g.ny, g.nz};
-            const double inv_nu = 1.0 / ac.nu, inv_K = 1.0 / K;
             // forward replay
-            double u[3] = {pre[b].u[0], pre[b].u[1], pre[b].u[2]};
+            float u[3] = {(float)pre[b].u[0], (float)pre[b].u[1], (float)pre[b].u[2]};
             double x[3] = {pre[b].x[0], pre[b].x[1], pre[b].x[2]};
             for (int kk = 0; kk < K; ++kk) {
                 SubRec& sr = sub[kk];
-                double s2 = 0.0;
+                float s2 = 0.0f;
                 for (int c = 0; c < 3; ++c) {
-                    sr.u[c] = u[c];
-                    sr.v[c] = u[c] - ul[c];
-                    s2 += sr.v[c] * sr.v[c];
+                    sr.v[c] = u[c] - ulf[c];
+                    s2 = fmaf(sr.v[c], sr.v[c], s2);
                 }
-                sr.s = sqrt(s2);
-                sr.inv_s = sr.s > 0.0 ? 1.0 / sr.s : 0.0;
-                sr.re = sr.s * d * inv_nu;
-                // FP64 pow is a long serial sequence on this GPU; the forward
-                // evaluates Re^e in FP32, so the replay does too.
-                sr.pw = sr.re > 0.0 ? (double)powf((float)sr.re, (float)ac.sn_exp) : 0.0;
-                const double A = A0 * (1.0 + ac.sn_coeff * sr.pw);
-                const double vis = fmin(A, Bv);
-                if (E * sr.s >= vis) {
-                    sr.cdv = E * sr.s;
+                sr.s = sqrtf(s2);
+                sr.inv_s = sr.s > 0.0f ? 1.0f / sr.s : 0.0f;
+                sr.re = sr.s * re_per_s;
+                sr.pw = sr.re > 0.0f ? powf(sr.re, sn_exp) : 0.0f;
+                const float A = A0_f * (1.0f + sn_coeff * sr.pw);
+                const float vis = fminf(A, Bv_f);
+                if (E_f * sr.s >= vis) {
+                    sr.cdv = E_f * sr.s;
                     sr.branch = 0;
                 } else {
                     sr.cdv = vis;
-                    sr.branch = A <= Bv ? 1 : 2;
+                    sr.branch = A <= Bv_f ? 1 : 2;
                 }
                 for (int c = 0; c < 3; ++c) {
-                    sr.fd[c] = -P * sr.cdv * sr.v[c];
-                    const double fz = c == 2 ? fb : 0.0;
-                    u[c] = u[c] + (fz + sr.fd[c] + fvm[c]) * kdt;
-                    x[c] = x[c] + u[c] * ac.dt_b;
+                    sr.fd[c] = -P_f * sr.cdv * sr.v[c];
+                    const float fz = c == 2 ? fb_f : 0.0f;
+                    u[c] = u[c] + (fz + sr.fd[c] + fvm[c]) * kdt_f;
+                    x[c] = x[c] + (double)u[c] * ac.dt_b;
                     sr.xclamp[c] = 0;
                     sr.uclamp[c] = 0;
                     if (g.walls & (1u << (2 * c))) {
                         if (x[c] < r) {
                             x[c] = r;
                             sr.xclamp[c] = 1;
-                            if (u[c] < 0.0) { u[c] = 0.0; sr.uclamp[c] = 1; }
+                            if (u[c] < 0.0f) { u[c] = 0.0f; sr.uclamp[c] = 1; }
                         }
                         if (x[c] > (double)L[c] - r) {
                             x[c] = (double)L[c] - r;
                             sr.xclamp[c] = 1;
-                            if (u[c] > 0.0) { u[c] = 0.0; sr.uclamp[c] = 1; }
+                            if (u[c] > 0.0f) { u[c] = 0.0f; sr.uclamp[c] = 1; }
                         }
                     }
                 }
             }
             // reverse
-            double lx[3], lu[3], lul[3], lq[3], lfvm[3] = {0.0, 0.0, 0.0};
-            double lP = 0.0, lkdt = 0.0, lfb = 0.0, lA0 = 0.0, lB = 0.0, lE = 0.0, ld_re = 0.0;
+            double lx[3], lu[3], lul[3], lq[3];
+            float lfvm[3] = {0.0f, 0.0f, 0.0f}, lpsi_f[3];
+            float lP = 0.0f, lkdt = 0.0f, lfb = 0.0f, lA0 = 0.0f, lB = 0.0f, lE = 0.0f, ld_re = 0.0f;
             for (int c = 0; c < 3; ++c) {
                 lx[c] = adj[b].lx[c] + gx[c];
                 lu[c] = adj[b].lu[c];
                 lul[c] = adj[b].lq[c];   // u_l of this step is the next step's history
                 lq[c] = 0.0;
+                lpsi_f[c] = (float)lpsi[c];
             }
             lu[2] += loss_seed;
             for (int kk = K - 1; kk >= 0; --kk) {
@@ -495,36 +525,36 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                     else lx[c] = 0.0;
                     lpre[c] = sr.uclamp[c] ? 0.0 : lu_next;
                 }
-                double lfd[3];
+                float lfd[3];
                 for (int c = 0; c < 3; ++c) {
-                    lfd[c] = lpre[c] * kdt - lpsi[c] * inv_K;
-                    lfvm[c] += lpre[c] * kdt;
-                    lkdt += lpre[c] * ((c == 2 ? fb : 0.0) + sr.fd[c] + fvm[c]);
-                    if (c == 2) lfb += lpre[c] * kdt;
+                    const float lp = (float)lpre[c];
+                    lfd[c] = lp * kdt_f - lpsi_f[c] * inv_K;
+                    lfvm[c] += lp * kdt_f;
+                    lkdt += lp * ((c == 2 ? fb_f : 0.0f) + sr.fd[c] + fvm[c]);
+                    if (c == 2) lfb += lp * kdt_f;
                     lu[c] = lpre[c];
                 }
                 // fd = -P cdv v
-                const double lfd_v = lfd[0] * sr.v[0] + lfd[1] * sr.v[1] + lfd[2] * sr.v[2];
-                const double lcdv = -P * lfd_v;
+                const float lfd_v = lfd[0] * sr.v[0] + lfd[1] * sr.v[1] + lfd[2] * sr.v[2];
+                const float lcdv = -P_f * lfd_v;
                 lP += -sr.cdv * lfd_v;
-                double lv[3] = {-P * sr.cdv * lfd[0], -P * sr.cdv * lfd[1], -P * sr.cdv * lfd[2]};
-                double ls = 0.0;
+                float lv[3] = {-P_f * sr.cdv * lfd[0], -P_f * sr.cdv * lfd[1], -P_f * sr.cdv * lfd[2]};
+                float ls = 0.0f;
                 if (sr.branch == 0) {
                     lE += lcdv * sr.s;
-                    ls += lcdv * E;
+                    ls += lcdv * E_f;
                 } else if (sr.branch == 1) {
-                    lA0 += lcdv * (1.0 + ac.sn_coeff * sr.pw);
-                    if (sr.re > 0.0) {
+                    lA0 += lcdv * (1.0f + sn_coeff * sr.pw);
+                    if (sr.re > 0.0f) {
                         // d(Re^e)/dRe = e Re^e / Re, with 1/Re = nu / (d |v|)
-                        const double lre = lcdv * A0 * ac.sn_coeff * ac.sn_exp * sr.pw *
-                                           (ac.nu / d) * sr.inv_s;
-                        ls += lre * d * inv_nu;
+                        const float lre = lcdv * A0_f * sn_coeff * sn_exp * sr.pw * nu_over_d * sr.inv_s;
+                        ls += lre * re_per_s;
                         ld_re += lre * sr.s * inv_nu;
                     }
                 } else {
                     lB += lcdv;
                 }
-                if (sr.s > 0.0)
+                if (sr.s > 0.0f)
                     for (int c = 0; c < 3; ++c) lv[c] += ls * sr.v[c] * sr.inv_s;
                 for (int c = 0; c < 3; ++c) {
                     lu[c] += lv[c];
@@ -550,7 +580,6 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
             }
         }
         __syncthreads();
-
         // -- Phase C: interpolation adjoint at x^n --------------------------------
         {
             Window w;
@@ -581,11 +610,16 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                 const int node = node_index(g, i, j, k);
                 const float lw[3] = {(float)(W * lul[0]) * inv_rho, (float)(W * lul[1]) * inv_rho,
                                      (float)(W * lul[2]) * inv_rho};
+                // Each window node belongs to one thread: load its 19 values
+                // first, so that the read-modify-writes do not serialise.
+                float cur[Q];
+#pragma unroll
+                for (int q2 = 0; q2 < Q; ++q2) cur[q2] = lam[(size_t)q2 * g.S + node];
 #pragma unroll
                 for (int q2 = 0; q2 < Q; ++q2) {
                     const float add = ((float)cx(q2) - uj[0]) * lw[0] + ((float)cy(q2) - uj[1]) * lw[1] +
                                       ((float)cz(q2) - uj[2]) * lw[2];
-                    lam[(size_t)q2 * g.S + node] += add;
+                    lam[(size_t)q2 * g.S + node] = cur[q2] + add;
                 }
             }
             for (int c = 0; c < 3; ++c) gx0[c] = block_sum_d(gx0[c], sh);
@@ -603,9 +637,11 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
 //   dL/du0 = sum_j Lambda^0_j w_j rho (3 c_j + 9 (c_j . u0) c_j - 3 u0).
 __global__ void k_adj_init(const float* __restrict__ f0, const float* __restrict__ lam, Geo g,
                            CollideParams cp, double* __restrict__ du0) {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.S) return;
-    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    const unsigned s = blockIdx.x * blockDim.x + threadIdx.x;   // 19 S < 2^32
+    if (s >= (unsigned)g.S) return;
+    const unsigned xy = s / (unsigned)g.nx;
+    const int x = (int)(s - xy * (unsigned)g.nx), y = (int)(xy % (unsigned)g.ny),
+              z = (int)(xy / (unsigned)g.ny);
     float gv[Q];
     gather<0>(f0, g, cp, x, y, z, gv);
     double drho = 0.0, m[3] = {0.0, 0.0, 0.0};
