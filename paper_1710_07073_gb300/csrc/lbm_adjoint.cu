@@ -345,17 +345,29 @@ k_adj_liquid(const float* __restrict__ fn, const float* __restrict__ lam_next,
     for (int j = 0; j < Q; ++j) lam[(size_t)j * g.S + s] = out[j];
 }
 
-__device__ double block_sum_d(double v, double* sh) {
+// Sums of N values over the CTA, in thread 0 only (per value: warp shuffles,
+// then the warps in order).  The N chains interleave, so the FP64 latency is
+// paid once rather than N times.
+template <int N>
+__device__ __forceinline__ void block_sum_dn(double v[N], double (*sh)[8]) {
+    static_assert(N <= 8, "at most 8 values");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    __syncthreads();   // the previous user of sh is done
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < N; ++i) sh[wid][i] = v[i];
     __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    __syncthreads();
-    return t;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+#pragma unroll
+            for (int i = 0; i < N; ++i) v[i] += sh[w][i];
+    }
 }
 
 // One replayed sub-step (FP32, like the forward): slip v = u - u_l, |v|, Re,
@@ -377,7 +389,7 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
               double* __restrict__ grad_d, double loss_seed) {
     __shared__ BubbleRec srec[ADJ_MAX_BUBBLES];
     __shared__ int sspread[ADJ_MAX_BUBBLES];
-    __shared__ double sh[ADJ_THREADS / 32];
+    __shared__ double shn[ADJ_THREADS / 32][8];
     __shared__ double s_lul[3];
     __shared__ SubRec sub[ADJ_MAX_SUB];
     const int tid = threadIdx.x;
@@ -420,11 +432,15 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                 gn += pl * dWdn;
             }
         }
-        for (int c = 0; c < 3; ++c) {
-            lpsi[c] = block_sum_d(lpsi[c], sh);
-            gx[c] = block_sum_d(gx[c], sh);
+        {
+            double sums[7] = {lpsi[0], lpsi[1], lpsi[2], gx[0], gx[1], gx[2], gn};
+            block_sum_dn<7>(sums, shn);   // results in thread 0, which runs Phase B
+            for (int c = 0; c < 3; ++c) {
+                lpsi[c] = sums[c];
+                gx[c] = sums[3 + c];
+            }
+            gn = sums[6];
         }
-        gn = block_sum_d(gn, sh);
 
         // -- Phase B: reverse of the sub-stepped update (thread 0) ---------------
         // The closure constants and their d-derivatives are FP64, once per step.
@@ -622,8 +638,10 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
                     lam[(size_t)q2 * g.S + node] = cur[q2] + add;
                 }
             }
-            for (int c = 0; c < 3; ++c) gx0[c] = block_sum_d(gx0[c], sh);
-            gn0 = block_sum_d(gn0, sh);
+            double sums[4] = {gx0[0], gx0[1], gx0[2], gn0};
+            block_sum_dn<4>(sums, shn);   // results in thread 0
+            for (int c = 0; c < 3; ++c) gx0[c] = sums[c];
+            gn0 = sums[3];
             if (tid == 0) {
                 for (int c = 0; c < 3; ++c) adj[b].lx[c] += gx0[c];
                 grad_d[b] += gn0 * ac.width_factor;
