@@ -287,36 +287,63 @@ __device__ __forceinline__ void collide_adjoint(const float g[Q], const float F[
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
         drho += g[j];
-        m[0] += (float)cx(j) * g[j];
-        m[1] += (float)cy(j) * g[j];
-        m[2] += (float)cz(j) * g[j];
+        if (cx(j) != 0) m[0] += (float)cx(j) * g[j];
+        if (cy(j) != 0) m[1] += (float)cy(j) * g[j];
+        if (cz(j) != 0) m[2] += (float)cz(j) * g[j];
     }
     const float rho = rho0 + drho, inv_rho = 1.0f / rho;
     const float u[3] = {(m[0] + 0.5f * F[0]) * inv_rho, (m[1] + 0.5f * F[1]) * inv_rho,
                         (m[2] + 0.5f * F[2]) * inv_rho};
     const float usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    float A_rho = 0.0f, A_u[3] = {0.0f, 0.0f, 0.0f}, G_F[3] = {0.0f, 0.0f, 0.0f};
+    // With aw_j = a_j w_j, the sums over j that the adjoint needs:
+    //   S0 = sum aw, S1 = sum aw c, S2 = sum aw (c.u) c, S3 = sum aw (c.F) c,
+    //   Su = sum aw (c.u), Su2 = sum aw (c.u)^2.
+    float S0 = 0.0f, Su = 0.0f, Su2 = 0.0f;
+    float S1[3] = {0.0f, 0.0f, 0.0f}, S2[3] = {0.0f, 0.0f, 0.0f}, S3[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        const float c[3] = {(float)cx(j), (float)cy(j), (float)cz(j)};
-        const float cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
-        const float cF = c[0] * F[0] + c[1] * F[1] + c[2] * F[2];
-        const float aw = a[j] * wf(j);
-        A_rho += aw * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * usq);
-        for (int d = 0; d < 3; ++d) {
-            A_u[d] += aw * (omega * rho * (3.0f * c[d] + 9.0f * cu * c[d] - 3.0f * u[d]) +
-                            pref * (9.0f * cF * c[d] - 3.0f * F[d]));
-            G_F[d] += aw * pref * (3.0f * (c[d] - u[d]) + 9.0f * cu * c[d]);
-        }
+        const int c[3] = {cx(j), cy(j), cz(j)};
+        float cu = 0.0f, cF = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (c[d] != 0) {
+                cu += (float)c[d] * u[d];
+                cF += (float)c[d] * F[d];
+            }
+        const float aw = a[j] * wf(j), awcu = aw * cu, awcF = aw * cF;
+        S0 += aw;
+        Su += awcu;
+        Su2 = fmaf(awcu, cu, Su2);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (c[d] != 0) {
+                S1[d] += (float)c[d] * aw;
+                S2[d] += (float)c[d] * awcu;
+                S3[d] += (float)c[d] * awcF;
+            }
     }
-    A_rho *= omega;
+    // The density and velocity adjoints of the forced equilibrium (Eq. 6, 14,
+    // 15): sum_j aw_j times the derivatives of f^eq_j and of the Guo term.
+    const float A_rho = omega * (S0 * (1.0f - 1.5f * usq) + 3.0f * Su + 4.5f * Su2);
+    float Au[3], base = A_rho;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float A_u = omega * rho * (3.0f * S1[d] + 9.0f * S2[d] - 3.0f * u[d] * S0) +
+                          pref * (9.0f * S3[d] - 3.0f * F[d] * S0);
+        const float G_F = pref * (3.0f * S1[d] - 3.0f * u[d] * S0 + 9.0f * S2[d]);
+        Au[d] = A_u * inv_rho;
+        base -= u[d] * Au[d];
+        lamF[d] = 0.5f * Au[d] + G_F;
+    }
+    // lam_k = (1 - omega) a_k + A_rho + (c_k - u) . A_u / rho
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-        const float cmu = ((float)cx(k) - u[0]) * A_u[0] + ((float)cy(k) - u[1]) * A_u[1] +
-                          ((float)cz(k) - u[2]) * A_u[2];
-        lam[k] = (1.0f - omega) * a[k] + A_rho + cmu * inv_rho;
+        float cA = base;
+        if (cx(k) != 0) cA += (float)cx(k) * Au[0];
+        if (cy(k) != 0) cA += (float)cy(k) * Au[1];
+        if (cz(k) != 0) cA += (float)cz(k) * Au[2];
+        lam[k] = (1.0f - omega) * a[k] + cA;
     }
-    for (int d = 0; d < 3; ++d) lamF[d] = 0.5f * A_u[d] * inv_rho + G_F[d];
 }
 
 // Lambda^n = C_f^T S^T Lambda^{n+1} at every node.
