@@ -337,9 +337,10 @@ int run_steps(lbm_batch* b, int nsteps) {
 }
 
 void free_bubbles(lbm_batch* b) {
-    void* ptrs[] = {b->bub.k, b->bub.xh, b->bub.xl, b->bub.u, b->bub.d, b->bub.n, b->bub.ulprev, b->bub.ul,
-                    b->bub.psi, b->bub.has_prev, b->bub.active, b->bub.spread, b->bub.cell,
-                    b->bub.rec, b->bubble_col_d, b->small.part, b->small.arrive};
+    void* ptrs[] = {b->bub.k, b->bub.xh, b->bub.xl, b->bub.u, b->bub.d, b->bub.n,
+                    b->bub.ulprev, b->bub.ul, b->bub.out64, b->bub.psi, b->bub.has_prev,
+                    b->bub.active, b->bub.spread, b->bub.cell, b->bub.rec, b->bubble_col_d,
+                    b->small.part, b->small.arrive};
     for (void* ptr : ptrs) bfree(b, ptr);
     b->bub = BubbleDev{};
     b->bubble_col_d = nullptr;
@@ -511,6 +512,7 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     B.ulprev = (float*)balloc(b, f3);
     B.ul = (float*)balloc(b, f3);
     B.psi = (float*)balloc(b, f3);
+    B.out64 = (double*)balloc(b, sizeof(double) * 12 * (size_t)n);
     B.has_prev = (int*)balloc(b, i1);
     B.active = (int*)balloc(b, i1);
     B.spread = (int*)balloc(b, i1);
@@ -520,7 +522,7 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     sb.parts = window_parts(hwmax);
     sb.part = (float*)balloc(b, sizeof(float) * 3 * WINDOW_CHUNKS_MAX * (size_t)n);
     sb.arrive = (int*)balloc(b, i1);
-    if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi ||
+    if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.out64 ||
         !B.has_prev || !B.active || !B.spread || !B.cell || !B.rec || !b->bubble_col_d ||
         !sb.part || !sb.arrive) {
         free_bubbles(b);

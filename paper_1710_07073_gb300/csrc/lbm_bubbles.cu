@@ -7,7 +7,8 @@
 //                    psi_b = -mean F_D (Algorithm 1 step 6) and the spreading
 //                    record; the last one bins all bubbles.
 //  k_moments_tiles,  many bubbles: Eq. 10 velocity of the covered tiles, then
-//  k_bubbles_warp    one warp per bubble with the same tail.
+//  k_bubbles_warp    one warp per 32 bubbles (window sums in turn, the 32
+//                    tails in parallel).
 //  binning           bubble windows to lattice tiles (Algorithm 1 step 2):
 //                    integer counting sort, then each tile's list in bubble
 //                    order.
@@ -435,8 +436,7 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
     if ((g.walls & 0x20) && !f2_lt(xb[2], top[2])) B.active[b] = 0;
 }
 
-// Many bubbles: one warp per bubble, window velocities from the moments of
-// the covered tiles.
+// Many bubbles: window velocities from the moments of the covered tiles.
 constexpr int WARP_BUBBLE_THREADS = 128;   // four warps, 32 bubbles each
 
 // Each warp serves 32 consecutive bubbles.  Lane k loads bubble 32 w + k and
@@ -1026,29 +1026,41 @@ cudaError_t launch_bubble_constants_batch(const BubbleDev& b, const BubbleConst&
 // Field utilities
 // ---------------------------------------------------------------------------
 
-// Eq. 10 moments of the pre-collision populations, FP64.
+// Node coordinates of site s (x fastest); 19 S < 2^32, so 32-bit arithmetic.
+__device__ __forceinline__ void site_coords(const Geo& g, unsigned s, int& x, int& y, int& z) {
+    const unsigned xy = s / (unsigned)g.nx;
+    x = (int)(s - xy * (unsigned)g.nx);
+    y = (int)(xy % (unsigned)g.ny);
+    z = (int)(xy / (unsigned)g.ny);
+}
+
+// rho and the bare Eq. 10 velocity of the current populations, summed in
+// FP64 over the stored values (the same sums as the FP64 totals).
 template <int ST>
 __global__ void k_fields(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
                          double* __restrict__ rho, double* __restrict__ u) {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.S) return;
-    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
+    const unsigned s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (unsigned)g.S) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
     float gv[Q];
     gather<ST>(f, g, cp, x, y, z, gv);
     double drho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
     for (int j = 0; j < Q; ++j) {
-        drho += gv[j];
-        jx += cx(j) * (double)gv[j];
-        jy += cy(j) * (double)gv[j];
-        jz += cz(j) * (double)gv[j];
+        const double v = gv[j];
+        drho += v;
+        if (cx(j) != 0) jx += cx(j) > 0 ? v : -v;
+        if (cy(j) != 0) jy += cy(j) > 0 ? v : -v;
+        if (cz(j) != 0) jz += cz(j) > 0 ? v : -v;
     }
     const double r = (double)cp.rho0 + drho;
     if (rho) rho[s] = r;
     if (u) {
-        u[s] = jx / r;
-        u[g.S + s] = jy / r;
-        u[2 * g.S + s] = jz / r;
+        const double inv_r = 1.0 / r;
+        u[s] = jx * inv_r;
+        u[g.S + s] = jy * inv_r;
+        u[2 * g.S + s] = jz * inv_r;
     }
 }
 
@@ -1111,21 +1123,29 @@ __global__ void k_set_pop(const double* __restrict__ fin, typename Store<ST>::T*
 template <int ST>
 __global__ void k_set_feq(const double* __restrict__ rho, const double* __restrict__ u,
                           typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp) {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.S) return;
-    const int x = (int)(s % g.nx), y = (int)((s / g.nx) % g.ny), z = (int)(s / ((long long)g.nx * g.ny));
-    for (int j = 0; j < Q; ++j) {
-        int dir;
-        long long node;
-        push_target(g, j, x, y, z, dir, node);
-        const double r = rho ? rho[node] : (double)cp.rho0;
-        const double ux = u ? u[node] : 0.0, uy = u ? u[g.S + node] : 0.0,
-                     uz = u ? u[2 * g.S + node] : 0.0;
-        const double cu = cx(dir) * ux + cy(dir) * uy + cz(dir) * uz;
-        const double usq = ux * ux + uy * uy + uz * uz;
-        const double v = wd(dir) * ((r - (double)cp.rho0) + r * (3.0 * cu + 4.5 * cu * cu - 1.5 * usq));
-        f[(size_t)j * g.S + s] = Store<ST>::from_double(v, j, cp);
+    // Each node writes its 19 equilibria (Eq. 6) to the places the first
+    // step's pull will read them from (pull_offset; a bijection, so no two
+    // threads write the same place).  FP32 arithmetic on the shifted value;
+    // rho - rho0 is formed in FP64 first.
+    const unsigned s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (unsigned)g.S) return;
+    int x, y, z;
+    site_coords(g, s, x, y, z);
+    const double rd = rho ? rho[s] : (double)cp.rho0;
+    const float dr = (float)(rd - (double)cp.rho0), r = (float)rd;
+    const float ux = u ? (float)u[s] : 0.0f, uy = u ? (float)u[g.S + s] : 0.0f,
+                uz = u ? (float)u[2 * g.S + s] : 0.0f;
+    const float usq15 = 1.5f * (ux * ux + uy * uy + uz * uz);
+#define LBM_FEQ(J)                                                                            \
+    {                                                                                         \
+        const float cu = (float)cx(J) * ux + (float)cy(J) * uy + (float)cz(J) * uz;           \
+        const float v = wf(J) * (dr + r * (cu * (3.0f + 4.5f * cu) - usq15));                 \
+        Store<ST>::template store<J>(f + pull_offset<J>(g, x, y, z), v, cp);                  \
     }
+    LBM_FEQ(0); LBM_FEQ(1); LBM_FEQ(2); LBM_FEQ(3); LBM_FEQ(4); LBM_FEQ(5); LBM_FEQ(6);
+    LBM_FEQ(7); LBM_FEQ(8); LBM_FEQ(9); LBM_FEQ(10); LBM_FEQ(11); LBM_FEQ(12); LBM_FEQ(13);
+    LBM_FEQ(14); LBM_FEQ(15); LBM_FEQ(16); LBM_FEQ(17); LBM_FEQ(18);
+#undef LBM_FEQ
 }
 
 // FP64 totals: per-block partial sums in fixed order, then one block.
@@ -1270,27 +1290,31 @@ cudaError_t upload_bubble_state(const BubbleDev& B, int n, const double* pos3, c
     return cudaStreamSynchronize(st);
 }
 
+// FP64 copies of the first k bubbles' state: out = [x | u | u_l | psi], each
+// 3k values.
+__global__ void k_export_bubbles(BubbleDev B, int k, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t m = 3 * (size_t)k;
+    if (i >= (int)m) return;
+    out[i] = join_f2(B.xh[i], B.xl[i]);
+    out[m + i] = B.u[i];
+    out[2 * m + i] = B.ul[i];
+    out[3 * m + i] = B.psi[i];
+}
+
 cudaError_t download_bubble_state(const BubbleDev& B, int k, double* pos3, double* vel3,
                                   double* ul3, double* psi3, cudaStream_t st) {
-    const size_t m = 3 * (size_t)k, bytes = sizeof(float) * m;
-    std::vector<float> xh(pos3 ? m : 0), xl(pos3 ? m : 0), u(vel3 ? m : 0), ul(ul3 ? m : 0),
-        psi(psi3 ? m : 0);
-    cudaError_t e;
-    if (pos3) {
-        if ((e = cudaMemcpyAsync(xh.data(), B.xh, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(xl.data(), B.xl, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    }
-    if (vel3 && (e = cudaMemcpyAsync(u.data(), B.u, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    if (ul3 && (e = cudaMemcpyAsync(ul.data(), B.ul, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    if (psi3 && (e = cudaMemcpyAsync(psi.data(), B.psi, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
-    for (size_t i = 0; i < m; ++i) {
-        if (pos3) pos3[i] = join_f2(xh[i], xl[i]);
-        if (vel3) vel3[i] = u[i];
-        if (ul3) ul3[i] = ul[i];
-        if (psi3) psi3[i] = psi[i];
-    }
-    return cudaSuccess;
+    double* const stage = B.out64;
+    const size_t m = 3 * (size_t)k, bytes = sizeof(double) * m;
+    k_export_bubbles<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(B, k, stage);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double* dst[4] = {pos3, vel3, ul3, psi3};
+    for (int q = 0; q < 4; ++q)
+        if (dst[q] && (e = cudaMemcpyAsync(dst[q], stage + q * m, bytes, cudaMemcpyDeviceToHost,
+                                           st)) != cudaSuccess)
+            return e;
+    return cudaStreamSynchronize(st);
 }
 
 }  // namespace lbm

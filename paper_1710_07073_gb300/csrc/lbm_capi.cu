@@ -152,9 +152,9 @@ int axis_tile_bound(double n, int T) {
 void free_bubbles(lbm_ctx* c) {
     BubbleDev& b = c->bub;
     SmallBins& sb = c->small;
-    void* ptrs[] = {b.k, b.xh, b.xl, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.has_prev, b.active, b.spread,
-                    b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items, sb.prev_tiles,
-                    sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, c->mom};
+    void* ptrs[] = {b.k, b.xh, b.xl, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.out64, b.has_prev,
+                    b.active, b.spread, b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items,
+                    sb.prev_tiles, sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, c->mom};
     for (void* p : ptrs) dfree(c, p);
     c->mom = nullptr;
     c->cover_valid = false;
@@ -476,6 +476,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     B.ulprev = (float*)dalloc(c, f3);
     B.ul = (float*)dalloc(c, f3);
     B.psi = (float*)dalloc(c, f3);
+    B.out64 = (double*)dalloc(c, sizeof(double) * 12 * (size_t)n);
     B.has_prev = (int*)dalloc(c, i1);
     B.active = (int*)dalloc(c, i1);
     B.spread = (int*)dalloc(c, i1);
@@ -516,8 +517,8 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         c->mom = (float*)dalloc(c, sizeof(float) * 3 * (size_t)c->nx * c->ny * c->nz);
         lists_ok = c->bins.items != nullptr && c->mom != nullptr;
     }
-    if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.has_prev ||
-        !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
+    if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi ||
+        !B.out64 || !B.has_prev || !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
         free_bubbles(c);
         return fail(c, LBM_ERR_ALLOC, "bubble state");
     }

@@ -116,6 +116,7 @@ struct BubbleDev {
     int* spread;      // [nb] 1 if the bubble spread in the last step
     int* cell;        // [nb] containing cell after the last update (-1 inactive)
     BubbleRec* rec;   // [nb]
+    double* out64;    // [12*nb] FP64 staging for exports to the host
 };
 
 struct BubbleConst {
@@ -207,11 +208,11 @@ cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, c
 cudaError_t upload_bubble_state(const BubbleDev& B, int n, const double* pos3, const double* vel3,
                                 cudaStream_t st);
 // Host: the first k bubbles' state as FP64 arrays (null pointers are
-// skipped).  Synchronises the stream.
+// skipped), converted on the device into B.out64.  Synchronises the stream.
 cudaError_t download_bubble_state(const BubbleDev& B, int k, double* pos3, double* vel3,
                                   double* ul3, double* psi3, cudaStream_t st);
 // Many bubbles: Eq. 10 velocity of the covered tiles into mom[3*S], then one
-// warp per bubble interpolating from it.  tile_count: the binning of the
+// warp per 32 bubbles interpolating from it.  tile_count: the binning of the
 // current centres (count > 0 marks a covered tile).
 cudaError_t launch_bubbles_many(int storage, const void* f, float* mom, const Geo& g,
                                 const CollideParams& cp, const BubbleDev& b, const BubbleConst& bc,
