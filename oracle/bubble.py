@@ -2,7 +2,7 @@
 
 Lattice units; gravity acts along -z with magnitude g.
 
-Readings (each listed in the design doc):
+Readings of the paper where it is garbled or silent:
 
 * Eq. 3 prints Eo = (rho_l - rho_b) g d_b / sigma; the Eotvos number carries
   d_b^2 (this reproduces the force-balance column of Table 4).

@@ -3,7 +3,7 @@
 Node j of the lattice sits at the centre (i + 1/2) of cell Omega_j = [i, i+1]
 along each axis; the box is [0, nx] x [0, ny] x [0, nz].
 
-Readings of the printed formulas (each listed in the design doc):
+Readings of the printed formulas:
 
 * Eq. 18 prints the polynomial as (r)/n^5 - 2 (r)/n^3 + 1/n.  Only the form
   Z(r) = 15/16 [r^4/n^5 - 2 r^2/n^3 + 1/n] on |r| <= n meets the stated
