@@ -891,6 +891,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
         step_rc(cudaMemcpyAsync(seg_f[0], t->ck_f[seg], fb, cudaMemcpyDeviceToDevice, s), "restore");
         k_restore<<<sb, 128, 0, s>>>(c->bub, t->ck_b[seg]);
         c->cover_valid = false;
+        guard_invalidate(c);
         for (int n = n0; n < n1 && rc == LBM_OK; ++n) {
             c->cur = 0;
             c->f[0] = seg_f[n - n0];
@@ -944,6 +945,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     step_rc(cudaMemcpyAsync(c->f[c->cur], t->final_f, fb, cudaMemcpyDeviceToDevice, s), "final");
     k_restore<<<sb, 128, 0, s>>>(c->bub, t->final_b);
     c->cover_valid = false;
+    guard_invalidate(c);
     step_rc(cudaStreamSynchronize(s), "adjoint");
     release();
     if (rc) return rc;

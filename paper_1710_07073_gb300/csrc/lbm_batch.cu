@@ -302,7 +302,9 @@ int check_flag(lbm_batch* b) {
     LBM_BCUDA(cudaStreamSynchronize(b->stream), "step");
     if (*b->flag_h) {
         b->unstable = true;
-        return bfail(b, LBM_ERR_UNSTABLE, "non-finite value or |u| >= 0.3 in a column");
+        return bfail(b, LBM_ERR_UNSTABLE,
+                     "non-finite value or |u| >= 0.3 in a column, or a bubble faster than %d "
+                     "cells per step", GUARD_CELLS);
     }
     int ov = 0;
     LBM_BCUDA(cudaMemcpy(&ov, b->small.overflow, sizeof(int), cudaMemcpyDeviceToHost), "overflow");

@@ -163,14 +163,16 @@ struct BubbleIn {
     int active, has_prev;
 };
 
+// The state the previous update wrote is read through L2 (ld.global.cg): that
+// update may have run as an overlapped launch.
 __device__ __forceinline__ void load_bubble(const BubbleDev& B, int b, bool full, BubbleIn& in) {
-    in.active = B.active[b];
-    for (int a = 0; a < 3; ++a) in.x[a] = F2{B.xh[3 * b + a], B.xl[3 * b + a]};
+    in.active = __ldcg(B.active + b);
+    for (int a = 0; a < 3; ++a) in.x[a] = F2{__ldcg(B.xh + 3 * b + a), __ldcg(B.xl + 3 * b + a)};
     in.k = B.k[b];
-    in.has_prev = full ? B.has_prev[b] : 0;
+    in.has_prev = full ? __ldcg(B.has_prev + b) : 0;
     for (int a = 0; a < 3; ++a) {
-        in.u[a] = full ? B.u[3 * b + a] : 0.0f;
-        in.ulprev[a] = full ? B.ulprev[3 * b + a] : 0.0f;
+        in.u[a] = full ? __ldcg(B.u + 3 * b + a) : 0.0f;
+        in.ulprev[a] = full ? __ldcg(B.ulprev + 3 * b + a) : 0.0f;
     }
 }
 
@@ -403,6 +405,19 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
             xb[a] = f2_from(v);
         }
     }
+    // A bubble that moved more than GUARD_CELLS cells along an axis in one
+    // step (lattice speed > 4) flags the instability.
+    bool too_fast = false;
+    for (int a = 0; a < 3; ++a) {
+        float d = (xb[a].h - in.x[a].h) + (xb[a].l - in.x[a].l);
+        if (!(g.walls & (1u << (2 * a)))) {
+            const float La = (float)L[a];
+            if (d > 0.5f * La) d -= La;
+            else if (d < -0.5f * La) d += La;
+        }
+        too_fast |= !(fabsf(d) <= (float)GUARD_CELLS);
+    }
+    if (too_fast) atomicOr(flag, 4);
     float psi[3];
     const float inv_sub = 1.0f / (float)bc.substeps;
     for (int a = 0; a < 3; ++a) {
@@ -845,6 +860,55 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
     if (tid == 0) *sb.prev_n = n;
 }
 
+__device__ __forceinline__ int floor_div(int a, int b) {
+    return a >= 0 ? a / b : -((-a + b - 1) / b);
+}
+
+// Overlap guard for the next step (single column): safe[l] = sb.safe_epoch
+// for every z tile layer l that the support of no active bubble, widened by
+// GUARD_CELLS cells, reaches.  Next step's forces lie inside those supports
+// unless a bubble moves more than GUARD_CELLS cells, which flags the
+// instability.  Every thread of the CTA calls it.
+__device__ void write_safe_layers(const Geo& g, const BubbleDev& B, const SmallBins& sb) {
+    __shared__ unsigned s_lay[GUARD_LAYERS_MAX / 32];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ntz = g.ntz;
+    if (ntz > GUARD_LAYERS_MAX) return;
+    for (int i = tid; i < GUARD_LAYERS_MAX / 32; i += nt) s_lay[i] = 0u;
+    __syncthreads();
+    const bool periodic = !(g.walls & 0x10);
+    for (int b = tid; b < B.nb; b += nt) {
+        if (!__ldcg(B.active + b)) continue;
+        int lo, hi;
+        support_cells(F2{__ldcg(B.xh + 3 * b + 2), __ldcg(B.xl + 3 * b + 2)},
+                      __ldcg(&B.k[b].nh), __ldcg(&B.k[b].nl), lo, hi);
+        lo = max(lo, -2 * g.nz) - GUARD_CELLS;
+        hi = min(hi, 3 * g.nz) + GUARD_CELLS;
+        int l0, l1;
+        if (!periodic) {
+            lo = max(lo, 0);
+            hi = min(hi, g.nz - 1);
+            if (hi < lo) continue;
+            l0 = lo / TZ;
+            l1 = hi / TZ;
+        } else if (hi - lo + 1 >= g.nz) {
+            l0 = 0;
+            l1 = ntz - 1;
+        } else {
+            l0 = floor_div(lo, TZ);
+            l1 = floor_div(hi, TZ);
+        }
+        for (int l = l0; l <= l1; ++l) {
+            int lw = l % ntz;
+            if (lw < 0) lw += ntz;
+            atomicOr(&s_lay[lw >> 5], 1u << (lw & 31));
+        }
+    }
+    __syncthreads();
+    for (int l = tid; l < ntz; l += nt)
+        if (!((s_lay[l >> 5] >> (l & 31)) & 1u)) sb.safe[l] = sb.safe_epoch;
+}
+
 // Bubble update with the few-pair binning fused behind it.
 //
 // The window of a bubble is cut into chunks of WINDOW_CHUNK nodes (node m of
@@ -858,6 +922,11 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
 // previous binning's tile counts; that is ordered before the new binning by
 // the same arrive / done counters.  With `cols` set (a batch), bubble b lives
 // in column bubble_col[b].
+//
+// Launched to overlap with the sweep before it, the update first waits for
+// that sweep (whose populations it reads and whose tile lists it rewrites),
+// then lets the next sweep start: that sweep runs alongside the rest of the
+// update and waits for it only in the z layers the guard does not clear.
 template <int ST>
 __global__ void __launch_bounds__(BUBBLE_THREADS, 1)
 k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
@@ -869,6 +938,8 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
     const int parts = sb.parts;
     const int b = blockIdx.x / parts, p = blockIdx.x - b * parts;
     const bool alone = gridDim.x == 1;   // one bubble, one CTA: nothing to publish
+    pdl_wait();
+    pdl_trigger();
     BubbleIn in;
     load_bubble(B, b, threadIdx.x == 0, in);
     if (blockIdx.x == 0) {
@@ -938,6 +1009,7 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
     if (!s_last) return;
     if (!alone) __threadfence();
     bin_small_block(g, B, sb, keys, &s_n, cols, bubble_col);
+    if (sb.safe != nullptr && cols == nullptr) write_safe_layers(g, B, sb);
     if (threadIdx.x == 0 && !alone) *sb.done = 0;        // ready for the next launch
 }
 
@@ -949,26 +1021,35 @@ int window_parts(double max_half_width) {
 
 namespace {
 template <int ST>
-void launch_binned(const void* f, const Geo& g, const CollideParams& cp, const BubbleDev& b,
-                   const BubbleConst& bc, int* flag, const SmallBins& sb, const BatchColumn* cols,
-                   const int* bubble_col, cudaStream_t st) {
+cudaError_t launch_binned(const void* f, const Geo& g, const CollideParams& cp,
+                          const BubbleDev& b, const BubbleConst& bc, int* flag,
+                          const SmallBins& sb, const BatchColumn* cols, const int* bubble_col,
+                          bool overlap, cudaStream_t st) {
     using T = typename Store<ST>::T;
-    k_bubbles_binned<ST><<<b.nb * sb.parts, BUBBLE_THREADS, 0, st>>>(
-        (const T*)f, g, cp, b, bc, flag, sb, cols, bubble_col);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.nb * sb.parts);
+    cfg.blockDim = dim3(BUBBLE_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_bubbles_binned<ST>, (const T*)f, g, cp, b, bc, flag, sb,
+                              cols, bubble_col);
 }
 }  // namespace
 
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag,
-                           const SmallBins& sb, cudaStream_t st) {
+                           const SmallBins& sb, bool overlap, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
     if (sb.parts < 1 || sb.parts > WINDOW_CHUNKS_MAX) return cudaErrorInvalidValue;
     switch (storage) {
-        case 0: launch_binned<0>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, st); break;
-        case 1: launch_binned<1>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, st); break;
-        default: launch_binned<2>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, st); break;
+        case 0: return launch_binned<0>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, overlap, st);
+        case 1: return launch_binned<1>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, overlap, st);
+        default: return launch_binned<2>(f, g, cp, b, bc, flag, sb, nullptr, nullptr, overlap, st);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* cols,
@@ -980,11 +1061,10 @@ cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* 
     const Geo g0{};
     const CollideParams cp0{};
     switch (storage) {
-        case 0: launch_binned<0>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, st); break;
-        case 1: launch_binned<1>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, st); break;
-        default: launch_binned<2>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, st); break;
+        case 0: return launch_binned<0>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, false, st);
+        case 1: return launch_binned<1>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, false, st);
+        default: return launch_binned<2>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, false, st);
     }
-    return cudaGetLastError();
 }
 
 // Per-bubble closure constants for a batch: nu from each bubble's column.

@@ -154,7 +154,8 @@ void free_bubbles(lbm_ctx* c) {
     SmallBins& sb = c->small;
     void* ptrs[] = {b.k, b.xh, b.xl, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.out64, b.has_prev,
                     b.active, b.spread, b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items,
-                    sb.prev_tiles, sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, c->mom};
+                    sb.prev_tiles, sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, sb.safe,
+                    c->mom};
     for (void* p : ptrs) dfree(c, p);
     c->mom = nullptr;
     c->cover_valid = false;
@@ -164,19 +165,42 @@ void free_bubbles(lbm_ctx* c) {
     c->bins.cap = 0;
     c->nb_cap = 0;
     c->use_small = false;
+    guard_invalidate(c);
 }
 
 }  // namespace
+
+void guard_invalidate(lbm_ctx* c) { c->epoch += 1; }
 
 int enqueue_one_step(lbm_ctx* c) {
     const Geo g = geo_of(c);
     const CollideParams cp = collide_params(c);
     const bool bubbles = c->bub.nb > 0;
     const bool two_way = bubbles && c->p.two_way;
+    // Few bubbles, two-way coupling, even rows: the update and the sweep
+    // overlap (programmatic dependent launches).  Timed launches keep plain
+    // stream order so that the sweep's events time the sweep alone.
+    const bool overlap = two_way && c->use_small && c->small.safe != nullptr && !c->timing &&
+                         (g.nx & 1) == 0;
+    if (c->epoch >= 0xFFFFFF00u) {
+        // Before the step number wraps: no stored tag may match a later one.
+        if (c->small.safe)
+            LBM_CUDA(cudaMemsetAsync(c->small.safe, 0, 2 * sizeof(unsigned) * (size_t)g.ntz,
+                                     c->stream), "guard reset");
+        c->epoch = 1;
+    }
+    const unsigned epoch = c->epoch++;
+    // Tag sets by step parity: this step's sweep reads set (epoch & 1) while
+    // its update writes the next step's into the other set.
+    const unsigned* safe_now =
+        c->small.safe ? c->small.safe + (size_t)(epoch & 1u) * (size_t)g.ntz : nullptr;
     if (bubbles) {
         if (c->use_small) {
+            SmallBins sb = c->small;
+            if (sb.safe) sb.safe += (size_t)((epoch + 1u) & 1u) * (size_t)g.ntz;
+            sb.safe_epoch = epoch + 1;   // the update clears layers for the next step
             LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
-                                    c->flag_d, c->small, c->stream),
+                                    c->flag_d, sb, overlap, c->stream),
                      "bubble update");
             c->launches += 1;   // binning fused into the bubble update
         } else {
@@ -213,7 +237,7 @@ int enqueue_one_step(lbm_ctx* c) {
     else tl = TileLists{c->bins.off, c->bins.cnt, c->bins.items, c->bins.cap};
     LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
                                    two_way ? &tl : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
-                                   c->stream),
+                                   overlap ? safe_now : nullptr, epoch, overlap, c->stream),
              "collide-stream");
     if (c->timing) LBM_CUDA(cudaEventRecord(e1, c->stream), "event record");
     c->launches += 1;
@@ -228,7 +252,9 @@ int finish_steps(lbm_ctx* c) {
     LBM_CUDA(cudaStreamSynchronize(c->stream), "step");
     if (*c->flag_h) {
         c->unstable = true;
-        return fail(c, LBM_ERR_UNSTABLE, "non-finite value or |u| >= 0.3 in the liquid");
+        return fail(c, LBM_ERR_UNSTABLE,
+                    "non-finite value or |u| >= 0.3 in the liquid, or a bubble faster than %d "
+                    "cells per step", GUARD_CELLS);
     }
     if (c->bins_valid) {
         int ov = 0;
@@ -345,6 +371,7 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
     }
     adjoint_free(c);
     c->p = *p;
+    guard_invalidate(c);
     if (c->bub.nb > 0)
         LBM_CUDA(launch_bubble_constants(c->bub, bubble_const(c), c->stream), "bubble constants");
     return LBM_OK;
@@ -511,6 +538,12 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sb.arrive = (int*)dalloc(c, sizeof(int) * (size_t)n);
         lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow &&
                    sb.done && sb.part && sb.arrive;
+        // Overlap guard tags, one set per step parity (zero: no layer
+        // cleared yet).
+        if (c->bins.T > 0 && geo_of(c).ntz <= GUARD_LAYERS_MAX) {
+            sb.safe = (unsigned*)dalloc(c, 2 * sizeof(unsigned) * (size_t)geo_of(c).ntz);
+            lists_ok = lists_ok && sb.safe;
+        }
     } else {
         c->bins.cap = (int)cap;
         c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
@@ -529,6 +562,9 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         LBM_CUDA(cudaMemsetAsync(sb.overflow, 0, sizeof(int), c->stream), "overflow");
         LBM_CUDA(cudaMemsetAsync(sb.done, 0, sizeof(int), c->stream), "done");
         LBM_CUDA(cudaMemsetAsync(sb.arrive, 0, sizeof(int) * (size_t)n, c->stream), "arrive");
+        if (sb.safe)
+            LBM_CUDA(cudaMemsetAsync(sb.safe, 0, 2 * sizeof(unsigned) * (size_t)geo_of(c).ntz,
+                                     c->stream), "guard");
     }
     B.nb = n;
     std::vector<double> hn(n);

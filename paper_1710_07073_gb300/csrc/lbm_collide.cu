@@ -248,10 +248,10 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
 // Resident CTAs per SM the register budget is sized for: FP32 rows move twice
 // the bytes per thread and keep more registers; the 16-bit formats need more
 // warps in flight to cover memory latency.  Measured on GB300 (FP16 sweep,
-// 256x256x512): 7 CTAs (72 registers, 48 B spilled) 0.458 ms, 8 CTAs
-// (64 registers, 116 B spilled) 0.463 ms, 6 CTAs 0.471 ms.
+// 256x256x512, rows kept packed until use): 8 CTAs (64 registers) 0.439 ms,
+// 7 CTAs 0.448 ms, 9 CTAs 0.461 ms.
 #ifndef LBM_PAIR_MINB_16
-#define LBM_PAIR_MINB_16 7
+#define LBM_PAIR_MINB_16 8
 #endif
 #ifndef LBM_PAIR_PZ
 #define LBM_PAIR_PZ 2
@@ -268,28 +268,57 @@ static_assert(TZ % PZ == 0, "a CTA's z-planes must lie in one binning tile");
 
 template <int ST> struct Vec2;
 template <> struct Vec2<0> {
-    static __device__ __forceinline__ float2 load(const float* p) {
-        return __ldg(reinterpret_cast<const float2*>(p));
-    }
     static __device__ __forceinline__ void store(float* p, float2 v) {
         __stcs(reinterpret_cast<float2*>(p), v);
     }
 };
 template <> struct Vec2<1> {
-    static __device__ __forceinline__ float2 load(const __half* p) {
-        return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
-    }
     static __device__ __forceinline__ void store(__half* p, float2 v) {
         __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(v.x, v.y));
     }
 };
 template <> struct Vec2<2> {
-    static __device__ __forceinline__ float2 load(const __nv_bfloat16* p) {
-        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
-    }
     static __device__ __forceinline__ void store(__nv_bfloat16* p, float2 v) {
         __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(v.x, v.y));
     }
+};
+
+// The stored values of one direction at an x-pair, as loaded.  FP32 keeps the
+// float2; the 16-bit formats keep both nodes packed in one 32-bit register
+// (node x0 in the low half) and widen at each use, which halves the registers
+// the 19 loaded rows hold while the moments and the relaxation run.
+template <int ST> struct Raw2 {
+    using T = unsigned;
+    using T1 = unsigned;
+    static __device__ __forceinline__ T load(const typename Store<ST>::T* p) {
+        return __ldg(reinterpret_cast<const unsigned*>(p));
+    }
+    static __device__ __forceinline__ T1 load1(const typename Store<ST>::T* p) {
+        return (unsigned)__ldg(reinterpret_cast<const unsigned short*>(p));
+    }
+    // (a, P.x) and (P.y, a)
+    static __device__ __forceinline__ T lo_from(T1 a, T P) { return __byte_perm(a, P, 0x5410); }
+    static __device__ __forceinline__ T hi_from(T P, T1 a) { return __byte_perm(P, a, 0x5432); }
+    static __device__ __forceinline__ T join(T1 a, T1 b) { return __byte_perm(a, b, 0x5410); }
+    static __device__ __forceinline__ float2 widen(T v);
+};
+template <> __device__ __forceinline__ float2 Raw2<1>::widen(unsigned v) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&v));
+}
+template <> __device__ __forceinline__ float2 Raw2<2>::widen(unsigned v) {
+    return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+template <> struct Raw2<0> {
+    using T = float2;
+    using T1 = float;
+    static __device__ __forceinline__ T load(const float* p) {
+        return __ldg(reinterpret_cast<const float2*>(p));
+    }
+    static __device__ __forceinline__ T1 load1(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ T lo_from(T1 a, T P) { return make_float2(a, P.x); }
+    static __device__ __forceinline__ T hi_from(T P, T1 a) { return make_float2(P.y, a); }
+    static __device__ __forceinline__ T join(T1 a, T1 b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float2 widen(T v) { return v; }
 };
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
@@ -354,28 +383,32 @@ __device__ __forceinline__ void add_bubble_force_pair(const BubbleRec& r, const 
 // opposite plane of the node itself (wall) or the other end of the row
 // (periodic).  Every lane issues the same loads, so none waits on another.
 template <int ST, int J>
-__device__ __forceinline__ float2 pull_pair(const typename Store<ST>::T* __restrict__ f,
-                                            unsigned S, unsigned site0, unsigned nx,
-                                            unsigned nxy, int x0, bool wallx) {
+__device__ __forceinline__ typename Raw2<ST>::T pull_pair(const typename Store<ST>::T* __restrict__ f,
+                                                          unsigned S, unsigned site0, unsigned nx,
+                                                          unsigned nxy, int x0, bool wallx) {
     const unsigned row = (unsigned)J * S + site0 - ((unsigned)cy(J) * nx + (unsigned)cz(J) * nxy);
-    const float2 P = Vec2<ST>::load(f + row);   // the source row at (x0, x0 + 1)
+    const typename Raw2<ST>::T P = Raw2<ST>::load(f + row);   // the source row at (x0, x0 + 1)
     if (cx(J) == 0) return P;
     if (cx(J) == 1) {
         // node x0 receives x0 - 1, node x0 + 1 receives x0
         unsigned a = row - 1u;
         if (x0 == 0) a = wallx ? (unsigned)opp(J) * S + site0 : row + nx - 1u;
-        return make_float2(Store<ST>::load_raw(f + a), P.x);
+        return Raw2<ST>::lo_from(Raw2<ST>::load1(f + a), P);
     }
     // cx == -1: node x0 receives x0 + 1, node x0 + 1 receives x0 + 2
     unsigned a = row + 2u;
     if ((unsigned)x0 + 2u >= nx) a = wallx ? (unsigned)opp(J) * S + site0 + 1u : row - (unsigned)x0;
-    return make_float2(P.y, Store<ST>::load_raw(f + a));
+    return Raw2<ST>::hi_from(P, Raw2<ST>::load1(f + a));
 }
 
 template <int ST, int J>
-__device__ __forceinline__ float2 pull_pair_any(const typename Store<ST>::T* __restrict__ f,
-                                                const Geo& g, int x0, int y, int z) {
-    return make_float2(pull_raw_any<ST, J>(f, g, x0, y, z), pull_raw_any<ST, J>(f, g, x0 + 1, y, z));
+__device__ __forceinline__ typename Raw2<ST>::T pull_pair_any(
+    const typename Store<ST>::T* __restrict__ f, const Geo& g, int x0, int y, int z) {
+    int p0, i0, p1, i1;
+    pull_source<J>(g, x0, y, z, p0, i0);
+    pull_source<J>(g, x0 + 1, y, z, p1, i1);
+    return Raw2<ST>::join(Raw2<ST>::load1(f + (size_t)p0 * (size_t)g.S + i0),
+                          Raw2<ST>::load1(f + (size_t)p1 * (size_t)g.S + i1));
 }
 
 // c_j . v for direction J (J odd; J + 1 is its opposite), written with adds
@@ -420,7 +453,8 @@ struct PairStore {
 };
 
 template <int ST, int J, bool FORCED, class Sink>
-__device__ __forceinline__ void relax_pair2(Sink& sink, const float2 rv[Q], const RelaxK& k,
+__device__ __forceinline__ void relax_pair2(Sink& sink, const typename Raw2<ST>::T rv[Q],
+                                            const RelaxK& k,
                                             float2 ux, float2 uy, float2 uz, float2 Fx, float2 Fy,
                                             float2 Fz, float2 uF, const CollideParams& cp) {
     const float2 cu = c_dot<J>(ux, uy, uz);
@@ -434,17 +468,20 @@ __device__ __forceinline__ void relax_pair2(Sink& sink, const float2 rv[Q], cons
         odd = fma2(f2(3.0f * C * cp.pref), cF, odd);
     }
     const float2 om1 = f2(1.0f - cp.omega);
-    sink.template put<J>(fma2(om1, rv[J], add2(even, odd)));
-    sink.template put<J + 1>(fma2(om1, rv[J + 1], sub2(even, odd)));
+    sink.template put<J>(fma2(om1, Raw2<ST>::widen(rv[J]), add2(even, odd)));
+    sink.template put<J + 1>(fma2(om1, Raw2<ST>::widen(rv[J + 1]), sub2(even, odd)));
 }
 
 // Collision of one x-pair of nodes (Eq. 13, 6, 14, 12, 15) from its
-// pre-collision values rv (stored units); `live` pairs take part in the
-// stability flag.
+// pre-collision values rr (stored units, as loaded); `live` pairs take part in
+// the stability flag.
 template <int ST, bool FORCED, class Sink>
-__device__ __forceinline__ void collide_pair(Sink& sink, const float2 rv[Q], float2 Fx, float2 Fy,
-                                             float2 Fz, const CollideParams& cp, int* flag,
-                                             bool live) {
+__device__ __forceinline__ void collide_pair(Sink& sink, const typename Raw2<ST>::T rr[Q],
+                                             float2 Fx, float2 Fy, float2 Fz,
+                                             const CollideParams& cp, int* flag, bool live) {
+    float2 rv[Q];   // widened for the moments; the relaxation widens rr again
+#pragma unroll
+    for (int j = 0; j < Q; ++j) rv[j] = Raw2<ST>::widen(rr[j]);
     const float2 s_axis = add2(add2(add2(rv[1], rv[2]), add2(rv[3], rv[4])), add2(rv[5], rv[6]));
     const float2 s_edge = add2(add2(add2(add2(rv[7], rv[8]), add2(rv[9], rv[10])),
                                     add2(add2(rv[11], rv[12]), add2(rv[13], rv[14]))),
@@ -489,15 +526,27 @@ __device__ __forceinline__ void collide_pair(Sink& sink, const float2 rv[Q], flo
     float2 e0 = mul2(f2(cp.omega), base);
     if (FORCED) e0 = fma2(f2(-3.0f * cp.pref), uF, e0);
     const float C0 = Store<ST>::kScaled ? cp.scale : wf(0);
-    sink.template put<0>(fma2(f2(1.0f - cp.omega), rv[0], mul2(f2(C0), e0)));
+    sink.template put<0>(fma2(f2(1.0f - cp.omega), Raw2<ST>::widen(rr[0]), mul2(f2(C0), e0)));
     // One coefficient class for the 16-bit formats (C = scale); FP32 has
     // the axis and the diagonal weights.
     const RelaxK ka = relax_k((Store<ST>::kScaled ? cp.scale : wf(1)) * cp.omega, base, rho);
     const RelaxK ke = Store<ST>::kScaled ? ka : relax_k(wf(7) * cp.omega, base, rho);
-#define LBM_PAIR2(J, K) relax_pair2<ST, J, FORCED>(sink, rv, K, ux, uy, uz, Fx, Fy, Fz, uF, cp)
+#define LBM_PAIR2(J, K) relax_pair2<ST, J, FORCED>(sink, rr, K, ux, uy, uz, Fx, Fy, Fz, uF, cp)
     LBM_PAIR2(1, ka); LBM_PAIR2(3, ka); LBM_PAIR2(5, ka); LBM_PAIR2(7, ke); LBM_PAIR2(9, ke);
     LBM_PAIR2(11, ke); LBM_PAIR2(13, ke); LBM_PAIR2(15, ke); LBM_PAIR2(17, ke);
 #undef LBM_PAIR2
+}
+
+// The tile lists and records are read through L2 (ld.global.cg): with the
+// sweep overlapping the bubble update, they are written while the sweep runs,
+// so the read-only cache path is not used for them.
+__device__ __forceinline__ BubbleRec load_rec(const BubbleRec* p) {
+    const int4* q = reinterpret_cast<const int4*>(p);
+    const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    return BubbleRec{a.x, a.y, a.z, a.w,
+                     __int_as_float(b.x), __int_as_float(b.y), __int_as_float(b.z),
+                     __int_as_float(b.w), __int_as_float(c.x), __int_as_float(c.y),
+                     __int_as_float(c.z), __int_as_float(c.w)};
 }
 
 // Eq. 21 at the pair (x0, x0 + 1), (y, z) of a block whose tile lists n_t > 0
@@ -520,7 +569,7 @@ __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __re
     constexpr int FB = FORCE_CHUNK, NAX = TX + TY + PZ;
     __shared__ float s_w[FB][NAX];   // x: [0, TX), y: [TX, TX + TY), z: the rest
     const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
-    const int beg = tile_start[t];
+    const int beg = __ldcg(tile_start + t);
     const int end = min(beg + n_t, cap);
     const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
     constexpr int NT = PX * TY * PZ;
@@ -529,8 +578,8 @@ __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __re
         const int cnt = min(FB, end - c0);
         __syncthreads();
         if (tid < cnt) {
-            const int id = items[c0 + tid];
-            if (id >= 0 && id < nb) srec[tid] = recs[id];
+            const int id = __ldcg(items + c0 + tid);
+            if (id >= 0 && id < nb) srec[tid] = load_rec(recs + id);
             else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         }
         __syncthreads();
@@ -574,7 +623,8 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
                                             const int* __restrict__ items, int cap,
                                             const BubbleRec* __restrict__ recs, int nb,
                                             int* __restrict__ flag, int bx, int by, int bz,
-                                            BubbleRec* srec) {
+                                            BubbleRec* srec, const unsigned* safe = nullptr,
+                                            unsigned epoch = 0) {
     const int x0 = bx * TX + 2 * threadIdx.x;
     const int y = by * TY + threadIdx.y;
     const int z = bz * PZ + threadIdx.z;
@@ -583,14 +633,22 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     const int xa = active ? x0 : 0;
     const int ya = min(y, g.ny - 1), za = min(z, g.nz - 1);
 
-    const int n_t = tile_count != nullptr
-                        ? tile_count[(((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx]
-                        : 0;
+    const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
+    // Read before the population loads: in plain stream order the tile count;
+    // overlapped with the bubble update, the guard tag of this z layer (written
+    // by the update before, which has completed).  CTA 0 never skips, so the
+    // sweep cannot complete before the update.
+    int n_t = 0;
+    bool skip = false;
+    if (tile_count != nullptr) {
+        if (safe == nullptr) n_t = __ldcg(tile_count + t);
+        else skip = (bx | by | bz) != 0 && __ldcg(safe + (bz * PZ) / TZ) == epoch;
+    }
 
     const unsigned S = (unsigned)g.S;
     const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
     const unsigned site0 = (unsigned)za * nxy + (unsigned)ya * nx + (unsigned)xa;
-    float2 rv[Q];
+    typename Raw2<ST>::T rv[Q];
     if (ya > 0 && ya < g.ny - 1 && za > 0 && za < g.nz - 1) {
         const bool wallx = (g.walls & 0x01) != 0;
 #define LBM_PP(J) rv[J] = pull_pair<ST, J>(fin, S, site0, nx, nxy, xa, wallx)
@@ -607,6 +665,12 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
         LBM_PA(15); LBM_PA(16); LBM_PA(17); LBM_PA(18);
 #undef LBM_PA
     }
+    if (tile_count != nullptr && safe != nullptr && !skip) {
+        // Overlapped, and the update before did not clear this layer: wait
+        // for this step's update, then read its tile lists.
+        pdl_wait();
+        n_t = __ldcg(tile_count + t);
+    }
     // The force gather (Eq. 21) runs after the population loads are issued,
     // so the tile-list lookup does not delay them.
     float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
@@ -619,16 +683,15 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
         Fz = F.z;
     } else if (forced) {
         // Few bubbles per tile: each node evaluates its listed bubbles directly.
-        const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
-        const int beg = tile_start[t];
+        const int beg = __ldcg(tile_start + t);
         const int end = min(beg + n_t, cap);
         const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
         for (int c0 = beg; c0 < end; c0 += FORCE_CHUNK) {
             const int cnt = min(FORCE_CHUNK, end - c0);
             __syncthreads();
             if (tid < cnt) {
-                const int id = items[c0 + tid];
-                if (id >= 0 && id < nb) srec[tid] = recs[id];
+                const int id = __ldcg(items + c0 + tid);
+                if (id >= 0 && id < nb) srec[tid] = load_rec(recs + id);
                 else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             }
             __syncthreads();
@@ -649,12 +712,15 @@ template <int ST, bool TAB>
 __global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
 k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                       typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
-                      const int* __restrict__ tile_start, const int* __restrict__ tile_count,
-                      const int* __restrict__ items, int cap,
-                      const BubbleRec* __restrict__ recs, int nb, int* __restrict__ flag) {
+                      const int* tile_start, const int* tile_count, const int* items, int cap,
+                      const BubbleRec* recs, int nb, int* __restrict__ flag,
+                      const unsigned* safe, unsigned epoch) {
     __shared__ BubbleRec srec[FORCE_CHUNK];
+    // The next bubble update may be scheduled once every CTA of the sweep has
+    // started; it waits for the sweep to complete before it reads anything.
+    pdl_trigger();
     sweep_block<ST, TAB>(fin, fout, g, cp, tile_start, tile_count, items, cap, recs, nb, flag,
-                         blockIdx.x, blockIdx.y, blockIdx.z, srec);
+                         blockIdx.x, blockIdx.y, blockIdx.z, srec, safe, epoch);
 }
 
 // ---------------------------------------------------------------------------
@@ -741,24 +807,33 @@ int pair_min_blocks(int storage) {
 
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
-                                  const BubbleRec* recs, int nb, int* flag, cudaStream_t st) {
+                                  const BubbleRec* recs, int nb, int* flag, const unsigned* safe,
+                                  unsigned epoch, bool overlap, cudaStream_t st) {
     const int* start = tl ? tl->start : nullptr;
     const int* count = tl ? tl->count : nullptr;
     const int* items = tl ? tl->items : nullptr;
     const int cap = tl ? tl->cap : 0;
+    if (overlap && (safe == nullptr || tl == nullptr)) return cudaErrorInvalidValue;
+    if (!overlap) safe = nullptr;
     if ((g.nx & 1) == 0) {
         // Even rows: two nodes per thread with aligned vector accesses.  Tile
         // lists longer than the few-bubble path's (many bubbles per tile)
         // take the tabulated force gather.
-        dim3 block(PX, TY, PZ);
-        dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + PZ - 1) / PZ);
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(PX, TY, PZ);
+        cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + PZ - 1) / PZ);
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = overlap ? 1 : 0;
         const bool tab = tl != nullptr && tl->cap > SMALL_MAX_PAIRS;
         switch (storage * 2 + (tab ? 1 : 0)) {
 #define LBM_LAUNCH_PAIR(SI, TB, T)                                                                \
     case SI * 2 + TB:                                                                             \
-        k_collide_stream_pair<SI, TB><<<grid, block, 0, st>>>(                                    \
-            (const T*)fin, (T*)fout, g, cp, start, count, items, cap, recs, nb, flag);            \
-        break;
+        return cudaLaunchKernelEx(&cfg, k_collide_stream_pair<SI, TB>, (const T*)fin, (T*)fout,   \
+                                  g, cp, start, count, items, cap, recs, nb, flag, safe, epoch);
             LBM_LAUNCH_PAIR(0, 0, float)
             LBM_LAUNCH_PAIR(0, 1, float)
             LBM_LAUNCH_PAIR(1, 0, __half)
@@ -769,8 +844,8 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
             default:
                 return cudaErrorInvalidValue;
         }
-        return cudaGetLastError();
     }
+    if (overlap) return cudaErrorInvalidValue;   // odd rows: plain stream order only
     dim3 block(TX, TY, 1);
     dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, g.nz);
     switch (storage) {

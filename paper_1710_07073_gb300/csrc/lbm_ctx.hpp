@@ -44,6 +44,11 @@ struct lbm_ctx {
     SmallBins small{};
     bool use_small = false;
     bool bins_valid = false;
+    // Number of the next step for the overlap guard (small.safe holds two
+    // tag sets of ntz, by step parity).  Any change of the bubble state
+    // outside a step moves it past every stored tag (guard_invalidate), so
+    // stale tags never clear a layer.
+    unsigned epoch = 1;
     // Large path: Eq. 10 velocity of the covered tiles (3 planes of S floats)
     // and whether bins.cnt marks the windows of the current centres.
     float* mom = nullptr;
@@ -74,6 +79,9 @@ lbm::BubbleConst bubble_const(const lbm_ctx* c);
 int ensure_device(lbm_ctx* c);
 // One coupled step on the context stream (the body of lbm_step's loop).
 int enqueue_one_step(lbm_ctx* c);
+// The bubble state changed outside a step: no stored guard tag may clear a
+// layer for the next step.
+void guard_invalidate(lbm_ctx* c);
 int finish_steps(lbm_ctx* c);
 void adjoint_free(lbm_ctx* c);
 

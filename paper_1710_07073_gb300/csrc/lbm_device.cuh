@@ -7,6 +7,16 @@
 
 namespace lbm {
 
+// ---- programmatic dependent launch -----------------------------------------
+// pdl_wait: block until the grids this one was launched to overlap with have
+// completed and their writes are visible (returns at once for a grid launched
+// in plain stream order).  pdl_trigger: this CTA no longer holds back the
+// launch of the grid queued after this one.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ---- population storage ------------------------------------------------------
 // Stored value of population j is the shifted deviation g_j = f_j - w_j rho0:
 // as is for FP32, times scale / w_j for the 16-bit formats.  load/store convert

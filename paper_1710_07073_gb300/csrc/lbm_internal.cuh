@@ -175,7 +175,23 @@ struct SmallBins {
     int parts;         // CTAs per bubble in the update, 1..WINDOW_CHUNKS_MAX
     float* part;       // [nb * WINDOW_CHUNKS_MAX * 3] chunk sums (parts > 1)
     int* arrive;       // [nb] CTAs of a bubble that have finished (0 between launches)
+    // Overlap guard (single column): safe[l] = e states that no bubble force
+    // reaches z tile layer l in the step numbered e.  The update writes
+    // safe_epoch (the next step's number) into the layers that no active
+    // bubble's support, widened by GUARD_CELLS, touches; the context keeps
+    // one set of ntz tags per step parity, so an update never rewrites the
+    // set its own sweep reads.  Null: not kept.
+    unsigned* safe;    // [ntz] (the set this launch writes)
+    unsigned safe_epoch;
 };
+
+// A bubble moves at most this many cells along an axis per liquid step (a
+// lattice speed of 4 is far past any stable state); a faster one raises the
+// instability flag (bit 4).  The overlap guard relies on it.
+constexpr int GUARD_CELLS = 4;
+// Tile layers the guard covers (nz <= 4 GUARD_LAYERS_MAX); taller columns keep
+// no guard.
+constexpr int GUARD_LAYERS_MAX = 2048;
 
 // One column of a batch: its geometry and relaxation, where its populations
 // start in the batch buffers (elements), and the first global tile and work
@@ -189,15 +205,21 @@ struct BatchColumn {
 };
 
 // ---- launchers (defined in the kernel translation units) -------------------
+// The sweep.  With `safe` set it is launched as a programmatic dependent of
+// the bubble update before it (`overlap`): CTAs whose z tile layer holds
+// safe[layer] == epoch run without waiting for the update; the others (and
+// CTA 0) wait for it before reading the tile lists.
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
-                                  const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
+                                  const BubbleRec* recs, int nb, int* flag, const unsigned* safe,
+                                  unsigned epoch, bool overlap, cudaStream_t st);
 
 // Bubble update with the few-pair binning in the same launch (sb.parts CTAs
-// per bubble).
+// per bubble).  `overlap`: launched as a programmatic dependent of the sweep
+// before it; it waits for that sweep, then lets the next sweep start.
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag,
-                           const SmallBins& sb, cudaStream_t st);
+                           const SmallBins& sb, bool overlap, cudaStream_t st);
 // CTAs per bubble for windows of half-width up to max_half_width: one per
 // 256-node chunk of the largest window.
 int window_parts(double max_half_width);

@@ -1,0 +1,101 @@
+"""GPU: the bubble update overlapped with the sweep gives the same bits as plain
+stream order.
+
+A single column with few bubbles runs each step's bubble update (Algorithm 1
+steps 2-6) and the collide-stream sweep (Eq. 12-16, 21) as overlapping
+launches: sweep CTAs whose z tile layer the previous update cleared (no
+bubble support, widened by 4 cells, reaches it) do not wait for the update.
+With kernel timing on, the library keeps plain stream order instead, so the
+two runs below differ only in that scheduling; every population and bubble
+value must agree bit for bit.  A bubble faster than 4 cells per step is
+reported as an instability.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import lattice as olat
+from paper_1710_07073_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu_library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    assert os.path.exists(lbm.LIB_PATH), "liblbm.so must be built (run __graft_entry__.build())"
+    torch.cuda.init()
+
+
+def _run(dims, walls, pos, vel, diam, steps, plain, storage=lbm.LBM_STORE_F32, scale=1.0,
+         g=1e-2, chunks=1):
+    p = lbm.lbm_default_params()
+    p.g = g
+    col = lbm.Column(dims, 1.6, walls, storage, scale, params=p)
+    lbm.lbm_set_bubbles(col.ctx, np.asarray(pos, float).reshape(-1),
+                        np.asarray(vel, float).reshape(-1), np.asarray(diam, float))
+    lbm.lbm_set_kernel_timing(col.ctx, plain)
+    for _ in range(chunks):
+        lbm.lbm_step(col.ctx, steps // chunks)
+    f = lbm.lbm_get_populations(col.ctx)
+    b = lbm.lbm_get_bubbles(col.ctx)
+    col.close()
+    return f, b
+
+
+def _assert_same(a, b):
+    fa, ba = a
+    fb, bb = b
+    assert np.array_equal(fa, fb)
+    for k in ("pos", "vel", "active"):
+        assert np.array_equal(ba[k], bb[k]), k
+
+
+# Bubbles rising at ~0.02-0.05 cells per step cross tile layers (4 cells).
+CASES = {
+    "walls, one bubble": ((32, 16, 40), olat.ALL_WALLS, [[16.0, 8.0, 7.7]], [[0, 0, 0.05]],
+                          [2.0]),
+    "periodic z, wraps through the top": (
+        (32, 16, 24), olat.WALL_XM | olat.WALL_XP | olat.WALL_YM | olat.WALL_YP,
+        [[12.0, 8.0, 21.5]], [[0, 0, 0.05]], [1.5]),
+    "three bubbles": ((64, 16, 48), olat.ALL_WALLS,
+                      [[10.0, 8.0, 6.0], [40.0, 6.0, 20.2], [52.5, 9.5, 33.9]],
+                      [[0, 0, 0.04], [0.01, 0, 0.03], [0, -0.01, 0.05]], [2.0, 1.6, 2.4]),
+    "window split over CTAs": ((48, 32, 48), olat.ALL_WALLS, [[24.0, 16.0, 11.9]],
+                               [[0, 0, 0.05]], [4.0]),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_overlapped_steps_match_plain_order(case):
+    dims, walls, pos, vel, diam = CASES[case]
+    plain = _run(dims, walls, pos, vel, diam, 240, plain=True)
+    over = _run(dims, walls, pos, vel, diam, 240, plain=False, chunks=3)
+    _assert_same(plain, over)
+    # the bubbles did move across at least one tile layer boundary
+    z0 = np.asarray(pos, float)[:, 2]
+    z1 = over[1]["pos"][:, 2]
+    assert np.any(np.floor(z0 / 4) != np.floor(z1 / 4))
+
+
+@pytest.mark.parametrize("storage,scale", [(lbm.LBM_STORE_F16, 256.0),
+                                           (lbm.LBM_STORE_BF16, 1.0)])
+def test_overlapped_steps_match_plain_order_16bit(storage, scale):
+    dims, walls, pos, vel, diam = CASES["three bubbles"]
+    plain = _run(dims, walls, pos, vel, diam, 120, plain=True, storage=storage, scale=scale)
+    over = _run(dims, walls, pos, vel, diam, 120, plain=False, storage=storage, scale=scale)
+    _assert_same(plain, over)
+
+
+def test_bubble_faster_than_guard_is_unstable():
+    # u_b = 20 cells per step: the drag slows it to ~9 over the step's
+    # sub-steps, so it moves ~14 cells, past the 4-cell bound.
+    dims = (32, 32, 64)
+    walls = olat.WALL_XM | olat.WALL_XP | olat.WALL_YM | olat.WALL_YP
+    col = lbm.Column(dims, 1.6, walls)
+    lbm.lbm_set_bubbles(col.ctx, [16.0, 16.0, 20.0], [0.0, 0.0, 20.0], [2.0])
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step(col.ctx, 1)
+    assert e.value.code == lbm.LBM_ERR_UNSTABLE
