@@ -29,8 +29,9 @@
  * LBM_ERR_* code; the context keeps a message readable with
  * lbm_last_error.  LBM_ERR_UNSTABLE is sticky: once the liquid solver has
  * flagged a non-finite value or |u| >= 0.3 (beyond the low-Mach range of
- * Eq. 6) every later lbm_step returns it until the state is reset with
- * lbm_set_fields or lbm_set_populations.
+ * Eq. 6), or a bubble has moved more than 4 cells along an axis in one step
+ * (a lattice speed of 4), every later lbm_step returns it until the state is
+ * reset with lbm_set_fields or lbm_set_populations.
  *
  * Threads.  A context may be used from one host thread at a time.  All work
  * is enqueued on the context's CUDA stream (lbm_set_stream); calls that
@@ -163,6 +164,11 @@ int lbm_set_bubbles(lbm_ctx* ctx, int n, const double* pos3, const double* vel3,
  *      applies Eq. 13, 6, 14, 12, 15 and streams (Eq. 16) with bounce-back;
  *   4. a bubble whose centre reached nz - r_b under a +z wall is deactivated
  *      (Algorithm 1, stop at the top) after spreading this step.
+ * With few bubbles (the single-launch binning) on even-nx lattices, a step's
+ * sweep may start while its bubble update still runs: lattice z layers that
+ * no bubble can reach this step (support widened by 4 cells) do not wait for
+ * it.  Results are the same bits as with the two in stream order (which the
+ * library keeps while kernel timing is on).
  * Returns after the work has completed, with LBM_ERR_UNSTABLE if flagged. */
 int lbm_step(lbm_ctx* ctx, int nsteps);
 
