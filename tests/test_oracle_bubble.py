@@ -127,3 +127,36 @@ def test_wall_clamp_and_periodic_wrap():
     x, u, _ = bub.advance([4.0, 4.0, 15.99], [0.0, 0.0, 0.1], d, np.zeros(3), np.zeros(3),
                           (8, 8, 16), lat.WALL_XM | lat.WALL_XP | lat.WALL_YM | lat.WALL_YP, p)
     assert 0.0 <= x[2] < 1.0
+
+
+def test_added_mass_liquid_acceleration_closed_form():
+    # Table 1's virtual-mass force carries C_A rho_l V_b D_t u_l.  With linear
+    # (Stokes) drag F_D = -K (u - u_l), K = 3 pi rho_l nu d, a constant u_l and
+    # a constant D_t u_l, the explicit update of Eq. 4 with m_eff is the
+    # geometric sequence u_k = v_inf (1 - q^k) from rest, with
+    # v_inf = u_l + (F_B + C_A rho_l V_b D_t u_l) / K and q = 1 - K dt_b / m_eff.
+    # Position: x_k = x_0 + sum_{i <= k} u_i dt_b; reaction: minus the mean drag
+    # of a liquid step's sub-steps, psi = K/N sum (u_i - u_l).
+    p = bub.BubbleParams(1.7, sn_coeff=0.0, sigma=1e30)
+    d = 1.8
+    dims = (64, 64, 64)
+    ul = np.array([1e-4, -2e-4, 3e-4])
+    dul = np.array([2e-6, 1e-6, -3e-6])
+    kdrag = 3.0 * math.pi * p.rho_l * p.nu * d
+    meff = bub.effective_mass(d, p)
+    force = bub.buoyancy_force(d, p) + p.c_added_mass * p.rho_l * bub.volume(d) * dul
+    vinf = ul + force / kdrag
+    q = 1.0 - kdrag * p.dt_b / meff
+    x0 = np.array([32.0, 32.0, 20.0])
+    x, u = x0.copy(), np.zeros(3)
+    xs = x0.copy()
+    for step in range(1, 11):
+        k0 = (step - 1) * p.substeps
+        x, u, psi = bub.advance(x, u, d, ul, dul, dims, lat.ALL_WALLS, p)
+        k = step * p.substeps
+        np.testing.assert_allclose(u, vinf * (1.0 - q ** k), rtol=1e-11, atol=0)
+        xs = xs + sum(vinf * (1.0 - q ** i) for i in range(k0 + 1, k + 1)) * p.dt_b
+        np.testing.assert_allclose(x, xs, rtol=1e-14, atol=0)
+        start = [vinf * (1.0 - q ** i) for i in range(k0, k)]   # velocity at each sub-step's start
+        psi_exp = kdrag / p.substeps * sum(s - ul for s in start)
+        np.testing.assert_allclose(psi, psi_exp, rtol=1e-10, atol=0)

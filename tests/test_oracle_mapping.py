@@ -131,3 +131,41 @@ def test_tile_lists_by_hand():
     expect = {4: [0], 5: [0], 2: [2]}
     for t in range(8):
         assert items[off[t]:off[t + 1]] == expect.get(t, [])
+
+
+def test_interpolation_hand_computed_two_cells():
+    # Eq. 18-20 by hand: half-width n = 1/2 around x_b = 5.25 touches cells 4
+    # ([4, 5], node 4.5) and 5 ([5, 6], node 5.5).  With s = r/n the cell
+    # integral of Z is 15/16 [s^5/5 - 2 s^3/3 + s] between the cell's ends:
+    # cell 4 spans s in [-1, -1/2], giving 15/16 (-203/480 + 256/480) = 53/512,
+    # and cell 5 the remaining 459/512.  A linear field sampled at the nodes
+    # interpolates to 4.5 * 53/512 + 5.5 * 459/512 = 2763/512.
+    cells, w = mapping.axis_window(5.25, 0.5, 12, False)
+    assert list(cells) == [4, 5]
+    assert w[0] == pytest.approx(53.0 / 512.0, abs=1e-15)
+    assert w[1] == pytest.approx(459.0 / 512.0, abs=1e-15)
+    dims = (12, 12, 12)
+    x_nodes = np.arange(dims[0]) + 0.5
+    sigma = np.broadcast_to(x_nodes[None, None, None, :], (1, 12, 12, 12)).copy()
+    out = mapping.interpolate(sigma, (5.25, 6.0, 6.0), 0.5, lat.ALL_WALLS)
+    assert out[0] == pytest.approx(2763.0 / 512.0, abs=1e-13)
+
+
+@pytest.mark.parametrize("n,tol", [(1.5, 3e-3), (3.0, 2e-4)])
+def test_interpolation_reproduces_linear_field(n, tol):
+    # The weights are the cell integrals of a symmetric Z, so their first
+    # moment over the node centres i + 1/2 lies within a small fraction of a
+    # cell of x_b (the sawtooth floor(x) + 1/2 - x integrated against Z): a
+    # linear field u = a x + b interpolates to a x_b + b.  Nodes placed half a
+    # cell off (at i or i + 1) would miss by |a| / 2.
+    rng = np.random.default_rng(3)
+    dims = (32, 32, 32)
+    c = np.arange(32) + 0.5
+    a = np.array([0.3, -0.7, 1.1])
+    b = 0.25
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")   # [z, y, x] node centres
+    sigma = np.stack([a[0] * xx + b, a[1] * yy + b, a[2] * zz + b])
+    for _ in range(60):
+        xb = rng.uniform(n + 1.0, 31.0 - n, 3)
+        out = mapping.interpolate(sigma, xb, n, lat.ALL_WALLS)
+        assert np.all(np.abs(out - (a * xb + b)) <= tol * np.abs(a)), (xb, out)
