@@ -308,7 +308,13 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  *                            shape lbm_get_bins reports, T = ceil(nx/32) *
  *                            ceil(ny/4) * ceil(nz/4), numbered x-fastest;
  *   tile_items  int[cap_items] out: bubble ids, ascending within each tile;
- *   status      int[1]       out: 0, or 1 if more than cap_items ids were due.
+ *   status      int[1]       out: bit flags, 0 when all is well:
+ *                            1  more than cap_items ids were due (the list
+ *                               is cut);
+ *                            2  a bubble was skipped: a non-finite centre or
+ *                               half-width, a half-width outside
+ *                               (0, LBM_NOALLOC_MAX_HALF_WIDTH], or a centre
+ *                               outside [0, L) on some axis.
  * The work is enqueued on `stream` (a cudaStream_t, may be NULL) and is
  * complete when that stream is.  The first call on a device looks up the
  * scratch array's device address for that device (a CUDA runtime query);
@@ -318,6 +324,9 @@ const char* lbm_batch_last_error(const lbm_batch* b);
  * Returns LBM_ERR_ARG for bad sizes or walls, or when T exceeds
  * LBM_NOALLOC_MAX_TILES; LBM_ERR_CUDA if a CUDA call fails. */
 #define LBM_NOALLOC_MAX_TILES 262144
+#define LBM_NOALLOC_MAX_HALF_WIDTH 9.0
+#define LBM_NOALLOC_STATUS_OVERFLOW 1
+#define LBM_NOALLOC_STATUS_SKIPPED  2
 int lbm_bin_bubbles_noalloc(int nx, int ny, int nz, unsigned walls, int n,
                             const double* pos3, const double* half_width, const int* active,
                             int* tile_offsets, int* tile_items, int cap_items, int* status,
@@ -325,6 +334,13 @@ int lbm_bin_bubbles_noalloc(int nx, int ny, int nz, unsigned walls, int n,
 
 /* Number of kernels this context has launched since it was created. */
 long long lbm_launch_count(const lbm_ctx* ctx);
+
+/* Name of the collide-stream kernel (step 3 of lbm_step) that the next step
+ * of this context launches, for reports that pair timings with profiles:
+ * the two-node sweep "k_collide_stream_pair<S,T>" (even nx; S the storage
+ * code, T = 1 for the tabulated force gather of long tile lists) or
+ * "k_collide_stream<S>" (odd nx).  A static string; "" for NULL. */
+const char* lbm_sweep_kernel(const lbm_ctx* ctx);
 
 /* Wait for all work enqueued by this context. */
 int lbm_sync(lbm_ctx* ctx);

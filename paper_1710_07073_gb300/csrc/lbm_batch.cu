@@ -185,10 +185,7 @@ int ensure_device(lbm_batch* b) {
     }
     layout_columns(b);
     const size_t bytes = (size_t)b->total_elems * elem_bytes(b->storage);
-    for (int k = 0; k < 2; ++k) {
-        b->f[k] = balloc(b, bytes);
-        if (!b->f[k]) return bfail(b, LBM_ERR_ALLOC, "population buffer of %zu bytes", bytes);
-    }
+    for (int k = 0; k < 2; ++k) b->f[k] = balloc(b, bytes);
     b->cols_d = (BatchColumn*)balloc(b, sizeof(BatchColumn) * b->ncols);
     b->col_nu_d = (double*)balloc(b, sizeof(double) * b->ncols);
     b->flag_d = (int*)balloc(b, sizeof(int));
@@ -202,10 +199,23 @@ int ensure_device(lbm_batch* b) {
     sb.prev_n = (int*)balloc(b, sizeof(int));
     sb.overflow = (int*)balloc(b, sizeof(int));
     sb.done = (int*)balloc(b, sizeof(int));
-    if (!b->cols_d || !b->col_nu_d || !b->flag_d || !b->work_counter || !sb.start || !sb.count ||
-        !sb.items || !sb.prev_tiles || !sb.prev_n || !sb.overflow || !sb.done)
-        return bfail(b, LBM_ERR_ALLOC, "batch state");
-    LBM_BCUDA(cudaMallocHost((void**)&b->flag_h, sizeof(int)), "cudaMallocHost");
+    if (!b->f[0] || !b->f[1] || !b->cols_d || !b->col_nu_d || !b->flag_d || !b->work_counter ||
+        !sb.start || !sb.count || !sb.items || !sb.prev_tiles || !sb.prev_n || !sb.overflow ||
+        !sb.done) {
+        // All or nothing: free what this call allocated so that the batch
+        // stays destroyable and a later call may retry.
+        void** owned[] = {&b->f[0], &b->f[1], (void**)&b->cols_d, (void**)&b->col_nu_d,
+                          (void**)&b->flag_d, (void**)&b->work_counter, (void**)&sb.start,
+                          (void**)&sb.count, (void**)&sb.items, (void**)&sb.prev_tiles,
+                          (void**)&sb.prev_n, (void**)&sb.overflow, (void**)&sb.done};
+        for (void** q : owned) {
+            bfree(b, *q);
+            *q = nullptr;
+        }
+        return bfail(b, LBM_ERR_ALLOC, "batch device state (%zu bytes per population buffer)",
+                     bytes);
+    }
+    if (!b->flag_h) LBM_BCUDA(cudaMallocHost((void**)&b->flag_h, sizeof(int)), "cudaMallocHost");
     cudaStream_t s = b->stream;
     LBM_BCUDA(cudaMemsetAsync(b->f[0], 0, bytes, s), "memset f");
     LBM_BCUDA(cudaMemsetAsync(b->flag_d, 0, sizeof(int), s), "flag");

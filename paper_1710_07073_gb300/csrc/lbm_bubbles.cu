@@ -630,11 +630,27 @@ __global__ void k_bin(Geo g, BubbleDev B, Bins bins, const int* __restrict__ sel
     if (b >= B.nb || !select[b]) return;
     const int L[3] = {g.nx, g.ny, g.nz};
     const int T[3] = {TX, TY, TZ};
+    if (B.x) {
+        // FP64 centres and half-widths from the caller (binning without a
+        // context) never passed lbm_set_bubbles' checks: a non-finite value,
+        // a half-width outside (0, MAX_HALF_WIDTH] or a centre outside the
+        // box skips the bubble and sets bit 2 of the status word.
+        const double n = B.n[b];
+        bool ok = isfinite(n) && n > 0.0 && n <= MAX_HALF_WIDTH;
+        for (int a = 0; a < 3; ++a) {
+            const double xa = B.x[3 * b + a];
+            ok = ok && isfinite(xa) && xa >= 0.0 && xa < (double)L[a];
+        }
+        if (!ok) {
+            atomicOr(bins.overflow, 2);
+            return;
+        }
+    }
     int tl[3][MAX_AXIS_TILES];
     int nt[3];
     for (int a = 0; a < 3; ++a) {
         int lo, hi;
-        if (B.x) {   // FP64 centres from the caller (binning without a context)
+        if (B.x) {
             const double xa = B.x[3 * b + a], n = B.n[b];
             lo = (int)floor(xa - n);
             hi = (int)ceil(xa + n) - 1;

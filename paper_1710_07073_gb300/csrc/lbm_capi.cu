@@ -100,31 +100,39 @@ BubbleConst bubble_const(const lbm_ctx* c) {
     return bc;
 }
 
+// Device state of a context, allocated on first use.  All or nothing: if
+// any allocation fails, what this call allocated is freed again, so the
+// context stays destroyable and a later call may retry.
 int ensure_device(lbm_ctx* c) {
     if (c->dev_ready) return LBM_OK;
     LBM_CUDA(cudaGetDevice(&c->device), "cudaGetDevice");
     const Geo g = geo_of(c);
     const size_t bytes = (size_t)Q * (size_t)g.S * elem_size(c->storage);
-    for (int k = 0; k < 2; ++k) {
-        c->f[k] = dalloc(c, bytes);
-        if (!c->f[k]) return fail(c, LBM_ERR_ALLOC, "population buffer of %zu bytes", bytes);
-    }
-    c->flag_d = (int*)dalloc(c, sizeof(int));
-    if (!c->flag_d) return fail(c, LBM_ERR_ALLOC, "flag");
-    LBM_CUDA(cudaMallocHost((void**)&c->flag_h, sizeof(int)), "cudaMallocHost");
-    // Rest state f = f^eq(rho_l, 0) has zero shifted value in every format.
-    LBM_CUDA(cudaMemsetAsync(c->f[0], 0, bytes, c->stream), "memset f");
-    LBM_CUDA(cudaMemsetAsync(c->flag_d, 0, sizeof(int), c->stream), "memset flag");
-    c->cur = 0;
-    // Tile bookkeeping.
     c->bins.T = g.ntx * g.nty * g.ntz;
     c->bins.nblocks = scan_blocks(c->bins.T);
+    for (int k = 0; k < 2; ++k) c->f[k] = dalloc(c, bytes);
+    c->flag_d = (int*)dalloc(c, sizeof(int));
     c->bins.cnt = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.T);
     c->bins.off = (int*)dalloc(c, sizeof(int) * ((size_t)c->bins.T + 1));
     c->bins.block_sums = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.nblocks);
     c->bins.overflow = (int*)dalloc(c, sizeof(int));
-    if (!c->bins.cnt || !c->bins.off || !c->bins.block_sums || !c->bins.overflow)
-        return fail(c, LBM_ERR_ALLOC, "tile bins");
+    if (!c->f[0] || !c->f[1] || !c->flag_d || !c->bins.cnt || !c->bins.off ||
+        !c->bins.block_sums || !c->bins.overflow) {
+        void** owned[] = {&c->f[0], &c->f[1], (void**)&c->flag_d, (void**)&c->bins.cnt,
+                          (void**)&c->bins.off, (void**)&c->bins.block_sums,
+                          (void**)&c->bins.overflow};
+        for (void** q : owned) {
+            dfree(c, *q);
+            *q = nullptr;
+        }
+        return fail(c, LBM_ERR_ALLOC, "device state of the column (%zu bytes per population "
+                    "buffer)", bytes);
+    }
+    if (!c->flag_h) LBM_CUDA(cudaMallocHost((void**)&c->flag_h, sizeof(int)), "cudaMallocHost");
+    // Rest state f = f^eq(rho_l, 0) has zero shifted value in every format.
+    LBM_CUDA(cudaMemsetAsync(c->f[0], 0, bytes, c->stream), "memset f");
+    LBM_CUDA(cudaMemsetAsync(c->flag_d, 0, sizeof(int), c->stream), "memset flag");
+    c->cur = 0;
     LBM_CUDA(cudaMemsetAsync(c->bins.overflow, 0, sizeof(int), c->stream), "memset overflow");
     c->bins.items = nullptr;
     c->bins.cap = 0;
@@ -742,6 +750,21 @@ int lbm_get_kernel_time(lbm_ctx* c, double* ms, int* launches) {
 }
 
 long long lbm_launch_count(const lbm_ctx* c) { return c ? c->launches : 0; }
+
+const char* lbm_sweep_kernel(const lbm_ctx* c) {
+    if (!c) return "";
+    // The choice launch_collide_stream makes for this context's next step.
+    static const char* const pair[3][2] = {
+        {"k_collide_stream_pair<0,0>", "k_collide_stream_pair<0,1>"},
+        {"k_collide_stream_pair<1,0>", "k_collide_stream_pair<1,1>"},
+        {"k_collide_stream_pair<2,0>", "k_collide_stream_pair<2,1>"}};
+    static const char* const single[3] = {"k_collide_stream<0>", "k_collide_stream<1>",
+                                          "k_collide_stream<2>"};
+    const int st = c->storage < 0 || c->storage > 2 ? 0 : c->storage;
+    if (c->nx & 1) return single[st];
+    const bool tab = c->bub.nb > 0 && c->p.two_way && !c->use_small;
+    return pair[st][tab ? 1 : 0];
+}
 
 int lbm_sync(lbm_ctx* c) {
     if (!c) return LBM_ERR_ARG;

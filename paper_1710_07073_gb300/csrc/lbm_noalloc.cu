@@ -18,6 +18,9 @@ using namespace lbm;
 
 namespace {
 
+static_assert(LBM_NOALLOC_MAX_HALF_WIDTH == MAX_HALF_WIDTH,
+              "the header's half-width limit is the one the binning kernels check");
+
 constexpr int NOALLOC_SCAN_CHUNK = 1024;   // counts per scan block (matches scan_blocks)
 constexpr int NOALLOC_MAX_BLOCKS =
     (LBM_NOALLOC_MAX_TILES + NOALLOC_SCAN_CHUNK - 1) / NOALLOC_SCAN_CHUNK;

@@ -117,6 +117,7 @@ def lib():
         "lbm_batch_sync": (i, [vp]),
         "lbm_batch_last_error": (ctypes.c_char_p, [vp]),
         "lbm_bin_bubbles_noalloc": (i, [i, i, i, u, i, vp, vp, vp, vp, vp, i, vp, vp]),
+        "lbm_sweep_kernel": (ctypes.c_char_p, [vp]),
         "lbm_sync": (i, [vp]),
         "lbm_last_error": (ctypes.c_char_p, [vp]),
         "lbm_status_string": (ctypes.c_char_p, [i]),
@@ -331,6 +332,9 @@ def lbm_adj_backward(ctx, dloss=1.0, want_u0=True):
 
 
 LBM_NOALLOC_MAX_TILES = 262144
+LBM_NOALLOC_MAX_HALF_WIDTH = 9.0
+LBM_NOALLOC_STATUS_OVERFLOW = 1
+LBM_NOALLOC_STATUS_SKIPPED = 2
 
 
 def lbm_bin_bubbles_noalloc(nx, ny, nz, walls, n, pos3_ptr, half_width_ptr, active_ptr,
@@ -348,6 +352,10 @@ def lbm_bin_bubbles_noalloc(nx, ny, nz, walls, n, pos3_ptr, half_width_ptr, acti
 
 def lbm_launch_count(ctx):
     return int(lib().lbm_launch_count(ctx))
+
+
+def lbm_sweep_kernel(ctx):
+    return lib().lbm_sweep_kernel(ctx).decode()
 
 
 def lbm_sync(ctx):
@@ -419,9 +427,14 @@ def lbm_batch_tune(b, trial_steps=10):
     return depth.value, grid.value
 
 
-def lbm_batch_get_fields(b, col, sites, rho=True, u=True):
-    r = np.empty(sites, dtype=np.float64) if rho else None
-    v = np.empty(3 * sites, dtype=np.float64) if u else None
+def lbm_batch_get_fields(b, col, sites, rho=True, u=True, out_rho=None, out_u=None):
+    """Fields of column ``col`` (``sites`` nodes); ``out_rho`` / ``out_u`` may
+    supply float64 buffers (e.g. pinned host memory) to fill."""
+    r = out_rho if out_rho is not None else (np.empty(sites, dtype=np.float64) if rho else None)
+    v = out_u if out_u is not None else (np.empty(3 * sites, dtype=np.float64) if u else None)
+    for a, size in ((r, sites), (v, 3 * sites)):
+        if a is not None and (a.dtype != np.float64 or a.size != size or not a.flags.c_contiguous):
+            raise ValueError("output buffer must be contiguous float64 of %d values" % size)
     _bcheck(b, lib().lbm_batch_get_fields(b, int(col), _dptr(r), _dptr(v)))
     return r, v
 

@@ -1,5 +1,5 @@
-"""bench.py's reference arm on CPU: the FP64 oracle timed on a bounded crop of the
-single-column workload, printed as one JSON line with the bench keys."""
+"""bench.py's reference arm on CPU: the FP64 oracle timed on bounded crops of the
+swarm workload, one process per core, printed as one JSON line with the bench keys."""
 import json
 import os
 import subprocess
@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_prints_one_bench_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     res = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
-                          "--warmup", "3"], cwd=ROOT, env=env, capture_output=True, text=True,
+                          "--warmup", "3", "--cpu-procs", "2"], cwd=ROOT, env=env, capture_output=True, text=True,
                          timeout=600)
     assert res.returncode == 0, res.stderr[-2000:]
     lines = [l for l in res.stdout.splitlines() if l.strip()]
@@ -24,8 +24,8 @@ def test_reference_arm_prints_one_bench_line():
     assert d["unit"] == "MLUPS" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0.0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"].startswith("single bubble column")
+    assert d["config"]["workload"].startswith("dispersed swarm 384x384x768")

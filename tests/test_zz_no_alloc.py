@@ -64,3 +64,30 @@ def test_noalloc_rejects_more_tiles_than_its_scratch():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_bin_bubbles_noalloc(2048, 2048, 64, lbm.LBM_WALL_ALL, 0, 0, 0, 0, 0, 0, 0, 0, 0)
     assert e.value.code == lbm.LBM_ERR_ARG
+
+
+def test_noalloc_skips_and_flags_invalid_bubbles():
+    # Caller input never passes lbm_set_bubbles' checks, so the kernel checks
+    # it: an oversized or non-finite half-width and a non-finite or out-of-box
+    # centre are skipped and set status bit 2; the valid bubbles are binned
+    # exactly as the oracle's brute-force binning (Algorithm 1 step 2) does.
+    import torch
+    from oracle import binning as obin
+    dims = (64, 32, 48)
+    walls = lbm.LBM_WALL_ALL
+    pos = np.array([[10.3, 12.1, 20.7], [40.5, 8.25, 30.0], [60.9, 30.2, 3.1],   # valid
+                    [20.0, 16.0, 24.0],                                           # n too large
+                    [np.nan, 16.0, 24.0],                                         # NaN centre
+                    [20.0, 33.5, 24.0],                                           # outside in y
+                    [20.0, 16.0, 24.0]])                                          # n = inf
+    hw = np.array([2.25, 3.0, 4.5, 9.5, 2.0, 2.0, np.inf])
+    valid = np.array([1, 1, 1, 0, 0, 0, 0], dtype=bool)
+    ntiles = -(-dims[0] // 32) * -(-dims[1] // 4) * -(-dims[2] // 4)
+    offsets = torch.empty(ntiles + 1, dtype=torch.int32, device="cuda")
+    items = torch.empty(4096, dtype=torch.int32, device="cuda")
+    status = torch.empty(1, dtype=torch.int32, device="cuda")
+    off, its, st = _noalloc_bins(torch, dims, walls, pos, hw, offsets, items, status)
+    assert st == lbm.LBM_NOALLOC_STATUS_SKIPPED
+    ref_off, ref_items = obin.tile_lists([p for p in pos], list(hw), valid, dims, walls, (32, 4, 4))
+    assert np.array_equal(off, np.array(ref_off))
+    assert np.array_equal(its, np.array(ref_items))
