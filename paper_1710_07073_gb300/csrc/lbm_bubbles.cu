@@ -6,9 +6,10 @@
 //                    sub-stepped Newton update (Eq. 4, Table 2), the reaction
 //                    psi_b = -mean F_D (Algorithm 1 step 6) and the spreading
 //                    record; the last one bins all bubbles.
-//  k_moments_tiles,  many bubbles: Eq. 10 velocity of the covered tiles, then
-//  k_bubbles_warp    one warp per 32 bubbles (window sums in turn, the 32
-//                    tails in parallel).
+//  k_tile_interp,    many bubbles: per listed tile, the Eq. 10 velocity of its
+//  k_swarm_tail,     nodes and each listed bubble's Eq. 20 sum over it; per
+//  k_swarm_bin       bubble, the parts added and the update; the binning in
+//                    one persistent launch.
 //  binning           bubble windows to lattice tiles (Algorithm 1 step 2):
 //                    integer counting sort, then each tile's list in bubble
 //                    order.
@@ -271,33 +272,6 @@ __device__ __forceinline__ void chunk_sum2(const typename Store<ST>::T* __restri
     }
 }
 
-// Eq. 20 partial sums over the window's x-rows (y, z) = tid, tid + nt, ...
-// from the precomputed Eq. 10 velocities `mom` (three planes of S floats).
-// Per row the y and z weights are formed once; along the row only the x
-// weight changes.
-__device__ __forceinline__ void window_sum_rows(const float* __restrict__ mom, const Geo& g,
-                                                const Window& w, float inv_n, int tid, int nt,
-                                                float& ax, float& ay, float& az) {
-    const float hh = 0.5f * inv_n;
-    const int rows = w.cnt[1] * w.cnt[2];
-    const size_t S = (size_t)g.S;
-    for (int r = tid; r < rows; r += nt) {
-        const int iz = r / w.cnt[1], iy = r - iz * w.cnt[1];
-        const int j = w.lo[1] + iy, k = w.lo[2] + iz;
-        const float wyz = cell_poly(((float)(j - w.anc[1]) + 0.5f - w.fr[1]) * inv_n, hh) *
-                          cell_poly(((float)(k - w.anc[2]) + 0.5f - w.fr[2]) * inv_n, hh);
-        const size_t row = ((size_t)wrap_axis(k, g.nz) * g.ny + wrap_axis(j, g.ny)) * g.nx;
-        for (int ix = 0; ix < w.cnt[0]; ++ix) {
-            const int i = w.lo[0] + ix;
-            const float wt = cell_poly(((float)(i - w.anc[0]) + 0.5f - w.fr[0]) * inv_n, hh) * wyz;
-            const size_t node = row + (size_t)wrap_axis(i, g.nx);
-            ax = fmaf(wt, __ldg(mom + node), ax);
-            ay = fmaf(wt, __ldg(mom + S + node), ay);
-            az = fmaf(wt, __ldg(mom + 2 * S + node), az);
-        }
-    }
-}
-
 __device__ __forceinline__ void warp_sum3(float& ax, float& ay, float& az) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -449,117 +423,6 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
     make_record(xb, K.inv_nf, g, psi, B.rec[b]);
     // Algorithm 1: the bubble stops once it reaches the top of the liquid.
     if ((g.walls & 0x20) && !f2_lt(xb[2], top[2])) B.active[b] = 0;
-}
-
-// Many bubbles: window velocities from the moments of the covered tiles.
-constexpr int WARP_BUBBLE_THREADS = 128;   // four warps, 32 bubbles each
-
-// Each warp serves 32 consecutive bubbles.  Lane k loads bubble 32 w + k and
-// sets up its window; the warp then sums the 32 windows one after another
-// (each window broadcast from its lane by shuffles), the sum ending with the
-// bubble's own lane; finally all lanes run their bubbles' tails at once.
-template <int ST>
-__global__ void __launch_bounds__(WARP_BUBBLE_THREADS)
-k_bubbles_warp(const typename Store<ST>::T* __restrict__ f, const float* __restrict__ mom, Geo g,
-               CollideParams cp, BubbleDev B, BubbleConst bc, int* __restrict__ flag) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int b0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32;
-    if (b0 >= B.nb) return;   // uniform over the warp
-    const int b = b0 + lane;
-    const bool have = b < B.nb;
-    BubbleIn in;
-    Window w{};
-    int state = BUBBLE_IDLE;
-    if (have) {
-        load_bubble(B, b, true, in);
-        state = bubble_window(g, in, w);
-    }
-    const float inv_n = have ? in.k.inv_nf : 0.0f;
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-    for (int j = 0; j < 32; ++j) {
-        if (__shfl_sync(full, state, j) != BUBBLE_LIVE) continue;   // uniform
-        Window wj;
-        for (int a = 0; a < 3; ++a) {
-            wj.lo[a] = __shfl_sync(full, w.lo[a], j);
-            wj.cnt[a] = __shfl_sync(full, w.cnt[a], j);
-            wj.anc[a] = __shfl_sync(full, w.anc[a], j);
-            wj.fr[a] = __shfl_sync(full, w.fr[a], j);
-        }
-        const float inv_nj = __shfl_sync(full, inv_n, j);
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;
-        window_sum_rows(mom, g, wj, inv_nj, lane, 32, ax, ay, az);
-        warp_sum3(ax, ay, az);
-        if (lane == j) {
-            sx = ax;
-            sy = ay;
-            sz = az;
-        }
-    }
-    if (have) bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz, in);
-}
-
-// Eq. 10 velocity of every node of the tiles some bubble window covers
-// (count > 0); other tiles are skipped.  One CTA per tile, TX x TY threads
-// looping over the tile's TZ planes.
-template <int ST>
-__global__ void __launch_bounds__(TX * TY)
-k_moments_tiles(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
-                const int* __restrict__ tile_count, float* __restrict__ mom) {
-    const int t = blockIdx.x;
-    if (tile_count[t] == 0) return;
-    const int bx = t % g.ntx, by = (t / g.ntx) % g.nty, bz = t / (g.ntx * g.nty);
-    const int x = bx * TX + threadIdx.x, y = by * TY + threadIdx.y;
-    if (x >= g.nx || y >= g.ny) return;
-    const int zend = min(bz * TZ + TZ, g.nz);
-    for (int z = bz * TZ; z < zend; z += 2) {   // two planes per pass: 38 loads in flight
-        const bool two = z + 1 < zend;
-        typename Store<ST>::T ra[Q], rb[Q];
-        gather_issue<ST>(f, g, x, y, z, ra);
-        gather_issue<ST>(f, g, x, y, two ? z + 1 : z, rb);
-        float gv[Q], u[3];
-        gather_finish<ST>(ra, cp, gv);
-        node_velocity(gv, cp, u);
-        size_t node = (size_t)site_index(g, x, y, z);
-        mom[node] = u[0];
-        mom[(size_t)g.S + node] = u[1];
-        mom[2 * (size_t)g.S + node] = u[2];
-        if (two) {
-            gather_finish<ST>(rb, cp, gv);
-            node_velocity(gv, cp, u);
-            node += (size_t)g.nx * g.ny;
-            mom[node] = u[0];
-            mom[(size_t)g.S + node] = u[1];
-            mom[2 * (size_t)g.S + node] = u[2];
-        }
-    }
-}
-
-cudaError_t launch_bubbles_many(int storage, const void* f, float* mom, const Geo& g,
-                                const CollideParams& cp, const BubbleDev& b, const BubbleConst& bc,
-                                const int* tile_count, int* flag, cudaStream_t st) {
-    if (b.nb == 0) return cudaSuccess;
-    const int T = g.ntx * g.nty * g.ntz;
-    const int blocks = (b.nb + WARP_BUBBLE_THREADS - 1) / WARP_BUBBLE_THREADS;   // a bubble per thread
-    dim3 tb(TX, TY);
-    switch (storage) {
-        case 0:
-            k_moments_tiles<0><<<T, tb, 0, st>>>((const float*)f, g, cp, tile_count, mom);
-            k_bubbles_warp<0><<<blocks, WARP_BUBBLE_THREADS, 0, st>>>((const float*)f, mom, g, cp, b,
-                                                                      bc, flag);
-            break;
-        case 1:
-            k_moments_tiles<1><<<T, tb, 0, st>>>((const __half*)f, g, cp, tile_count, mom);
-            k_bubbles_warp<1><<<blocks, WARP_BUBBLE_THREADS, 0, st>>>((const __half*)f, mom, g, cp,
-                                                                      b, bc, flag);
-            break;
-        default:
-            k_moments_tiles<2><<<T, tb, 0, st>>>((const __nv_bfloat16*)f, g, cp, tile_count, mom);
-            k_bubbles_warp<2><<<blocks, WARP_BUBBLE_THREADS, 0, st>>>((const __nv_bfloat16*)f, mom,
-                                                                      g, cp, b, bc, flag);
-            break;
-    }
-    return cudaGetLastError();
 }
 
 // Table 1 / Eq. 3 constants of each bubble (FP64).
@@ -880,6 +743,62 @@ __device__ __forceinline__ int floor_div(int a, int b) {
     return a >= 0 ? a / b : -((-a + b - 1) / b);
 }
 
+// Sweep order of the z blocks for the next step, written by one CTA (every
+// thread calls it): the blocks whose tile layer is not marked in `lay` (bit
+// l: layer l is guarded), ascending, then the guarded ones, ascending.  Each
+// thread places a contiguous run of blocks; a block-wide scan of the cleared
+// counts gives every run's first slot.
+__device__ void write_zperm(int nbz, const unsigned* lay, int* __restrict__ zperm) {
+    __shared__ int ws[33];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (nbz + nt - 1) / nt;
+    const int b0 = min(tid * per, nbz), b1 = min(b0 + per, nbz);
+    int cleared = 0;
+    for (int bz = b0; bz < b1; ++bz) {
+        const int l = (bz * SWEEP_PZ) / TZ;
+        cleared += !((lay[l >> 5] >> (l & 31)) & 1u);
+    }
+    int total;
+    const int before = block_exclusive_scan(cleared, ws, total);
+    int sc = before, sg = total + (b0 - before);   // guarded blocks before b0: b0 - before
+    for (int bz = b0; bz < b1; ++bz) {
+        const int l = (bz * SWEEP_PZ) / TZ;
+        if ((lay[l >> 5] >> (l & 31)) & 1u) zperm[sg++] = bz;
+        else zperm[sc++] = bz;
+    }
+}
+
+// The z tile layers the support of an active bubble, widened by GUARD_CELLS
+// cells, reaches: bits of `lay` (atomicOr; shared or global memory).
+__device__ __forceinline__ void mark_guarded_layers(const Geo& g, F2 z, float nh, float nl,
+                                                    unsigned* lay) {
+    const int ntz = g.ntz;
+    const bool periodic = !(g.walls & 0x10);
+    int lo, hi;
+    support_cells(z, nh, nl, lo, hi);
+    lo = max(lo, -2 * g.nz) - GUARD_CELLS;
+    hi = min(hi, 3 * g.nz) + GUARD_CELLS;
+    int l0, l1;
+    if (!periodic) {
+        lo = max(lo, 0);
+        hi = min(hi, g.nz - 1);
+        if (hi < lo) return;
+        l0 = lo / TZ;
+        l1 = hi / TZ;
+    } else if (hi - lo + 1 >= g.nz) {
+        l0 = 0;
+        l1 = ntz - 1;
+    } else {
+        l0 = floor_div(lo, TZ);
+        l1 = floor_div(hi, TZ);
+    }
+    for (int l = l0; l <= l1; ++l) {
+        int lw = l % ntz;
+        if (lw < 0) lw += ntz;
+        atomicOr(&lay[lw >> 5], 1u << (lw & 31));
+    }
+}
+
 // Overlap guard for the next step (single column): safe[l] = sb.safe_epoch
 // for every z tile layer l that the support of no active bubble, widened by
 // GUARD_CELLS cells, reaches.  Next step's forces lie inside those supports
@@ -892,37 +811,15 @@ __device__ void write_safe_layers(const Geo& g, const BubbleDev& B, const SmallB
     if (ntz > GUARD_LAYERS_MAX) return;
     for (int i = tid; i < GUARD_LAYERS_MAX / 32; i += nt) s_lay[i] = 0u;
     __syncthreads();
-    const bool periodic = !(g.walls & 0x10);
     for (int b = tid; b < B.nb; b += nt) {
         if (!__ldcg(B.active + b)) continue;
-        int lo, hi;
-        support_cells(F2{__ldcg(B.xh + 3 * b + 2), __ldcg(B.xl + 3 * b + 2)},
-                      __ldcg(&B.k[b].nh), __ldcg(&B.k[b].nl), lo, hi);
-        lo = max(lo, -2 * g.nz) - GUARD_CELLS;
-        hi = min(hi, 3 * g.nz) + GUARD_CELLS;
-        int l0, l1;
-        if (!periodic) {
-            lo = max(lo, 0);
-            hi = min(hi, g.nz - 1);
-            if (hi < lo) continue;
-            l0 = lo / TZ;
-            l1 = hi / TZ;
-        } else if (hi - lo + 1 >= g.nz) {
-            l0 = 0;
-            l1 = ntz - 1;
-        } else {
-            l0 = floor_div(lo, TZ);
-            l1 = floor_div(hi, TZ);
-        }
-        for (int l = l0; l <= l1; ++l) {
-            int lw = l % ntz;
-            if (lw < 0) lw += ntz;
-            atomicOr(&s_lay[lw >> 5], 1u << (lw & 31));
-        }
+        mark_guarded_layers(g, F2{__ldcg(B.xh + 3 * b + 2), __ldcg(B.xl + 3 * b + 2)},
+                            __ldcg(&B.k[b].nh), __ldcg(&B.k[b].nl), s_lay);
     }
     __syncthreads();
     for (int l = tid; l < ntz; l += nt)
         if (!((s_lay[l >> 5] >> (l & 31)) & 1u)) sb.safe[l] = sb.safe_epoch;
+    if (sb.zperm != nullptr) write_zperm(sb.nbz, s_lay, sb.zperm);
 }
 
 // Bubble update with the few-pair binning fused behind it.
@@ -1081,6 +978,534 @@ cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* 
         case 1: return launch_binned<1>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, false, st);
         default: return launch_binned<2>(f, g0, cp0, b, bc, flag, sb, cols, bubble_col, false, st);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Many bubbles: interpolation by tiles, update per bubble, binning in one
+// persistent launch
+// ---------------------------------------------------------------------------
+// The window sum of Eq. 20 splits over the lattice tiles a bubble's window
+// touches.  The binning of the current centres lists, per tile, the bubbles
+// whose windows touch it; k_tile_interp forms per tile the Eq. 10 velocity of
+// its 512 nodes once, in shared memory, and for each listed bubble the part
+// of its sum over the tile (a separable tensor product: x-rows first, then the
+// y and z weights).  k_swarm_tail adds a bubble's parts in the order of its
+// tiles (ascending) and runs the update; k_swarm_bin bins the updated
+// bubbles and records, for every bubble and tile, the list position of the
+// pair, where the next step's parts are written and read.  All sums run in a
+// fixed order, so the results do not depend on scheduling.
+
+constexpr int INTERP_THREADS = TX * TY * 2;   // two of a tile's TZ planes per thread
+constexpr int INTERP_CHUNK = 32;              // listed bubbles per pass
+constexpr int INTERP_ROWS = TY * TZ;          // (y, z) rows of a tile: 16
+static_assert(INTERP_THREADS % INTERP_ROWS == 0 && TZ == 4, "tile shape of the interpolation");
+
+// One covered tile t: the Eq. 10 velocity of its nodes, then for each listed
+// bubble the part of its Eq. 20 sum over the tile, written at the bubble's
+// list position.  Every thread of the CTA calls it.
+template <int ST, bool PAIR>
+__device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restrict__ f,
+                                            const Geo& g, const CollideParams& cp, int t,
+                                            const int* __restrict__ cnt,
+                                            const int* __restrict__ off,
+                                            const int* __restrict__ items, int cap,
+                                            const BubbleRec* __restrict__ recs, int nb,
+                                            float* __restrict__ partial) {
+    constexpr int NAX = TX + TY + TZ;
+    __shared__ float s_u[3][INTERP_ROWS][TX + 1];   // node velocities by (z, y) row, padded
+    __shared__ float s_w[INTERP_CHUNK][NAX];         // per-axis cell integrals per bubble
+    __shared__ BubbleRec s_rec[INTERP_CHUNK];
+    __shared__ int s_xlo[INTERP_CHUNK], s_xhi[INTERP_CHUNK];   // non-zero x weights
+    const int tid = threadIdx.x;
+    const int bx = t % g.ntx, by = (t / g.ntx) % g.nty, bz = t / (g.ntx * g.nty);
+    const int xb0 = bx * TX, yb0 = by * TY, zb0 = bz * TZ;
+    // The population loads go out first; the list and the first chunk's
+    // records (a chain of dependent loads) are fetched while they are in
+    // flight.  PAIR (even nx): thread (px, y, z) gathers the x-pair
+    // (2 px, 2 px + 1) of row (y, z) with aligned 2-wide row loads; else
+    // thread (x, y, zp) gathers nodes (x, y, zp) and (x, y, zp + 2).
+    const int tx = tid % TX, ty = (tid / TX) % TY, zp = tid / (TX * TY);
+    const int x = xb0 + tx, y = yb0 + ty, za = zb0 + zp, zb = zb0 + zp + 2;
+    const bool inxy = x < g.nx && y < g.ny;
+    const bool ina = inxy && za < g.nz, inb = inxy && zb < g.nz;
+    const int ppx = tid % (TX / 2), py2 = (tid / (TX / 2)) % TY, pz2 = tid / ((TX / 2) * TY);
+    const int px0 = xb0 + 2 * ppx, pyy = yb0 + py2, pzz = zb0 + pz2;
+    const bool inp = px0 < g.nx && pyy < g.ny && pzz < g.nz;
+    typename Store<ST>::T ra[PAIR ? 1 : Q], rb[PAIR ? 1 : Q];
+    typename Raw2<ST>::T rp[PAIR ? Q : 1];
+    if (PAIR) {
+        gather_pair<ST>(f, g, inp ? px0 : 0, inp ? pyy : 0, inp ? pzz : 0, rp);
+    } else {
+        gather_issue<ST>(f, g, ina ? x : 0, ina ? y : 0, ina ? za : 0, ra);
+        gather_issue<ST>(f, g, inb ? x : 0, inb ? y : 0, inb ? zb : 0, rb);
+    }
+    const int n_t = __ldcg(cnt + t);
+    const int beg = __ldcg(off + t);
+    const int end = min(beg + n_t, cap);
+    BubbleRec rec0{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (tid < min(INTERP_CHUNK, end - beg)) {
+        const int id = __ldcg(items + beg + tid);
+        if (id >= 0 && id < nb) rec0 = load_rec(recs + id);
+    }
+    if (PAIR) {
+        // Eq. 10 velocity of the pair (zero for nodes beyond the box).
+        float2 drho, jx, jy, jz;
+        pair_moments<ST>(rp, cp, drho, jx, jy, jz);
+        const float ra0 = 1.0f / (cp.rho0 + drho.x), ra1 = 1.0f / (cp.rho0 + drho.y);
+        const int row = pz2 * TY + py2;
+        s_u[0][row][2 * ppx] = inp ? jx.x * ra0 : 0.0f;
+        s_u[0][row][2 * ppx + 1] = inp ? jx.y * ra1 : 0.0f;
+        s_u[1][row][2 * ppx] = inp ? jy.x * ra0 : 0.0f;
+        s_u[1][row][2 * ppx + 1] = inp ? jy.y * ra1 : 0.0f;
+        s_u[2][row][2 * ppx] = inp ? jz.x * ra0 : 0.0f;
+        s_u[2][row][2 * ppx + 1] = inp ? jz.y * ra1 : 0.0f;
+    } else {
+        // Eq. 10 velocity of the tile's nodes (zero for nodes beyond the box).
+        float gv[Q], u[3];
+        gather_finish<ST>(ra, cp, gv);
+        node_velocity(gv, cp, u);
+        for (int c = 0; c < 3; ++c) s_u[c][zp * TY + ty][tx] = ina ? u[c] : 0.0f;
+        gather_finish<ST>(rb, cp, gv);
+        node_velocity(gv, cp, u);
+        for (int c = 0; c < 3; ++c) s_u[c][(zp + 2) * TY + ty][tx] = inb ? u[c] : 0.0f;
+    }
+    const bool px = !(g.walls & 0x01), py = !(g.walls & 0x04), pz = !(g.walls & 0x10);
+    for (int c0 = beg; c0 < end; c0 += INTERP_CHUNK) {
+        const int cntc = min(INTERP_CHUNK, end - c0);
+        __syncthreads();
+        if (tid < cntc) {
+            if (c0 == beg) {
+                s_rec[tid] = rec0;
+            } else {
+                const int id = __ldcg(items + c0 + tid);
+                if (id >= 0 && id < nb) s_rec[tid] = load_rec(recs + id);
+                else s_rec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            }
+            s_xlo[tid] = TX;
+            s_xhi[tid] = -1;
+        }
+        __syncthreads();
+        for (int e = tid; e < cntc * NAX; e += INTERP_THREADS) {
+            const int k = e / NAX, q = e - k * NAX;
+            const BubbleRec& r = s_rec[k];
+            if (q < TX) {
+                const float w = axis_weight(r, xb0 + q, r.ax, r.fx, g.nx, px);
+                s_w[k][q] = w;
+                if (w != 0.0f) {
+                    atomicMin(&s_xlo[k], q);
+                    atomicMax(&s_xhi[k], q);
+                }
+            } else if (q < TX + TY) {
+                s_w[k][q] = axis_weight(r, yb0 + q - TX, r.ay, r.fy, g.ny, py);
+            } else {
+                s_w[k][q] = axis_weight(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, pz);
+            }
+        }
+        __syncthreads();
+        // INTERP_ROWS threads per bubble, one (z, y) row each; the row sums
+        // are added over the rows by shuffles (fixed order).
+        for (int k0 = 0; k0 < cntc; k0 += INTERP_THREADS / INTERP_ROWS) {
+            const int k = k0 + tid / INTERP_ROWS, row = tid % INTERP_ROWS;
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            if (k < cntc) {
+                const float wyz = s_w[k][TX + row % TY] * s_w[k][TX + TY + row / TY];
+                if (wyz != 0.0f) {
+                    // Only the x columns with a non-zero weight: zero terms
+                    // add nothing.
+                    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+                    const int xe = s_xhi[k];
+                    for (int x = s_xlo[k]; x <= xe; ++x) {
+                        const float wx = s_w[k][x];
+                        ax = fmaf(wx, s_u[0][row][x], ax);
+                        ay = fmaf(wx, s_u[1][row][x], ay);
+                        az = fmaf(wx, s_u[2][row][x], az);
+                    }
+                    sx = ax * wyz;
+                    sy = ay * wyz;
+                    sz = az * wyz;
+                }
+            }
+#pragma unroll
+            for (int o = INTERP_ROWS / 2; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            }
+            if (row == 0 && k < cntc) {
+                float* q = partial + 3 * (size_t)(c0 + k);
+                q[0] = sx;
+                q[1] = sy;
+                q[2] = sz;
+            }
+        }
+    }
+}
+
+// Persistent over the list of covered tiles, a tile per CTA in turn.
+template <int ST, bool PAIR>
+__global__ void __launch_bounds__(INTERP_THREADS, 4)
+k_tile_interp(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
+              const int* __restrict__ cnt, const int* __restrict__ off,
+              const int* __restrict__ items, int cap, const BubbleRec* __restrict__ recs, int nb,
+              const int* __restrict__ cover, const int* __restrict__ ncover,
+              float* __restrict__ partial) {
+    const int ntiles = __ldcg(ncover);
+    for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+        __syncthreads();   // the shared tables of the previous tile are done with
+        tile_interp<ST, PAIR>(f, g, cp, __ldcg(cover + i), cnt, off, items, cap, recs, nb,
+                              partial);
+    }
+}
+
+// The update, a thread per bubble: its Eq. 20 sum is the parts of its tiles
+// added in tile order.  The tile counts and the list of covered tiles start
+// again for the binning after it.
+constexpr int TAIL_THREADS = 128;
+
+__global__ void __launch_bounds__(TAIL_THREADS)
+k_swarm_tail(Geo g, BubbleDev B, BubbleConst bc, int* __restrict__ flag, Bins bins,
+             SwarmBins sw) {
+    const int tid = threadIdx.x;
+    const int gtid = blockIdx.x * TAIL_THREADS + tid, nthreads = gridDim.x * TAIL_THREADS;
+    for (int t = gtid; t < bins.T; t += nthreads) bins.cnt[t] = 0;
+    if (gtid == 0) *sw.ncover = 0;
+    const int b = gtid;
+    if (b < B.nb) {
+        BubbleIn in;
+        load_bubble(B, b, true, in);
+        Window w;
+        const int state = bubble_window(g, in, w);
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        if (state == BUBBLE_LIVE) {
+            const int n = min(__ldcg(sw.ntile + b), sw.per);
+            const int* sl = sw.slots + (size_t)b * sw.per;
+            for (int k = 0; k < n; ++k) {
+                const int p = __ldcg(sl + k);
+                if (p < 0 || p >= bins.cap) continue;
+                const float* q = sw.partial + 3 * (size_t)p;
+                sx += __ldcg(q);
+                sy += __ldcg(q + 1);
+                sz += __ldcg(q + 2);
+            }
+        }
+        bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz, in);
+    }
+}
+
+// Binning of the updated bubbles in one persistent launch, phases separated
+// by grid barriers (all its CTAs are resident):
+//   1. count: every selected bubble adds itself to the tiles its window
+//      touches (Algorithm 1 step 2);
+//   2. scan of the counts (per-CTA chunk totals, then offsets), and the list
+//      of covered tiles;
+//   3. fill: each bubble takes slots through per-tile cursors, noting which
+//      of its tiles each is;
+//   4. each tile's list ordered by bubble id (a warp per tile: an id's rank
+//      is the number of smaller ids in the list), and the list positions
+//      recorded per bubble.
+// The counts, offsets and lists are those of launch_binning.  Everything
+// written earlier in the launch is read through L2 (ld.global.cg).
+constexpr int SWARM_THREADS = 256;
+constexpr int SWARM_WARPS = SWARM_THREADS / 32;
+constexpr int SWARM_SORT_MAX = 128;   // longer tile lists are ordered by one thread
+// A grid barrier that waits longer than this (a CTA that never arrives) gives
+// up: flag bit 8, and the launch ends.
+constexpr unsigned long long SWARM_WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier over the launch's CTAs (bar[0] arrivals, bar[1] generation).
+// The last CTA to arrive resets the arrivals before it advances the
+// generation, so the counter is zero again for the next barrier and launch.
+// Returns false (in every thread of the CTA) if the wait ran out.
+__device__ bool grid_barrier(unsigned* bar, int* flag) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned* vbar = bar;
+        const unsigned gen = vbar[1];
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (vbar[1] == gen) {
+                __nanosleep(64);
+                if (global_ns() - t0 > SWARM_WAIT_NS) {
+                    atomicOr(flag, 8);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum over the CTA (fixed order), returned in every thread.
+__device__ __forceinline__ int block_sum_int(int v, int* red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    int t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    __syncthreads();
+    return t;
+}
+
+// The tiles bubble b's window touches, per axis (ascending), as k_bin finds
+// them; returns false for a bubble that is not selected.
+__device__ __forceinline__ bool bubble_tiles(const Geo& g, const BubbleDev& B, const int* select,
+                                             int b, int tl[3][MAX_AXIS_TILES], int nt[3]) {
+    if (!__ldcg(select + b)) return false;
+    const int L[3] = {g.nx, g.ny, g.nz};
+    const int T[3] = {TX, TY, TZ};
+    const float nh = B.k[b].nh, nl = B.k[b].nl;
+    for (int a = 0; a < 3; ++a) {
+        int lo, hi;
+        support_cells(F2{__ldcg(B.xh + 3 * b + a), __ldcg(B.xl + 3 * b + a)}, nh, nl, lo, hi);
+        nt[a] = axis_tiles(lo, hi, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(SWARM_THREADS)
+k_swarm_bin(Geo g, BubbleDev B, Bins bins, SwarmBins sw, const int* __restrict__ select,
+            int* __restrict__ flag) {
+    __shared__ int s_red[SWARM_WARPS];
+    __shared__ int s_id[SWARM_WARPS][SWARM_SORT_MAX];
+    __shared__ int s_k[SWARM_WARPS][SWARM_SORT_MAX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthreads = gridDim.x * SWARM_THREADS;
+    const int gtid = blockIdx.x * SWARM_THREADS + tid;
+    const int T = bins.T;
+
+    // 1. Count.
+    for (int b = gtid; b < B.nb; b += nthreads) {
+        int tl[3][MAX_AXIS_TILES], nt[3];
+        int n = 0;
+        if (bubble_tiles(g, B, select, b, tl, nt)) {
+            for (int iz = 0; iz < nt[2]; ++iz)
+                for (int iy = 0; iy < nt[1]; ++iy)
+                    for (int ix = 0; ix < nt[0]; ++ix)
+                        atomicAdd(&bins.cnt[(tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix]], 1);
+            n = nt[0] * nt[1] * nt[2];
+        }
+        sw.ntile[b] = n;
+    }
+    if (!grid_barrier(sw.bar, flag)) return;
+
+    // 2. Scan, chunk totals.
+    const int chunk = (T + gridDim.x - 1) / gridDim.x;
+    const int c0 = min(blockIdx.x * chunk, T), c1 = min(c0 + chunk, T);
+    int part = 0;
+    for (int t = c0 + tid; t < c1; t += SWARM_THREADS) part += __ldcg(bins.cnt + t);
+    part = block_sum_int(part, s_red);
+    if (tid == 0) sw.chunk_sums[blockIdx.x] = part;
+    if (!grid_barrier(sw.bar, flag)) return;
+
+    // Scan, offsets (and the fill cursors).
+    int prefix = 0;
+    for (int c = tid; c < (int)blockIdx.x; c += SWARM_THREADS) prefix += __ldcg(sw.chunk_sums + c);
+    prefix = block_sum_int(prefix, s_red);
+    {
+        __shared__ int ws[33];
+        int carry = prefix;
+        for (int base = c0; base < c1; base += SWARM_THREADS) {
+            const int t = base + tid;
+            const int v = t < c1 ? __ldcg(bins.cnt + t) : 0;
+            int total;
+            const int ex = block_exclusive_scan(v, ws, total);
+            if (t < c1) {
+                bins.off[t] = carry + ex;
+                sw.cursor[t] = carry + ex;
+            }
+            // The tiles with a non-empty list, appended a warp at a time.
+            const unsigned m = __ballot_sync(0xffffffffu, v > 0);
+            if (m) {
+                int at = 0;
+                if (lane == 0) at = atomicAdd(sw.ncover, __popc(m));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (v > 0) sw.cover[at + __popc(m & ((1u << lane) - 1u))] = t;
+            }
+            carry += total;
+        }
+        if (c1 == T && c0 < c1 && tid == 0) bins.off[T] = carry;
+    }
+    if (!grid_barrier(sw.bar, flag)) return;
+
+    // 3. Fill.
+    for (int b = gtid; b < B.nb; b += nthreads) {
+        int tl[3][MAX_AXIS_TILES], nt[3];
+        if (!bubble_tiles(g, B, select, b, tl, nt)) continue;
+        int k = 0;
+        for (int iz = 0; iz < nt[2]; ++iz)
+            for (int iy = 0; iy < nt[1]; ++iy)
+                for (int ix = 0; ix < nt[0]; ++ix, ++k) {
+                    const int t = (tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix];
+                    const int at = atomicAdd(&sw.cursor[t], 1);
+                    if (at < bins.cap) {
+                        bins.items[at] = b;
+                        sw.kidx[at] = k;
+                    } else {
+                        atomicOr(bins.overflow, 1);
+                    }
+                }
+    }
+    if (!grid_barrier(sw.bar, flag)) return;
+
+    // 4. Each tile's list in bubble order, and each bubble's list positions.
+    // A bubble is listed at most once per tile, so the ids of a list are
+    // distinct and their ranks are the positions.
+    int* ids = s_id[warp];
+    int* ks = s_k[warp];
+    for (int t = blockIdx.x * SWARM_WARPS + warp; t < T; t += gridDim.x * SWARM_WARPS) {
+        const int n = __ldcg(bins.cnt + t);
+        if (n == 0) continue;   // uniform over the warp
+        const int beg = __ldcg(bins.off + t);
+        const int end = min(beg + n, bins.cap);
+        const int m = end - beg;
+        if (m <= SWARM_SORT_MAX) {
+            for (int i = lane; i < m; i += 32) {
+                ids[i] = __ldcg(bins.items + beg + i);
+                ks[i] = __ldcg(sw.kidx + beg + i);
+            }
+            __syncwarp();
+            for (int i = lane; i < m; i += 32) {
+                const int v = ids[i];
+                int rank = 0;
+                for (int j = 0; j < m; ++j) rank += ids[j] < v;
+                bins.items[beg + rank] = v;
+                sw.slots[(size_t)v * sw.per + min(ks[i], sw.per - 1)] = beg + rank;
+            }
+            __syncwarp();
+        } else if (lane == 0) {
+            for (int i = beg + 1; i < end; ++i) {
+                const int v = __ldcg(bins.items + i), kv = __ldcg(sw.kidx + i);
+                int j = i - 1;
+                while (j >= beg) {
+                    const int w = __ldcg(bins.items + j);
+                    if (w <= v) break;
+                    bins.items[j + 1] = w;
+                    sw.kidx[j + 1] = __ldcg(sw.kidx + j);
+                    --j;
+                }
+                bins.items[j + 1] = v;
+                sw.kidx[j + 1] = kv;
+            }
+            for (int i = beg; i < end; ++i) {
+                const int v = __ldcg(bins.items + i);
+                sw.slots[(size_t)v * sw.per + min(__ldcg(sw.kidx + i), sw.per - 1)] = i;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Spreading records of the current centres (with the current reaction).
+__global__ void k_bubble_records(Geo g, BubbleDev B) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nb) return;
+    const F2 xb[3] = {F2{B.xh[3 * b], B.xl[3 * b]}, F2{B.xh[3 * b + 1], B.xl[3 * b + 1]},
+                      F2{B.xh[3 * b + 2], B.xl[3 * b + 2]}};
+    const float psi[3] = {B.psi[3 * b], B.psi[3 * b + 1], B.psi[3 * b + 2]};
+    make_record(xb, B.k[b].inv_nf, g, psi, B.rec[b]);
+}
+
+cudaError_t launch_bubble_records(const Geo& g, const BubbleDev& b, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    k_bubble_records<<<(b.nb + 127) / 128, 128, 0, st>>>(g, b);
+    return cudaGetLastError();
+}
+
+int swarm_grid(int /*storage*/) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_swarm_bin, SWARM_THREADS, 0) !=
+            cudaSuccess || per < 1)
+        return 0;
+    return sms * std::min(per, LBM_SWARM_CTAS_PER_SM);
+}
+
+int interp_grid(int storage) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cudaError_t e;
+    switch (storage) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<0, true>, INTERP_THREADS, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<1, true>, INTERP_THREADS, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<2, true>, INTERP_THREADS, 0); break;
+    }
+    if (e != cudaSuccess || per < 1) return 0;
+    return sms * per;
+}
+
+namespace {
+template <int ST, bool PAIR>
+cudaError_t launch_interp_as(const void* f, const Geo& g, const CollideParams& cp,
+                             const Bins& bins, const BubbleDev& b, const SwarmBins& sw,
+                             cudaStream_t st) {
+    using T = typename Store<ST>::T;
+    k_tile_interp<ST, PAIR><<<sw.interp_grid, INTERP_THREADS, 0, st>>>(
+        (const T*)f, g, cp, bins.cnt, bins.off, bins.items, bins.cap, b.rec, b.nb, sw.cover,
+        sw.ncover, sw.partial);
+    return cudaGetLastError();
+}
+
+// Two-node gathers with aligned row loads on even rows.
+template <int ST>
+cudaError_t launch_interp(const void* f, const Geo& g, const CollideParams& cp, const Bins& bins,
+                          const BubbleDev& b, const SwarmBins& sw, cudaStream_t st) {
+    return (g.nx & 1) == 0 ? launch_interp_as<ST, true>(f, g, cp, bins, b, sw, st)
+                           : launch_interp_as<ST, false>(f, g, cp, bins, b, sw, st);
+}
+
+bool swarm_ready(const SwarmBins& sw) {
+    return sw.grid >= 1 && sw.interp_grid >= 1 && sw.bar && sw.cursor && sw.kidx && sw.slots &&
+           sw.ntile && sw.per >= 1 && sw.partial && sw.cover && sw.ncover && sw.chunk_sums;
+}
+}  // namespace
+
+cudaError_t launch_swarm_update(int storage, const void* f, const Geo& g,
+                                const CollideParams& cp, const BubbleDev& b,
+                                const BubbleConst& bc, int* flag, const Bins& bins,
+                                const SwarmBins& sw, cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    if (!swarm_ready(sw)) return cudaErrorInvalidValue;
+    cudaError_t e;
+    switch (storage) {
+        case 0: e = launch_interp<0>(f, g, cp, bins, b, sw, st); break;
+        case 1: e = launch_interp<1>(f, g, cp, bins, b, sw, st); break;
+        default: e = launch_interp<2>(f, g, cp, bins, b, sw, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    k_swarm_tail<<<(b.nb + TAIL_THREADS - 1) / TAIL_THREADS, TAIL_THREADS, 0, st>>>(g, b, bc, flag,
+                                                                                   bins, sw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_swarm_binning(g, b, bins, sw, b.spread, flag, st);
+}
+
+cudaError_t launch_swarm_binning(const Geo& g, const BubbleDev& b, const Bins& bins,
+                                 const SwarmBins& sw, const int* select, int* flag,
+                                 cudaStream_t st) {
+    if (b.nb == 0) return cudaSuccess;
+    if (!swarm_ready(sw)) return cudaErrorInvalidValue;
+    k_swarm_bin<<<sw.grid, SWARM_THREADS, 0, st>>>(g, b, bins, sw, select, flag);
+    return cudaGetLastError();
 }
 
 // Per-bubble closure constants for a batch: nu from each bubble's column.

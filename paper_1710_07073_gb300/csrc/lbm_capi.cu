@@ -160,15 +160,17 @@ int axis_tile_bound(double n, int T) {
 void free_bubbles(lbm_ctx* c) {
     BubbleDev& b = c->bub;
     SmallBins& sb = c->small;
+    SwarmBins& sw = c->swarm;
     void* ptrs[] = {b.k, b.xh, b.xl, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.out64, b.has_prev,
                     b.active, b.spread, b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items,
                     sb.prev_tiles, sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, sb.safe,
-                    c->mom};
+                    sb.zperm, sw.bar, sw.cursor, sw.kidx, sw.slots, sw.ntile, sw.partial, sw.cover,
+                    sw.ncover, sw.chunk_sums};
     for (void* p : ptrs) dfree(c, p);
-    c->mom = nullptr;
     c->cover_valid = false;
     b = BubbleDev{};
     sb = SmallBins{};
+    sw = SwarmBins{};
     c->bins.items = nullptr;
     c->bins.cap = 0;
     c->nb_cap = 0;
@@ -180,49 +182,79 @@ void free_bubbles(lbm_ctx* c) {
 
 void guard_invalidate(lbm_ctx* c) { c->epoch += 1; }
 
+namespace {
+
+// Two tag sets of ntz (zero: no layer cleared) and two sweep orders of nbz z
+// blocks (identity), by step parity.
+int alloc_guard(lbm_ctx* c, unsigned** safe, int** zperm, int* nbz) {
+    const Geo g = geo_of(c);
+    *nbz = sweep_z_blocks(g.nz);
+    *safe = (unsigned*)dalloc(c, 2 * sizeof(unsigned) * (size_t)g.ntz);
+    *zperm = (int*)dalloc(c, 2 * sizeof(int) * (size_t)*nbz);
+    if (!*safe || !*zperm) return LBM_ERR_ALLOC;
+    std::vector<int> ident(2 * (size_t)*nbz);
+    for (int k = 0; k < 2 * *nbz; ++k) ident[k] = k % *nbz;
+    LBM_CUDA(cudaMemsetAsync(*safe, 0, 2 * sizeof(unsigned) * (size_t)g.ntz, c->stream), "guard");
+    LBM_CUDA(cudaMemcpyAsync(*zperm, ident.data(), sizeof(int) * ident.size(),
+                             cudaMemcpyHostToDevice, c->stream), "sweep order");
+    return LBM_OK;
+}
+
+}  // namespace
+
 int enqueue_one_step(lbm_ctx* c) {
     const Geo g = geo_of(c);
     const CollideParams cp = collide_params(c);
     const bool bubbles = c->bub.nb > 0;
     const bool two_way = bubbles && c->p.two_way;
-    // Few bubbles, two-way coupling, even rows: the update and the sweep
-    // overlap (programmatic dependent launches).  Timed launches keep plain
-    // stream order so that the sweep's events time the sweep alone.
-    const bool overlap = two_way && c->use_small && c->small.safe != nullptr && !c->timing &&
-                         (g.nx & 1) == 0;
+    // Two-way coupling on even rows: the update and the sweep overlap
+    // (programmatic dependent launches), guarded by the tags the update before
+    // wrote.  Timed launches keep plain stream order so that the sweep's
+    // events time the sweep alone.
+    unsigned* const safe = c->use_small ? c->small.safe : nullptr;
+    int* const zperm = c->use_small ? c->small.zperm : nullptr;
+    const int nbz = c->small.nbz;
+    const bool overlap = two_way && safe != nullptr && !c->timing && (g.nx & 1) == 0;
     if (c->epoch >= 0xFFFFFF00u) {
         // Before the step number wraps: no stored tag may match a later one.
-        if (c->small.safe)
-            LBM_CUDA(cudaMemsetAsync(c->small.safe, 0, 2 * sizeof(unsigned) * (size_t)g.ntz,
-                                     c->stream), "guard reset");
+        if (safe)
+            LBM_CUDA(cudaMemsetAsync(safe, 0, 2 * sizeof(unsigned) * (size_t)g.ntz, c->stream),
+                     "guard reset");
         c->epoch = 1;
     }
     const unsigned epoch = c->epoch++;
-    // Tag sets by step parity: this step's sweep reads set (epoch & 1) while
-    // its update writes the next step's into the other set.
-    const unsigned* safe_now =
-        c->small.safe ? c->small.safe + (size_t)(epoch & 1u) * (size_t)g.ntz : nullptr;
+    // Tag sets and sweep orders by step parity: this step's sweep reads set
+    // (epoch & 1) while its update writes the next step's into the other.
+    const size_t now = epoch & 1u, next = (epoch + 1u) & 1u;
+    const unsigned* safe_now = safe ? safe + now * (size_t)g.ntz : nullptr;
+    const int* zperm_now = zperm ? zperm + now * (size_t)nbz : nullptr;
     if (bubbles) {
         if (c->use_small) {
             SmallBins sb = c->small;
-            if (sb.safe) sb.safe += (size_t)((epoch + 1u) & 1u) * (size_t)g.ntz;
+            if (sb.safe) sb.safe += next * (size_t)g.ntz;
+            if (sb.zperm) sb.zperm += next * (size_t)nbz;
             sb.safe_epoch = epoch + 1;   // the update clears layers for the next step
             LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
                                     c->flag_d, sb, overlap, c->stream),
                      "bubble update");
             c->launches += 1;   // binning fused into the bubble update
         } else {
-            // The tiles holding the windows of the current centres: left by
-            // the previous step's binning, else binned here from `active`.
+            // The tile lists of the current centres and their spreading
+            // records: left by the previous step, else made here from
+            // `active` (first step after the bubbles were set).
             if (!c->cover_valid) {
-                LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream, c->bub.active), "cover");
-                c->launches += BINNING_LAUNCHES;
+                LBM_CUDA(launch_bubble_records(g, c->bub, c->stream), "records");
+                LBM_CUDA(cudaMemsetAsync(c->bins.cnt, 0, sizeof(int) * (size_t)c->bins.T,
+                                         c->stream), "cover counts");
+                LBM_CUDA(cudaMemsetAsync(c->swarm.ncover, 0, sizeof(int), c->stream), "cover list");
+                LBM_CUDA(launch_swarm_binning(g, c->bub, c->bins, c->swarm, c->bub.active,
+                                              c->flag_d, c->stream), "cover");
+                c->launches += 2;
             }
-            LBM_CUDA(launch_bubbles_many(c->storage, c->f[c->cur], c->mom, g, cp, c->bub,
-                                         bubble_const(c), c->bins.cnt, c->flag_d, c->stream),
+            LBM_CUDA(launch_swarm_update(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
+                                         c->flag_d, c->bins, c->swarm, c->stream),
                      "bubble update");
-            LBM_CUDA(launch_binning(g, c->bub, c->bins, c->stream), "binning");
-            c->launches += 2 + BINNING_LAUNCHES;
+            c->launches += SWARM_LAUNCHES;   // interpolation by tiles; update; binning
             c->cover_valid = true;
         }
         c->bins_valid = true;
@@ -245,7 +277,8 @@ int enqueue_one_step(lbm_ctx* c) {
     else tl = TileLists{c->bins.off, c->bins.cnt, c->bins.items, c->bins.cap};
     LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
                                    two_way ? &tl : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
-                                   overlap ? safe_now : nullptr, epoch, overlap, c->stream),
+                                   overlap ? safe_now : nullptr, epoch, overlap,
+                                   two_way ? zperm_now : nullptr, c->stream),
              "collide-stream");
     if (c->timing) LBM_CUDA(cudaEventRecord(e1, c->stream), "event record");
     c->launches += 1;
@@ -258,6 +291,16 @@ int finish_steps(lbm_ctx* c) {
     LBM_CUDA(cudaMemcpyAsync(c->flag_h, c->flag_d, sizeof(int), cudaMemcpyDeviceToHost,
                              c->stream), "read flag");
     LBM_CUDA(cudaStreamSynchronize(c->stream), "step");
+    if (*c->flag_h & 8) {
+        // A grid barrier of the many-bubble update gave up waiting: its
+        // arrival counter may be left part-way, so it starts again at zero.
+        c->unstable = true;
+        if (c->swarm.bar)
+            LBM_CUDA(cudaMemsetAsync(c->swarm.bar, 0, 2 * sizeof(unsigned), c->stream), "barrier");
+        LBM_CUDA(cudaStreamSynchronize(c->stream), "barrier reset");
+        return fail(c, LBM_ERR_TIMEOUT,
+                    "a device-wide wait of the bubble update ran out (more than 1 s)");
+    }
     if (*c->flag_h) {
         c->unstable = true;
         return fail(c, LBM_ERR_UNSTABLE,
@@ -546,17 +589,43 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sb.arrive = (int*)dalloc(c, sizeof(int) * (size_t)n);
         lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow &&
                    sb.done && sb.part && sb.arrive;
-        // Overlap guard tags, one set per step parity (zero: no layer
-        // cleared yet).
+        // Overlap guard: tags and sweep orders, one set per step parity.
         if (c->bins.T > 0 && geo_of(c).ntz <= GUARD_LAYERS_MAX) {
-            sb.safe = (unsigned*)dalloc(c, 2 * sizeof(unsigned) * (size_t)geo_of(c).ntz);
-            lists_ok = lists_ok && sb.safe;
+            int rc = alloc_guard(c, &sb.safe, &sb.zperm, &sb.nbz);
+            if (rc == LBM_ERR_CUDA) {
+                free_bubbles(c);
+                return rc;
+            }
+            lists_ok = lists_ok && rc == LBM_OK;
         }
     } else {
         c->bins.cap = (int)cap;
         c->bins.items = (int*)dalloc(c, sizeof(int) * (size_t)cap);
-        c->mom = (float*)dalloc(c, sizeof(float) * 3 * (size_t)c->nx * c->ny * c->nz);
-        lists_ok = c->bins.items != nullptr && c->mom != nullptr;
+        SwarmBins& sw = c->swarm;
+        sw.grid = swarm_grid(c->storage);
+        if (sw.grid < 1) {
+            free_bubbles(c);
+            return fail(c, LBM_ERR_CUDA, "occupancy of the bubble binning");
+        }
+        sw.per = (int)per;
+        sw.interp_grid = interp_grid(c->storage);
+        if (sw.interp_grid < 1) {
+            free_bubbles(c);
+            return fail(c, LBM_ERR_CUDA, "occupancy of the interpolation");
+        }
+        sw.bar = (unsigned*)dalloc(c, 2 * sizeof(unsigned));
+        sw.cursor = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.T);
+        sw.kidx = (int*)dalloc(c, sizeof(int) * (size_t)cap);
+        sw.slots = (int*)dalloc(c, sizeof(int) * (size_t)cap);   // n * per
+        sw.ntile = (int*)dalloc(c, sizeof(int) * (size_t)n);
+        sw.partial = (float*)dalloc(c, 3 * sizeof(float) * (size_t)cap);
+        sw.cover = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.T);
+        sw.ncover = (int*)dalloc(c, sizeof(int));
+        sw.chunk_sums = (int*)dalloc(c, sizeof(int) * (size_t)sw.grid);
+        lists_ok = c->bins.items && sw.bar && sw.cursor && sw.kidx && sw.slots && sw.ntile &&
+                   sw.partial && sw.cover && sw.ncover && sw.chunk_sums;
+        if (lists_ok)
+            LBM_CUDA(cudaMemsetAsync(sw.bar, 0, 2 * sizeof(unsigned), c->stream), "barrier");
     }
     if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi ||
         !B.out64 || !B.has_prev || !B.active || !B.spread || !B.cell || !B.rec || !lists_ok) {
@@ -570,9 +639,6 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         LBM_CUDA(cudaMemsetAsync(sb.overflow, 0, sizeof(int), c->stream), "overflow");
         LBM_CUDA(cudaMemsetAsync(sb.done, 0, sizeof(int), c->stream), "done");
         LBM_CUDA(cudaMemsetAsync(sb.arrive, 0, sizeof(int) * (size_t)n, c->stream), "arrive");
-        if (sb.safe)
-            LBM_CUDA(cudaMemsetAsync(sb.safe, 0, 2 * sizeof(unsigned) * (size_t)geo_of(c).ntz,
-                                     c->stream), "guard");
     }
     B.nb = n;
     std::vector<double> hn(n);

@@ -253,9 +253,6 @@ k_collide_stream(const typename Store<ST>::T* __restrict__ fin,
 #ifndef LBM_PAIR_MINB_16
 #define LBM_PAIR_MINB_16 8
 #endif
-#ifndef LBM_PAIR_PZ
-#define LBM_PAIR_PZ 2
-#endif
 template <int ST> struct PairOccupancy {
     static constexpr int kMinBlocks = ST == 0 ? 6 : LBM_PAIR_MINB_16;
 };
@@ -263,82 +260,9 @@ constexpr int PX = TX / 2;   // threads along x
 // Bubbles staged per pass of the sweep's force gather (records and per-axis
 // weight tables in shared memory).
 constexpr int FORCE_CHUNK = 32;
-constexpr int PZ = LBM_PAIR_PZ;   // z-planes per CTA (divides TZ)
+constexpr int PZ = SWEEP_PZ;      // z-planes per CTA (divides TZ)
 static_assert(TZ % PZ == 0, "a CTA's z-planes must lie in one binning tile");
 
-template <int ST> struct Vec2;
-template <> struct Vec2<0> {
-    static __device__ __forceinline__ void store(float* p, float2 v) {
-        __stcs(reinterpret_cast<float2*>(p), v);
-    }
-};
-template <> struct Vec2<1> {
-    static __device__ __forceinline__ void store(__half* p, float2 v) {
-        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(v.x, v.y));
-    }
-};
-template <> struct Vec2<2> {
-    static __device__ __forceinline__ void store(__nv_bfloat16* p, float2 v) {
-        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(v.x, v.y));
-    }
-};
-
-// The stored values of one direction at an x-pair, as loaded.  FP32 keeps the
-// float2; the 16-bit formats keep both nodes packed in one 32-bit register
-// (node x0 in the low half) and widen at each use, which halves the registers
-// the 19 loaded rows hold while the moments and the relaxation run.
-template <int ST> struct Raw2 {
-    using T = unsigned;
-    using T1 = unsigned;
-    static __device__ __forceinline__ T load(const typename Store<ST>::T* p) {
-        return __ldg(reinterpret_cast<const unsigned*>(p));
-    }
-    static __device__ __forceinline__ T1 load1(const typename Store<ST>::T* p) {
-        return (unsigned)__ldg(reinterpret_cast<const unsigned short*>(p));
-    }
-    // (a, P.x) and (P.y, a)
-    static __device__ __forceinline__ T lo_from(T1 a, T P) { return __byte_perm(a, P, 0x5410); }
-    static __device__ __forceinline__ T hi_from(T P, T1 a) { return __byte_perm(P, a, 0x5432); }
-    static __device__ __forceinline__ T join(T1 a, T1 b) { return __byte_perm(a, b, 0x5410); }
-    static __device__ __forceinline__ float2 widen(T v);
-};
-template <> __device__ __forceinline__ float2 Raw2<1>::widen(unsigned v) {
-    return __half22float2(*reinterpret_cast<const __half2*>(&v));
-}
-template <> __device__ __forceinline__ float2 Raw2<2>::widen(unsigned v) {
-    return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
-}
-template <> struct Raw2<0> {
-    using T = float2;
-    using T1 = float;
-    static __device__ __forceinline__ T load(const float* p) {
-        return __ldg(reinterpret_cast<const float2*>(p));
-    }
-    static __device__ __forceinline__ T1 load1(const float* p) { return __ldg(p); }
-    static __device__ __forceinline__ T lo_from(T1 a, T P) { return make_float2(a, P.x); }
-    static __device__ __forceinline__ T hi_from(T P, T1 a) { return make_float2(P.y, a); }
-    static __device__ __forceinline__ T join(T1 a, T1 b) { return make_float2(a, b); }
-    static __device__ __forceinline__ float2 widen(T v) { return v; }
-};
-
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
-
-// Cell integral of the mapping along one axis for lattice coordinate c, with
-// the record's anchor cell `anc` and offset `fr` (Eq. 19), wrapped on a
-// periodic axis of length L as in add_bubble_force_pair.
-__device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc, float fr, int L,
-                                             bool periodic) {
-    float rc = (float)(c - anc) + 0.5f - fr;
-    if (periodic) {
-        if (rc > 0.5f * L) rc -= (float)L;
-        else if (rc < -0.5f * L) rc += (float)L;
-    }
-    return cell_poly(rc * r.inv_n, r.h);
-}
 
 // Force of one bubble record on the pair (x0, x0 + 1) at (y, z), Eq. 19 and 21.
 __device__ __forceinline__ void add_bubble_force_pair(const BubbleRec& r, const Geo& g, int x0,
@@ -372,43 +296,6 @@ __device__ __forceinline__ void add_bubble_force_pair(const BubbleRec& r, const 
     Fx = fma2(wv, f2(r.px), Fx);
     Fy = fma2(wv, f2(r.py), Fy);
     Fz = fma2(wv, f2(r.pz), Fz);
-}
-
-// Raw values of direction J arriving at the pair (x0, x0 + 1) of a row whose
-// y and z neighbours are inside the box.
-// Raw values of direction J arriving at the pair (x0, x0 + 1) of a row whose
-// y and z neighbours are inside the box.  The aligned pair of the source row
-// covers one of the two; the population crossing x for the other node is one
-// scalar load, at x0 - 1 or x0 + 2 of the source row, or, on an x face, at the
-// opposite plane of the node itself (wall) or the other end of the row
-// (periodic).  Every lane issues the same loads, so none waits on another.
-template <int ST, int J>
-__device__ __forceinline__ typename Raw2<ST>::T pull_pair(const typename Store<ST>::T* __restrict__ f,
-                                                          unsigned S, unsigned site0, unsigned nx,
-                                                          unsigned nxy, int x0, bool wallx) {
-    const unsigned row = (unsigned)J * S + site0 - ((unsigned)cy(J) * nx + (unsigned)cz(J) * nxy);
-    const typename Raw2<ST>::T P = Raw2<ST>::load(f + row);   // the source row at (x0, x0 + 1)
-    if (cx(J) == 0) return P;
-    if (cx(J) == 1) {
-        // node x0 receives x0 - 1, node x0 + 1 receives x0
-        unsigned a = row - 1u;
-        if (x0 == 0) a = wallx ? (unsigned)opp(J) * S + site0 : row + nx - 1u;
-        return Raw2<ST>::lo_from(Raw2<ST>::load1(f + a), P);
-    }
-    // cx == -1: node x0 receives x0 + 1, node x0 + 1 receives x0 + 2
-    unsigned a = row + 2u;
-    if ((unsigned)x0 + 2u >= nx) a = wallx ? (unsigned)opp(J) * S + site0 + 1u : row - (unsigned)x0;
-    return Raw2<ST>::hi_from(P, Raw2<ST>::load1(f + a));
-}
-
-template <int ST, int J>
-__device__ __forceinline__ typename Raw2<ST>::T pull_pair_any(
-    const typename Store<ST>::T* __restrict__ f, const Geo& g, int x0, int y, int z) {
-    int p0, i0, p1, i1;
-    pull_source<J>(g, x0, y, z, p0, i0);
-    pull_source<J>(g, x0 + 1, y, z, p1, i1);
-    return Raw2<ST>::join(Raw2<ST>::load1(f + (size_t)p0 * (size_t)g.S + i0),
-                          Raw2<ST>::load1(f + (size_t)p1 * (size_t)g.S + i1));
 }
 
 // c_j . v for direction J (J odd; J + 1 is its opposite), written with adds
@@ -479,34 +366,8 @@ template <int ST, bool FORCED, class Sink>
 __device__ __forceinline__ void collide_pair(Sink& sink, const typename Raw2<ST>::T rr[Q],
                                              float2 Fx, float2 Fy, float2 Fz,
                                              const CollideParams& cp, int* flag, bool live) {
-    float2 rv[Q];   // widened for the moments; the relaxation widens rr again
-#pragma unroll
-    for (int j = 0; j < Q; ++j) rv[j] = Raw2<ST>::widen(rr[j]);
-    const float2 s_axis = add2(add2(add2(rv[1], rv[2]), add2(rv[3], rv[4])), add2(rv[5], rv[6]));
-    const float2 s_edge = add2(add2(add2(add2(rv[7], rv[8]), add2(rv[9], rv[10])),
-                                    add2(add2(rv[11], rv[12]), add2(rv[13], rv[14]))),
-                               add2(add2(rv[15], rv[16]), add2(rv[17], rv[18])));
-    const float2 ax_x = sub2(rv[1], rv[2]), ax_y = sub2(rv[3], rv[4]), ax_z = sub2(rv[5], rv[6]);
-    const float2 d78 = sub2(rv[7], rv[8]), d910 = sub2(rv[9], rv[10]);
-    const float2 d1112 = sub2(rv[11], rv[12]), d1314 = sub2(rv[13], rv[14]);
-    const float2 d1516 = sub2(rv[15], rv[16]), d1718 = sub2(rv[17], rv[18]);
-    const float2 ed_x = add2(add2(d78, d910), add2(d1112, d1314));
-    const float2 ed_y = add2(sub2(d78, d910), add2(d1516, d1718));
-    const float2 ed_z = add2(sub2(d1112, d1314), sub2(d1516, d1718));
     float2 drho, jx, jy, jz;
-    if (Store<ST>::kScaled) {
-        const float2 k0 = f2(wf(0) * cp.inv_scale), ka = f2(wf(1) * cp.inv_scale),
-                     ke = f2(wf(7) * cp.inv_scale);
-        drho = fma2(k0, rv[0], fma2(ka, s_axis, mul2(ke, s_edge)));
-        jx = fma2(ka, ax_x, mul2(ke, ed_x));
-        jy = fma2(ka, ax_y, mul2(ke, ed_y));
-        jz = fma2(ka, ax_z, mul2(ke, ed_z));
-    } else {
-        drho = add2(rv[0], add2(s_axis, s_edge));
-        jx = add2(ax_x, ed_x);
-        jy = add2(ax_y, ed_y);
-        jz = add2(ax_z, ed_z);
-    }
+    pair_moments<ST>(rr, cp, drho, jx, jy, jz);
     const float2 rho = add2(f2(cp.rho0), drho);
     const float2 inv_rho = make_float2(1.0f / rho.x, 1.0f / rho.y);
     float2 ux, uy, uz;
@@ -535,18 +396,6 @@ __device__ __forceinline__ void collide_pair(Sink& sink, const typename Raw2<ST>
     LBM_PAIR2(1, ka); LBM_PAIR2(3, ka); LBM_PAIR2(5, ka); LBM_PAIR2(7, ke); LBM_PAIR2(9, ke);
     LBM_PAIR2(11, ke); LBM_PAIR2(13, ke); LBM_PAIR2(15, ke); LBM_PAIR2(17, ke);
 #undef LBM_PAIR2
-}
-
-// The tile lists and records are read through L2 (ld.global.cg): with the
-// sweep overlapping the bubble update, they are written while the sweep runs,
-// so the read-only cache path is not used for them.
-__device__ __forceinline__ BubbleRec load_rec(const BubbleRec* p) {
-    const int4* q = reinterpret_cast<const int4*>(p);
-    const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
-    return BubbleRec{a.x, a.y, a.z, a.w,
-                     __int_as_float(b.x), __int_as_float(b.y), __int_as_float(b.z),
-                     __int_as_float(b.w), __int_as_float(c.x), __int_as_float(c.y),
-                     __int_as_float(c.z), __int_as_float(c.w)};
 }
 
 // Eq. 21 at the pair (x0, x0 + 1), (y, z) of a block whose tile lists n_t > 0
@@ -624,7 +473,7 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
                                             const BubbleRec* __restrict__ recs, int nb,
                                             int* __restrict__ flag, int bx, int by, int bz,
                                             BubbleRec* srec, const unsigned* safe = nullptr,
-                                            unsigned epoch = 0) {
+                                            unsigned epoch = 0, bool lead = false) {
     const int x0 = bx * TX + 2 * threadIdx.x;
     const int y = by * TY + threadIdx.y;
     const int z = bz * PZ + threadIdx.z;
@@ -636,35 +485,20 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
     // Read before the population loads: in plain stream order the tile count;
     // overlapped with the bubble update, the guard tag of this z layer (written
-    // by the update before, which has completed).  CTA 0 never skips, so the
-    // sweep cannot complete before the update.
+    // by the update before, which has completed).  The launch's first CTA
+    // (`lead`) never skips, so the sweep cannot complete before the update.
     int n_t = 0;
     bool skip = false;
     if (tile_count != nullptr) {
         if (safe == nullptr) n_t = __ldcg(tile_count + t);
-        else skip = (bx | by | bz) != 0 && __ldcg(safe + (bz * PZ) / TZ) == epoch;
+        else skip = !lead && __ldcg(safe + (bz * PZ) / TZ) == epoch;
     }
 
     const unsigned S = (unsigned)g.S;
     const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
     const unsigned site0 = (unsigned)za * nxy + (unsigned)ya * nx + (unsigned)xa;
     typename Raw2<ST>::T rv[Q];
-    if (ya > 0 && ya < g.ny - 1 && za > 0 && za < g.nz - 1) {
-        const bool wallx = (g.walls & 0x01) != 0;
-#define LBM_PP(J) rv[J] = pull_pair<ST, J>(fin, S, site0, nx, nxy, xa, wallx)
-        LBM_PP(0); LBM_PP(1); LBM_PP(2); LBM_PP(3); LBM_PP(4);
-        LBM_PP(5); LBM_PP(6); LBM_PP(7); LBM_PP(8); LBM_PP(9);
-        LBM_PP(10); LBM_PP(11); LBM_PP(12); LBM_PP(13); LBM_PP(14);
-        LBM_PP(15); LBM_PP(16); LBM_PP(17); LBM_PP(18);
-#undef LBM_PP
-    } else {
-#define LBM_PA(J) rv[J] = pull_pair_any<ST, J>(fin, g, xa, ya, za)
-        LBM_PA(0); LBM_PA(1); LBM_PA(2); LBM_PA(3); LBM_PA(4);
-        LBM_PA(5); LBM_PA(6); LBM_PA(7); LBM_PA(8); LBM_PA(9);
-        LBM_PA(10); LBM_PA(11); LBM_PA(12); LBM_PA(13); LBM_PA(14);
-        LBM_PA(15); LBM_PA(16); LBM_PA(17); LBM_PA(18);
-#undef LBM_PA
-    }
+    gather_pair<ST>(fin, g, xa, ya, za, rv);
     if (tile_count != nullptr && safe != nullptr && !skip) {
         // Overlapped, and the update before did not clear this layer: wait
         // for this step's update, then read its tile lists.
@@ -714,13 +548,17 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                       typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
                       const int* tile_start, const int* tile_count, const int* items, int cap,
                       const BubbleRec* recs, int nb, int* __restrict__ flag,
-                      const unsigned* safe, unsigned epoch) {
+                      const unsigned* safe, unsigned epoch, const int* zperm) {
     __shared__ BubbleRec srec[FORCE_CHUNK];
     // The next bubble update may be scheduled once every CTA of the sweep has
     // started; it waits for the sweep to complete before it reads anything.
     pdl_trigger();
+    // z blocks in the order the bubble update before chose (cleared layers
+    // first); the order was written by an update that has completed.
+    const int bz = zperm != nullptr ? __ldcg(zperm + blockIdx.z) : (int)blockIdx.z;
+    const bool lead = (blockIdx.x | blockIdx.y | blockIdx.z) == 0;
     sweep_block<ST, TAB>(fin, fout, g, cp, tile_start, tile_count, items, cap, recs, nb, flag,
-                         blockIdx.x, blockIdx.y, blockIdx.z, srec, safe, epoch);
+                         blockIdx.x, blockIdx.y, bz, srec, safe, epoch, lead);
 }
 
 // ---------------------------------------------------------------------------
@@ -800,6 +638,7 @@ cudaError_t launch_collide_batch(int storage, const void* fin, void* fout,
 }
 
 int batch_block_threads() { return PX * TY * PZ; }
+int sweep_z_blocks(int nz) { return (nz + PZ - 1) / PZ; }
 int batch_z_block() { return PZ; }
 int pair_min_blocks(int storage) {
     return storage == 0 ? PairOccupancy<0>::kMinBlocks : PairOccupancy<1>::kMinBlocks;
@@ -808,7 +647,8 @@ int pair_min_blocks(int storage) {
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, const unsigned* safe,
-                                  unsigned epoch, bool overlap, cudaStream_t st) {
+                                  unsigned epoch, bool overlap, const int* zperm,
+                                  cudaStream_t st) {
     const int* start = tl ? tl->start : nullptr;
     const int* count = tl ? tl->count : nullptr;
     const int* items = tl ? tl->items : nullptr;
@@ -833,7 +673,8 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
 #define LBM_LAUNCH_PAIR(SI, TB, T)                                                                \
     case SI * 2 + TB:                                                                             \
         return cudaLaunchKernelEx(&cfg, k_collide_stream_pair<SI, TB>, (const T*)fin, (T*)fout,   \
-                                  g, cp, start, count, items, cap, recs, nb, flag, safe, epoch);
+                                  g, cp, start, count, items, cap, recs, nb, flag, safe, epoch,  \
+                                  zperm);
             LBM_LAUNCH_PAIR(0, 0, float)
             LBM_LAUNCH_PAIR(0, 1, float)
             LBM_LAUNCH_PAIR(1, 0, __half)

@@ -14,6 +14,7 @@ struct AdjointTape;   // lbm_adjoint.cu
 using lbm::Bins;
 using lbm::BubbleDev;
 using lbm::SmallBins;
+using lbm::SwarmBins;
 
 struct lbm_ctx {
     int nx = 0, ny = 0, nz = 0;
@@ -49,10 +50,11 @@ struct lbm_ctx {
     // outside a step moves it past every stored tag (guard_invalidate), so
     // stale tags never clear a layer.
     unsigned epoch = 1;
-    // Large path: Eq. 10 velocity of the covered tiles (3 planes of S floats)
-    // and whether bins.cnt marks the windows of the current centres.
-    float* mom = nullptr;
+    // Large path: whether the tile lists (bins) and spreading records are
+    // those of the current centres.
     bool cover_valid = false;
+    // Large path: interpolation parts, list positions and binning scratch.
+    SwarmBins swarm{};
 
     // timing of the collide-stream launches
     bool timing = false;

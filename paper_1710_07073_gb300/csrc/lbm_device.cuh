@@ -233,4 +233,195 @@ __device__ __forceinline__ double cell_poly_d(double a, double b) {
     return (b - a) * (p4 * 0.2 - p2 * (2.0 / 3.0) + 1.0);
 }
 
+// Cell integral of the mapping along one axis for lattice coordinate c, with
+// the record's anchor cell `anc` and offset `fr` (Eq. 19), wrapped on a
+// periodic axis of length L to the nearer image.  The sweep's force gather and
+// the many-bubble interpolation both take their weights from it.
+__device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc, float fr, int L,
+                                             bool periodic) {
+    float rc = (float)(c - anc) + 0.5f - fr;
+    if (periodic) {
+        if (rc > 0.5f * L) rc -= (float)L;
+        else if (rc < -0.5f * L) rc += (float)L;
+    }
+    return cell_poly(rc * r.inv_n, r.h);
+}
+
+// The tile lists and records are read through L2 (ld.global.cg): with the
+// sweep overlapping the bubble update, they are written while the sweep runs,
+// so the read-only cache path is not used for them.
+__device__ __forceinline__ BubbleRec load_rec(const BubbleRec* p) {
+    const int4* q = reinterpret_cast<const int4*>(p);
+    const int4 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    return BubbleRec{a.x, a.y, a.z, a.w,
+                     __int_as_float(b.x), __int_as_float(b.y), __int_as_float(b.z),
+                     __int_as_float(b.w), __int_as_float(c.x), __int_as_float(c.y),
+                     __int_as_float(c.z), __int_as_float(c.w)};
+}
+
+// ---- two nodes per thread (even nx) -----------------------------------------
+// A thread owns the x-pair (x0, x0 + 1), x0 even, so every plane row is read
+// with one aligned 2-wide access (float2, half2, bfloat162) and the moments
+// run on packed FP32 pairs (FFMA2 / FADD2 / FMUL2).
+template <int ST> struct Vec2;
+template <> struct Vec2<0> {
+    static __device__ __forceinline__ void store(float* p, float2 v) {
+        __stcs(reinterpret_cast<float2*>(p), v);
+    }
+};
+template <> struct Vec2<1> {
+    static __device__ __forceinline__ void store(__half* p, float2 v) {
+        __stcs(reinterpret_cast<__half2*>(p), __floats2half2_rn(v.x, v.y));
+    }
+};
+template <> struct Vec2<2> {
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float2 v) {
+        __stcs(reinterpret_cast<__nv_bfloat162*>(p), __floats2bfloat162_rn(v.x, v.y));
+    }
+};
+
+// The stored values of one direction at an x-pair, as loaded.  FP32 keeps the
+// float2; the 16-bit formats keep both nodes packed in one 32-bit register
+// (node x0 in the low half) and widen at each use, which halves the registers
+// the 19 loaded rows hold while the moments and the relaxation run.
+template <int ST> struct Raw2 {
+    using T = unsigned;
+    using T1 = unsigned;
+    static __device__ __forceinline__ T load(const typename Store<ST>::T* p) {
+        return __ldg(reinterpret_cast<const unsigned*>(p));
+    }
+    static __device__ __forceinline__ T1 load1(const typename Store<ST>::T* p) {
+        return (unsigned)__ldg(reinterpret_cast<const unsigned short*>(p));
+    }
+    // (a, P.x) and (P.y, a)
+    static __device__ __forceinline__ T lo_from(T1 a, T P) { return __byte_perm(a, P, 0x5410); }
+    static __device__ __forceinline__ T hi_from(T P, T1 a) { return __byte_perm(P, a, 0x5432); }
+    static __device__ __forceinline__ T join(T1 a, T1 b) { return __byte_perm(a, b, 0x5410); }
+    static __device__ __forceinline__ float2 widen(T v);
+};
+template <> __device__ __forceinline__ float2 Raw2<1>::widen(unsigned v) {
+    return __half22float2(*reinterpret_cast<const __half2*>(&v));
+}
+template <> __device__ __forceinline__ float2 Raw2<2>::widen(unsigned v) {
+    return make_float2(__uint_as_float(v << 16), __uint_as_float(v & 0xffff0000u));
+}
+template <> struct Raw2<0> {
+    using T = float2;
+    using T1 = float;
+    static __device__ __forceinline__ T load(const float* p) {
+        return __ldg(reinterpret_cast<const float2*>(p));
+    }
+    static __device__ __forceinline__ T1 load1(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ T lo_from(T1 a, T P) { return make_float2(a, P.x); }
+    static __device__ __forceinline__ T hi_from(T P, T1 a) { return make_float2(P.y, a); }
+    static __device__ __forceinline__ T join(T1 a, T1 b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float2 widen(T v) { return v; }
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+
+// Raw values of direction J arriving at the pair (x0, x0 + 1) of a row whose
+// y and z neighbours are inside the box.  The aligned pair of the source row
+// covers one of the two; the population crossing x for the other node is one
+// scalar load, at x0 - 1 or x0 + 2 of the source row, or, on an x face, at the
+// opposite plane of the node itself (wall) or the other end of the row
+// (periodic).  Every lane issues the same loads, so none waits on another.
+template <int ST, int J>
+__device__ __forceinline__ typename Raw2<ST>::T pull_pair(const typename Store<ST>::T* __restrict__ f,
+                                                          unsigned S, unsigned site0, unsigned nx,
+                                                          unsigned nxy, int x0, bool wallx) {
+    const unsigned row = (unsigned)J * S + site0 - ((unsigned)cy(J) * nx + (unsigned)cz(J) * nxy);
+    const typename Raw2<ST>::T P = Raw2<ST>::load(f + row);   // the source row at (x0, x0 + 1)
+    if (cx(J) == 0) return P;
+    if (cx(J) == 1) {
+        // node x0 receives x0 - 1, node x0 + 1 receives x0
+        unsigned a = row - 1u;
+        if (x0 == 0) a = wallx ? (unsigned)opp(J) * S + site0 : row + nx - 1u;
+        return Raw2<ST>::lo_from(Raw2<ST>::load1(f + a), P);
+    }
+    // cx == -1: node x0 receives x0 + 1, node x0 + 1 receives x0 + 2
+    unsigned a = row + 2u;
+    if ((unsigned)x0 + 2u >= nx) a = wallx ? (unsigned)opp(J) * S + site0 + 1u : row - (unsigned)x0;
+    return Raw2<ST>::hi_from(P, Raw2<ST>::load1(f + a));
+}
+
+template <int ST, int J>
+__device__ __forceinline__ typename Raw2<ST>::T pull_pair_any(
+    const typename Store<ST>::T* __restrict__ f, const Geo& g, int x0, int y, int z) {
+    int p0, i0, p1, i1;
+    pull_source<J>(g, x0, y, z, p0, i0);
+    pull_source<J>(g, x0 + 1, y, z, p1, i1);
+    return Raw2<ST>::join(Raw2<ST>::load1(f + (size_t)p0 * (size_t)g.S + i0),
+                          Raw2<ST>::load1(f + (size_t)p1 * (size_t)g.S + i1));
+}
+
+// Eq. 10 moments of an x-pair from its raw stored values (as loaded):
+// drho = sum_j g_j and j = sum_j c_j g_j of the shifted populations, on packed
+// FP32 pairs.  The sum order is fixed (the sweep and the many-bubble
+// interpolation share it).
+template <int ST>
+__device__ __forceinline__ void pair_moments(const typename Raw2<ST>::T rr[Q],
+                                             const CollideParams& cp, float2& drho, float2& jx,
+                                             float2& jy, float2& jz) {
+    float2 rv[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) rv[j] = Raw2<ST>::widen(rr[j]);
+    const float2 s_axis = add2(add2(add2(rv[1], rv[2]), add2(rv[3], rv[4])), add2(rv[5], rv[6]));
+    const float2 s_edge = add2(add2(add2(add2(rv[7], rv[8]), add2(rv[9], rv[10])),
+                                    add2(add2(rv[11], rv[12]), add2(rv[13], rv[14]))),
+                               add2(add2(rv[15], rv[16]), add2(rv[17], rv[18])));
+    const float2 ax_x = sub2(rv[1], rv[2]), ax_y = sub2(rv[3], rv[4]), ax_z = sub2(rv[5], rv[6]);
+    const float2 d78 = sub2(rv[7], rv[8]), d910 = sub2(rv[9], rv[10]);
+    const float2 d1112 = sub2(rv[11], rv[12]), d1314 = sub2(rv[13], rv[14]);
+    const float2 d1516 = sub2(rv[15], rv[16]), d1718 = sub2(rv[17], rv[18]);
+    const float2 ed_x = add2(add2(d78, d910), add2(d1112, d1314));
+    const float2 ed_y = add2(sub2(d78, d910), add2(d1516, d1718));
+    const float2 ed_z = add2(sub2(d1112, d1314), sub2(d1516, d1718));
+    if (Store<ST>::kScaled) {
+        const float2 k0 = f2(wf(0) * cp.inv_scale), ka = f2(wf(1) * cp.inv_scale),
+                     ke = f2(wf(7) * cp.inv_scale);
+        drho = fma2(k0, rv[0], fma2(ka, s_axis, mul2(ke, s_edge)));
+        jx = fma2(ka, ax_x, mul2(ke, ed_x));
+        jy = fma2(ka, ax_y, mul2(ke, ed_y));
+        jz = fma2(ka, ax_z, mul2(ke, ed_z));
+    } else {
+        drho = add2(rv[0], add2(s_axis, s_edge));
+        jx = add2(ax_x, ed_x);
+        jy = add2(ax_y, ed_y);
+        jz = add2(ax_z, ed_z);
+    }
+}
+
+// The raw values of all 19 directions arriving at the pair (x0, x0 + 1) of
+// row (y, z) (x0 even, x0 + 1 < nx): the aligned-row gather inside, the
+// general one on the y and z faces.
+template <int ST>
+__device__ __forceinline__ void gather_pair(const typename Store<ST>::T* __restrict__ f,
+                                            const Geo& g, int x0, int y, int z,
+                                            typename Raw2<ST>::T rv[Q]) {
+    if (y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1) {
+        const unsigned S = (unsigned)g.S;
+        const unsigned nx = (unsigned)g.nx, nxy = (unsigned)g.nx * (unsigned)g.ny;
+        const unsigned site0 = (unsigned)z * nxy + (unsigned)y * nx + (unsigned)x0;
+        const bool wallx = (g.walls & 0x01) != 0;
+#define LBM_PP(J) rv[J] = pull_pair<ST, J>(f, S, site0, nx, nxy, x0, wallx)
+        LBM_PP(0); LBM_PP(1); LBM_PP(2); LBM_PP(3); LBM_PP(4);
+        LBM_PP(5); LBM_PP(6); LBM_PP(7); LBM_PP(8); LBM_PP(9);
+        LBM_PP(10); LBM_PP(11); LBM_PP(12); LBM_PP(13); LBM_PP(14);
+        LBM_PP(15); LBM_PP(16); LBM_PP(17); LBM_PP(18);
+#undef LBM_PP
+    } else {
+#define LBM_PA(J) rv[J] = pull_pair_any<ST, J>(f, g, x0, y, z)
+        LBM_PA(0); LBM_PA(1); LBM_PA(2); LBM_PA(3); LBM_PA(4);
+        LBM_PA(5); LBM_PA(6); LBM_PA(7); LBM_PA(8); LBM_PA(9);
+        LBM_PA(10); LBM_PA(11); LBM_PA(12); LBM_PA(13); LBM_PA(14);
+        LBM_PA(15); LBM_PA(16); LBM_PA(17); LBM_PA(18);
+#undef LBM_PA
+    }
+}
+
 }  // namespace lbm

@@ -22,6 +22,16 @@ constexpr int Q = 19;
 // all threads of a CTA share one tile.
 constexpr int TX = 32, TY = 4, TZ = 4;
 constexpr int MAX_AXIS_TILES = 8;   // per-axis tiles a window may touch (n <= 9)
+// z planes per CTA of the two-node collide-stream sweep (divides TZ); a
+// compile-time knob of the sweep's launch shape.
+#ifndef LBM_PAIR_PZ
+#define LBM_PAIR_PZ 2
+#endif
+constexpr int SWEEP_PZ = LBM_PAIR_PZ;
+// Resident CTAs per SM of the many-bubble binning launch.
+#ifndef LBM_SWARM_CTAS_PER_SM
+#define LBM_SWARM_CTAS_PER_SM 4
+#endif
 constexpr double MAX_HALF_WIDTH = 9.0;
 
 __host__ __device__ __forceinline__ constexpr int cx(int j) {
@@ -183,6 +193,33 @@ struct SmallBins {
     // set its own sweep reads.  Null: not kept.
     unsigned* safe;    // [ntz] (the set this launch writes)
     unsigned safe_epoch;
+    // Order of the next sweep's z blocks (PZ planes each): the blocks of
+    // cleared layers first, then the guarded ones, each in ascending order,
+    // so that the sweep reaches the layers that wait for the update last.
+    // Null: not kept.
+    int* zperm;        // [nbz] (the set this launch writes)
+    int nbz;
+};
+
+// Many bubbles: the bubble side of a step in three launches
+// (launch_swarm_update), with the binning done by one persistent launch whose
+// phases are separated by grid barriers over CTAs that are all resident.
+// Besides the tile lists of `Bins`, the binning records where each bubble sits
+// in each of its tiles' lists (slots), so that the next step's interpolation
+// can be summed per tile and gathered per bubble in a fixed order.
+struct SwarmBins {
+    unsigned* bar;        // [2] grid barrier: arrivals, generation (zero between launches)
+    int* cursor;          // [T] fill cursors of the counting sort
+    int* kidx;            // [cap] for each list entry: which of its bubble's tiles it is
+    int* slots;           // [nb * per] list position of bubble b's k-th tile
+    int* ntile;           // [nb] tiles of bubble b in the last binning (0: not binned)
+    int per;              // tiles a bubble's window can touch at most
+    float* partial;       // [3 * cap] Eq. 20 sums of each (tile, bubble) entry
+    int* cover;           // [T] the tiles with a non-empty list (any order)
+    int* ncover;          // [1] their number
+    int interp_grid;      // CTAs of the interpolation launch
+    int* chunk_sums;      // [grid] per-CTA count totals (scan)
+    int grid;             // CTAs of the binning launch (all resident)
 };
 
 // A bubble moves at most this many cells along an axis per liquid step (a
@@ -209,10 +246,13 @@ struct BatchColumn {
 // the bubble update before it (`overlap`): CTAs whose z tile layer holds
 // safe[layer] == epoch run without waiting for the update; the others (and
 // CTA 0) wait for it before reading the tile lists.
+// zperm (may be null): the order of the z blocks (PZ planes each) in which
+// the CTAs are handed out, a permutation of 0 .. ceil(nz / PZ) - 1.
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, const unsigned* safe,
-                                  unsigned epoch, bool overlap, cudaStream_t st);
+                                  unsigned epoch, bool overlap, const int* zperm,
+                                  cudaStream_t st);
 
 // Bubble update with the few-pair binning in the same launch (sb.parts CTAs
 // per bubble).  `overlap`: launched as a programmatic dependent of the sweep
@@ -233,12 +273,36 @@ cudaError_t upload_bubble_state(const BubbleDev& B, int n, const double* pos3, c
 // skipped), converted on the device into B.out64.  Synchronises the stream.
 cudaError_t download_bubble_state(const BubbleDev& B, int k, double* pos3, double* vel3,
                                   double* ul3, double* psi3, cudaStream_t st);
-// Many bubbles: Eq. 10 velocity of the covered tiles into mom[3*S], then one
-// warp per 32 bubbles interpolating from it.  tile_count: the binning of the
-// current centres (count > 0 marks a covered tile).
-cudaError_t launch_bubbles_many(int storage, const void* f, float* mom, const Geo& g,
-                                const CollideParams& cp, const BubbleDev& b, const BubbleConst& bc,
-                                const int* tile_count, int* flag, cudaStream_t st);
+// Many bubbles, three launches per step, in stream order:
+//   1. per tile the current binning lists (persistent over the list of
+//      covered tiles): the Eq. 10 velocity of its nodes, and for each listed
+//      bubble the part of its Eq. 20 sum over the tile (weights from the
+//      bubble's spreading record, which holds the current centre);
+//   2. per bubble (a thread each): its parts added in tile order, the Table 1
+//      forces and Eq. 4 sub-steps, the reaction and the new record;
+//   3. the binning of the updated bubbles (one persistent launch, sw.grid
+//      CTAs): tile lists, list positions and the list of covered tiles.
+// A grid barrier that waits longer than a second sets flag bit 8.
+constexpr int SWARM_LAUNCHES = 3;
+cudaError_t launch_swarm_update(int storage, const void* f, const Geo& g,
+                                const CollideParams& cp, const BubbleDev& b,
+                                const BubbleConst& bc, int* flag, const Bins& bins,
+                                const SwarmBins& sw, cudaStream_t st);
+// Many bubbles: the binning alone, of the bubbles with select[b] != 0 (the
+// first step's lists of the current centres); bins.cnt and *sw.ncover must
+// be zero.
+cudaError_t launch_swarm_binning(const Geo& g, const BubbleDev& b, const Bins& bins,
+                                 const SwarmBins& sw, const int* select, int* flag,
+                                 cudaStream_t st);
+// Spreading records (anchor cell, offset, window) of the current centres,
+// with the current reaction.
+cudaError_t launch_bubble_records(const Geo& g, const BubbleDev& b, cudaStream_t st);
+// CTAs of the many-bubble binning launch that are resident at once on this
+// device, and of the interpolation launch (persistent over the covered tiles).
+int swarm_grid(int storage);
+int interp_grid(int storage);
+// Sweep z blocks (planes per CTA of the pair sweep) for nz planes.
+int sweep_z_blocks(int nz);
 // Kernels launched by one launch_binning call (count, 3-pass scan, fill, sort).
 // Bubbles b with select[b] != 0 are binned; select defaults to b.spread.
 constexpr int BINNING_LAUNCHES = 6;

@@ -46,22 +46,37 @@ class CountingAllocator:
 DIMS = (16, 16, 32)
 
 
-def _column_workflow(ctx, many):
-    """set_fields, set_bubbles, step, read back; returns the outputs."""
-    S = int(np.prod(DIMS))
+def _run_from(phases, start):
+    """Run phases[start:], each a callable; returns (index of a phase that raised
+    LbmError or None, the error)."""
+    for i in range(start, len(phases)):
+        try:
+            phases[i]()
+        except lbm.LbmError as e:
+            return i, e
+    return None, None
+
+
+def _column_phases(ctx, many, out):
+    """set_fields, set_bubbles, step, read back: each a separate call."""
     rho, u = workloads.random_fields(DIMS, seed=11, amp=1e-4, rho_amp=1e-4)
-    lbm.lbm_set_fields(ctx, rho.reshape(-1), u.reshape(-1))
     if many:
         pos, vel, diam = workloads.swarm(DIMS, 120, seed=5)
     else:
         pos, vel, diam = workloads.single_bubble(DIMS)
-    lbm.lbm_set_bubbles(ctx, pos.reshape(-1), vel.reshape(-1), diam)
-    lbm.lbm_step(ctx, 3)
-    _, uo = lbm.lbm_get_fields(ctx)
-    tot = lbm.lbm_get_totals(ctx)
-    b = lbm.lbm_get_bubbles(ctx)
-    assert uo.size == 3 * S
-    return uo, tot, b["pos"]
+
+    def fields():
+        out["u"] = lbm.lbm_get_fields(ctx)[1]
+
+    def totals():
+        out["tot"] = lbm.lbm_get_totals(ctx)
+
+    def bubbles():
+        out["pos"] = lbm.lbm_get_bubbles(ctx)["pos"]
+
+    return [lambda: lbm.lbm_set_fields(ctx, rho.reshape(-1), u.reshape(-1)),
+            lambda: lbm.lbm_set_bubbles(ctx, pos.reshape(-1), vel.reshape(-1), diam),
+            lambda: lbm.lbm_step(ctx, 3), fields, totals, bubbles]
 
 
 def _fresh(torch, fail_at):
@@ -71,31 +86,40 @@ def _fresh(torch, fail_at):
     return ctx, alloc
 
 
+def _check_every_failure(torch, fresh, phases_of, last_error, destroy):
+    """Make allocation k fail for every k of a clean run: the failing call
+    returns LBM_ERR_ALLOC with a message and keeps nothing; retrying it (and
+    running the rest) gives the bits of the clean run; destroy frees all."""
+    h, alloc = fresh(torch, None)
+    ref = {}
+    assert _run_from(phases_of(h, ref), 0) == (None, None)
+    ncalls = alloc.calls
+    destroy(h)
+    assert alloc.live == {} and not alloc.errors
+    assert ncalls >= 10
+    for k in range(1, ncalls + 1):
+        h, alloc = fresh(torch, k)
+        out = {}
+        phases = phases_of(h, out)
+        i, err = _run_from(phases, 0)
+        assert err is not None and err.code == lbm.LBM_ERR_ALLOC, (k, i, str(err))
+        assert last_error(h), k
+        alloc.fail_at = None
+        assert _run_from(phases, i) == (None, None), k
+        assert ref.keys() == out.keys()
+        for key in ref:
+            assert np.array_equal(ref[key], out[key]), (k, i, key)
+        destroy(h)
+        assert alloc.live == {}, (k, len(alloc.live))
+        assert not alloc.errors, k
+
+
 @pytest.mark.parametrize("many", [False, True], ids=["few_bubbles", "many_bubbles"])
 def test_column_alloc_failure_every_call(many):
     import torch
     assert torch.cuda.is_available()
-    ctx, alloc = _fresh(torch, None)
-    ref = _column_workflow(ctx, many)
-    ncalls = alloc.calls
-    lbm.lbm_destroy(ctx)
-    assert alloc.live == {} and not alloc.errors
-    assert ncalls >= 10
-    for k in range(1, ncalls + 1):
-        ctx, alloc = _fresh(torch, k)
-        with pytest.raises(lbm.LbmError) as e:
-            _column_workflow(ctx, many)
-        assert e.value.code == lbm.LBM_ERR_ALLOC, (k, str(e.value))
-        assert lbm.lbm_last_error(ctx), k
-        # The failed call kept nothing: what is live is what earlier calls
-        # completed with.  The same context then runs the whole workflow.
-        alloc.fail_at = None
-        out = _column_workflow(ctx, many)
-        for a, b in zip(out, ref):
-            assert np.array_equal(a, b), k
-        lbm.lbm_destroy(ctx)
-        assert alloc.live == {}, (k, len(alloc.live))
-        assert not alloc.errors, k
+    _check_every_failure(torch, _fresh, lambda h, out: _column_phases(h, many, out),
+                         lbm.lbm_last_error, lbm.lbm_destroy)
 
 
 def test_step_as_first_device_call_reports_alloc():
@@ -112,42 +136,34 @@ def test_step_as_first_device_call_reports_alloc():
         assert alloc.live == {} and not alloc.errors
 
 
-def _batch_workflow(b):
-    cols = workloads.batch_columns(3, seed=3)
+BATCH_COLS = workloads.batch_columns(3, seed=3)
+
+
+def _batch_phases(b, out):
+    cols = BATCH_COLS
     pos = np.concatenate([c[2] for c in cols])
     vel = np.concatenate([c[3] for c in cols])
     diam = np.concatenate([c[4] for c in cols])
-    lbm.lbm_batch_set_bubbles(b, [1, 1, 1], pos.reshape(-1), vel.reshape(-1), diam)
-    lbm.lbm_batch_step(b, 4)
-    _, u = lbm.lbm_batch_get_fields(b, 1, int(np.prod(cols[1][0])))
-    return u, lbm.lbm_batch_get_bubbles(b)["pos"]
+
+    def fields():
+        out["u"] = lbm.lbm_batch_get_fields(b, 1, int(np.prod(cols[1][0])))[1]
+
+    def bubbles():
+        out["pos"] = lbm.lbm_batch_get_bubbles(b)["pos"]
+
+    return [lambda: lbm.lbm_batch_set_bubbles(b, [1, 1, 1], pos.reshape(-1), vel.reshape(-1),
+                                              diam),
+            lambda: lbm.lbm_batch_step(b, 4), fields, bubbles]
 
 
 def _fresh_batch(torch, fail_at):
-    cols = workloads.batch_columns(3, seed=3)
     alloc = CountingAllocator(torch, fail_at)
-    b = lbm.lbm_batch_create([c[0] for c in cols], [c[1] for c in cols])
+    b = lbm.lbm_batch_create([c[0] for c in BATCH_COLS], [c[1] for c in BATCH_COLS])
     lbm.lbm_batch_set_allocator(b, alloc.alloc, alloc.free)
     return b, alloc
 
 
 def test_batch_alloc_failure_every_call():
     import torch
-    b, alloc = _fresh_batch(torch, None)
-    ref = _batch_workflow(b)
-    ncalls = alloc.calls
-    lbm.lbm_batch_destroy(b)
-    assert alloc.live == {} and not alloc.errors
-    for k in range(1, ncalls + 1):
-        b, alloc = _fresh_batch(torch, k)
-        with pytest.raises(lbm.LbmError) as e:
-            _batch_workflow(b)
-        assert e.value.code == lbm.LBM_ERR_ALLOC, (k, str(e.value))
-        assert lbm.lbm_batch_last_error(b), k
-        alloc.fail_at = None
-        out = _batch_workflow(b)
-        for x, y in zip(out, ref):
-            assert np.array_equal(x, y), k
-        lbm.lbm_batch_destroy(b)
-        assert alloc.live == {}, (k, len(alloc.live))
-        assert not alloc.errors, k
+    _check_every_failure(torch, _fresh_batch, _batch_phases, lbm.lbm_batch_last_error,
+                         lbm.lbm_batch_destroy)

@@ -1,10 +1,12 @@
 """GPU: the bubble update overlapped with the sweep gives the same bits as plain
 stream order.
 
-A single column with few bubbles runs each step's bubble update (Algorithm 1
-steps 2-6) and the collide-stream sweep (Eq. 12-16, 21) as overlapping
-launches: sweep CTAs whose z tile layer the previous update cleared (no
-bubble support, widened by 4 cells, reaches it) do not wait for the update.
+A single column runs each step's bubble update (Algorithm 1 steps 2-6; one
+launch for few bubbles, and one persistent launch of covered-tile
+velocities, update and binning for many) and the collide-stream sweep
+(Eq. 12-16, 21) as overlapping launches: sweep CTAs whose z tile layer the
+previous update cleared (no bubble support, widened by 4 cells, reaches it)
+do not wait for the update, and run first.
 With kernel timing on, the library keeps plain stream order instead, so the
 two runs below differ only in that scheduling; every population and bubble
 value must agree bit for bit.  A bubble faster than 4 cells per step is
@@ -15,8 +17,9 @@ import os
 import numpy as np
 import pytest
 
+from oracle import binning as obin
 from oracle import lattice as olat
-from paper_1710_07073_gb300 import lbm
+from paper_1710_07073_gb300 import lbm, workloads
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +44,8 @@ def _run(dims, walls, pos, vel, diam, steps, plain, storage=lbm.LBM_STORE_F32, s
         lbm.lbm_step(col.ctx, steps // chunks)
     f = lbm.lbm_get_populations(col.ctx)
     b = lbm.lbm_get_bubbles(col.ctx)
+    b["bins"] = lbm.lbm_get_bins(col.ctx)
+    b["sweep"] = lbm.lbm_sweep_kernel(col.ctx)
     col.close()
     return f, b
 
@@ -99,3 +104,42 @@ def test_bubble_faster_than_guard_is_unstable():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_step(col.ctx, 1)
     assert e.value.code == lbm.LBM_ERR_UNSTABLE
+
+
+def _swarm_case(dims, walls, count, seed):
+    pos, _, diam = workloads.swarm(dims, count, seed=seed, bottom_fraction=0.4)
+    rng = np.random.default_rng(seed)
+    vel = np.zeros((count, 3))
+    vel[:, 2] = rng.uniform(0.02, 0.06, count)
+    return dims, walls, pos, vel, diam
+
+
+# Enough bubbles that their (tile, bubble) pairs may exceed 4096: the
+# many-bubble path.
+MANY = {
+    "swarm, walls": _swarm_case((64, 32, 96), olat.ALL_WALLS, 320, 9),
+    "swarm, periodic z": _swarm_case((64, 32, 64), olat.WALL_XM | olat.WALL_XP | olat.WALL_YM
+                                     | olat.WALL_YP, 300, 10),
+}
+
+
+@pytest.mark.parametrize("case", sorted(MANY))
+@pytest.mark.parametrize("storage,scale", [(lbm.LBM_STORE_F32, 1.0), (lbm.LBM_STORE_F16, 256.0)])
+def test_many_bubbles_overlapped_match_plain_order(case, storage, scale):
+    dims, walls, pos, vel, diam = MANY[case]
+    plain = _run(dims, walls, pos, vel, diam, 120, plain=True, storage=storage, scale=scale)
+    over = _run(dims, walls, pos, vel, diam, 120, plain=False, storage=storage, scale=scale,
+                chunks=3)
+    _assert_same(plain, over)
+    z0 = np.asarray(pos, float)[:, 2]
+    z1 = over[1]["pos"][:, 2]
+    assert np.count_nonzero(np.floor(z0 / 4) != np.floor(z1 / 4)) > 10
+    # The binning left by the last update is the oracle's brute-force binning
+    # of the same centres (Algorithm 1 step 2).
+    bins = over[1]["bins"]
+    hw = lbm.lbm_default_params().width_factor * np.asarray(diam)
+    assert over[1]["sweep"].endswith(",1>")   # the many-bubble path ran
+    off, items = obin.tile_lists(list(over[1]["pos"]), list(hw), np.ones(len(hw), bool), dims,
+                                 walls, bins["tile"])
+    assert np.array_equal(bins["offsets"], np.array(off))
+    assert np.array_equal(bins["items"], np.array(items))
