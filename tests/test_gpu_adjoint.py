@@ -4,7 +4,8 @@ FP64 oracle (central, FP64) and through the PyTorch autograd.Function.
 Objective: L = (ubar - target)^2, ubar the mean rise velocity u_b,z over the
 last `window` steps.  Gradients with respect to the drag scale, the bubble
 diameter and the initial velocity field (along a seeded Gaussian direction).
-Bar: 1e-4 relative for the drag scale and the diameter.
+Bar: 1e-4 relative for all three, against central differences of the FP64
+oracle; a 16x16x32 column and a 32x32x64 column over 200 steps.
 """
 import numpy as np
 import pytest
@@ -51,7 +52,7 @@ def _gpu_grads(prob, sd, d, u0):
     return loss, g_sd, g_d.sum(), g_u0
 
 
-def _check(prob, sd=1.0, d=2.5, eps=1.0, seed=4, rel_u0=1e-3):
+def _check(prob, sd=1.0, d=2.5, eps=1.0, seed=4):
     P = workloads.gaussian_velocity_perturbation(prob.dims, seed=seed, amp=1e-4)
     loss, g_sd, g_d, g_u0 = _gpu_grads(prob, sd, d, eps * P)
     l_or = _oracle_loss(prob, sd, d, eps * P)
@@ -66,12 +67,20 @@ def _check(prob, sd=1.0, d=2.5, eps=1.0, seed=4, rel_u0=1e-3):
           % (g_sd, fd_sd, g_d, fd_d, g_e, fd_e))
     assert abs(g_sd / fd_sd - 1.0) < REL
     assert abs(g_d / fd_d - 1.0) < REL
-    assert abs(g_e - fd_e) <= rel_u0 * abs(fd_e) + 1e-3 * abs(fd_sd) * 1e-4
+    assert abs(g_e / fd_e - 1.0) < REL
     return g_u0
 
 
 def test_adjoint_single_bubble_against_oracle_fd():
     _check(_problem())
+
+
+def test_adjoint_mid_size_column_against_oracle_fd():
+    # 32x32x64 over 200 steps with a checkpoint every 50 (the full-size
+    # workload's segment length), d = 2.5.
+    prob = _problem(dims=(32, 32, 64), positions=((16.0, 16.0, 8.0),), steps=200, every=50,
+                    window=40)
+    _check(prob, d=2.5)
 
 
 def test_adjoint_two_bubbles_periodic_x_against_oracle_fd():
