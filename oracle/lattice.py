@@ -31,6 +31,13 @@ OPP = np.array([int(np.flatnonzero((C == -C[j]).all(axis=1))[0]) for j in range(
 # Wall bit for each face, in the order (-x, +x, -y, +y, -z, +z).
 WALL_XM, WALL_XP, WALL_YM, WALL_YP, WALL_ZM, WALL_ZP = (1 << k for k in range(6))
 ALL_WALLS = 0x3F
+# With the +z face bounded (WALL_ZP), this bit makes it free-slip instead of
+# no-slip (Sec. 3.3: free-slip top).
+TOP_FREE_SLIP = 0x40
+
+# The direction with c_z reversed (same tangential components) of each c_j.
+MIRZ = np.array([int(np.flatnonzero((C == C[j] * np.array([1, 1, -1])).all(axis=1))[0])
+                 for j in range(Q)])
 
 
 def viscosity(omega):
@@ -123,11 +130,19 @@ def stream(fpost, walls):
     (outside) node (Sec. 3.3, read as plain half-way bounce-back): a population
     whose link x -> x + c_j crosses a wall returns to x as the opposite
     population, f_{opp(j)}(x, t + 1) = f''_j(x, t).
+
+    With ``TOP_FREE_SLIP`` set the +z face is a free-slip plane half-way above
+    the top layer (Sec. 3.3): a population leaving through it is reflected
+    specularly, its z component reversed and its tangential ones kept, so it
+    arrives one tangential step further in the top layer,
+    f_{mirz(j)}(x + (c_x, c_y, 0), t + 1) = f''_j(x, t).  A link that also
+    crosses a no-slip face bounces back instead.
     """
     _check_walls(walls)
     nz, ny, nx = fpost.shape[1:]
     shape = (nx, ny, nz)
     wall_axis = [bool(walls & (1 << (2 * d))) for d in range(3)]
+    free_top = bool(walls & TOP_FREE_SLIP)
     out = np.empty_like(fpost)
     # Coordinates of every node, per axis, broadcast to the field shape.
     coord = [np.arange(shape[0])[None, None, :], np.arange(shape[1])[None, :, None],
@@ -142,12 +157,29 @@ def stream(fpost, walls):
     # that link crosses a wall, the value is instead f''_{opp(j)}(x).
     for j in range(Q):
         crosses = np.zeros(fpost.shape[1:], dtype=bool)
+        through_top = np.zeros(fpost.shape[1:], dtype=bool)
         for d in range(3):
             if C[j, d] == 0 or not wall_axis[d]:
                 continue
             src = coord[d] - C[j, d]
-            crosses = crosses | np.broadcast_to((src < 0) | (src >= shape[d]), crosses.shape)
+            out_lo = np.broadcast_to(src < 0, crosses.shape)
+            out_hi = np.broadcast_to(src >= shape[d], crosses.shape)
+            if d == 2 and free_top:
+                crosses = crosses | out_lo
+                through_top = out_hi
+            else:
+                crosses = crosses | out_lo | out_hi
         out[j][crosses] = fpost[OPP[j]][crosses]
+        if free_top and C[j, 2] == -1:
+            # Specular reflection at the free-slip top: the population c_j
+            # arrives from the mirrored one, mirz(j), that left the top layer
+            # one tangential step back (wrapped on periodic axes).
+            mirrored = fpost[MIRZ[j]]
+            for d in range(2):
+                if C[j, d] != 0:
+                    mirrored = np.roll(mirrored, C[j, d], axis=2 - d)
+            specular = through_top & ~crosses
+            out[j][specular] = mirrored[specular]
     return out
 
 
@@ -157,6 +189,8 @@ def _check_walls(walls):
         hi = bool(walls & (1 << (2 * d + 1)))
         if lo != hi:
             raise ValueError("both faces of an axis must be walls, or both periodic")
+    if (walls & TOP_FREE_SLIP) and not (walls & WALL_ZP):
+        raise ValueError("a free-slip top needs a bounded z axis")
 
 
 def lb_step(f, omega, walls, force=None):

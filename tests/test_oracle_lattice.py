@@ -189,3 +189,85 @@ def test_poiseuille_second_order_in_height():
     e16 = _poiseuille(1.0, 16, 3000)
     assert e16 < 5e-3
     assert 3.5 < e8 / e16 < 4.5
+
+
+# ---- free-slip top (Sec. 3.3) --------------------------------------------------
+
+def _mirror_z(f):
+    """Populations of the column reflected in z: f'_j(z) = f_{mirz(j)}(nz - 1 - z)."""
+    return f[lat.MIRZ][:, ::-1]
+
+
+@pytest.mark.parametrize("side_walls", [lat.WALL_XM | lat.WALL_XP, 0])
+def test_free_slip_top_is_a_mirror_plane(side_walls):
+    # A specular (free-slip) plane half-way above the top layer is a plane of
+    # symmetry: a column of height H with a free-slip top evolves exactly like
+    # the lower half of a column of height 2H with no-slip walls at both ends,
+    # started from the mirror image of itself (populations with c_z reversed,
+    # the force with F_z reversed).  This fixes the reflected direction, the
+    # tangential shift, and the height of the plane.
+    rng = np.random.default_rng(11)
+    nx, ny, H = 6, 5, 7
+    rho = 1.0 + 1e-3 * rng.standard_normal((H, ny, nx))
+    u = 1e-2 * rng.standard_normal((3, H, ny, nx))
+    f = lat.equilibrium(rho, u) * (1.0 + 1e-3 * rng.standard_normal((lat.Q, H, ny, nx)))
+    force = 1e-4 * rng.standard_normal((3, H, ny, nx))
+    full = np.concatenate([f, _mirror_z(f)], axis=1)
+    fmir = force[:, ::-1].copy()
+    fmir[2] *= -1.0
+    force_full = np.concatenate([force, fmir], axis=1)
+    w_half = side_walls | lat.WALL_ZM | lat.WALL_ZP | lat.TOP_FREE_SLIP
+    w_full = side_walls | lat.WALL_ZM | lat.WALL_ZP
+    for _ in range(4):
+        f = lat.lb_step(f, 1.3, w_half, force)
+        full = lat.lb_step(full, 1.3, w_full, force_full)
+        assert np.abs(full[:, :H] - f).max() < 1e-15
+        assert np.abs(full[:, H:] - _mirror_z(f)).max() < 1e-15
+
+
+def test_free_slip_top_reflects_a_single_population():
+    # A population leaving the top layer through the free-slip plane comes
+    # back into the top layer with c_z reversed, one tangential step along
+    # (c_x, c_y) (periodic sides), and nothing is lost.
+    nx, ny, nz = 5, 4, 6
+    walls = lat.WALL_ZM | lat.WALL_ZP | lat.TOP_FREE_SLIP
+    for j in range(lat.Q):
+        f = np.zeros((lat.Q, nz, ny, nx))
+        f[j, nz - 1, 2, 1] = 1.0
+        out = lat.stream(f, walls)
+        cx, cy, cz = lat.C[j]
+        if cz == 1:
+            assert out[lat.MIRZ[j], nz - 1, (2 + cy) % ny, (1 + cx) % nx] == 1.0
+        else:
+            assert out[j, nz - 1 + cz, (2 + cy) % ny, (1 + cx) % nx] == 1.0
+        assert out.sum() == 1.0
+    # Also through an edge where the top meets a no-slip side wall: the
+    # link crosses the wall, so it bounces back to the same node.
+    walls_x = walls | lat.WALL_XM | lat.WALL_XP
+    for j in range(lat.Q):
+        if lat.C[j, 2] != 1 or lat.C[j, 0] != 1:
+            continue
+        f = np.zeros((lat.Q, nz, ny, nx))
+        f[j, nz - 1, 2, nx - 1] = 1.0
+        out = lat.stream(f, walls_x)
+        assert out[lat.OPP[j], nz - 1, 2, nx - 1] == 1.0
+
+
+def test_free_slip_top_half_poiseuille_exact():
+    # Body-force driven flow between a no-slip wall at z = 0 and a free-slip
+    # plane at z = H: u = F z (2H - z) / (2 rho nu), zero shear at z = H (half
+    # of the Poiseuille profile of height 2H).  Exact at (tau - 1/2)^2 = 3/16,
+    # where half-way bounce-back puts the wall at z = 0.
+    omega = 1.0 / (0.5 + np.sqrt(3.0) / 4.0)
+    H = 6
+    f = lat.equilibrium(np.ones((H, 1, 1)), np.zeros((3, H, 1, 1)))
+    force = np.zeros((3, H, 1, 1))
+    gx = 1e-6
+    force[0] = gx
+    walls = lat.WALL_ZM | lat.WALL_ZP | lat.TOP_FREE_SLIP
+    for _ in range(3000):
+        f = lat.lb_step(f, omega, walls, force)
+    u = lat.velocity(f, force)[0, :, 0, 0]
+    z = np.arange(H) + 0.5
+    exact = gx / (2.0 * lat.viscosity(omega)) * z * (2.0 * H - z)
+    assert np.abs(u - exact).max() / exact.max() < 1e-9
