@@ -57,7 +57,14 @@ extern "C" {
 
 /* ---- walls: one bit per box face; a set bit is a half-way bounce-back
  * no-slip wall (Sec. 3.3), a clear bit makes the axis periodic.  Both faces
- * of an axis must agree. ---------------------------------------------------- */
+ * of an axis must agree.  LBM_TOP_FREE_SLIP, with LBM_WALL_ZP set, makes the
+ * +z face a free-slip plane half-way above the top layer instead (Sec. 3.3:
+ * free-slip top): a population leaving through it is reflected specularly,
+ * c_z reversed and the tangential components kept, into the top layer one
+ * tangential step along; a link that also crosses a no-slip face bounces
+ * back.  Bubbles treat the face like a wall (clipped windows, clamped
+ * centres, the stop at the top).  LBM_WALL_ALL_FREE_TOP: no-slip everywhere
+ * but the free-slip top. --------------------------------------------------- */
 #define LBM_WALL_XM  0x01
 #define LBM_WALL_XP  0x02
 #define LBM_WALL_YM  0x04
@@ -65,6 +72,8 @@ extern "C" {
 #define LBM_WALL_ZM  0x10
 #define LBM_WALL_ZP  0x20
 #define LBM_WALL_ALL 0x3F
+#define LBM_TOP_FREE_SLIP 0x40
+#define LBM_WALL_ALL_FREE_TOP 0x7F
 
 /* ---- population storage precision (collision arithmetic is always FP32).
  * Populations are stored shifted by their rest-state value w_j * rho_l:
@@ -227,7 +236,9 @@ int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
  * treated as fixed switches.  Needs FP32 storage, 1..64 bubbles.  After the
  * backward the context is back at the state the forward ended in.  Any call
  * that changes the state between the two (lbm_step, lbm_set_*) discards the
- * record; lbm_adj_backward then returns LBM_ERR_STATE.  Memory: one state per
+ * record; lbm_adj_backward then returns LBM_ERR_STATE.  A free-slip top
+ * (LBM_TOP_FREE_SLIP) is not covered: lbm_adj_forward returns LBM_ERR_STATE.
+ * Memory: one state per
  * checkpoint plus checkpoint_every states during the backward.  With kernel
  * timing on (lbm_set_kernel_timing), lbm_adj_backward times each launch of
  * the per-node adjoint sweep instead of the forward collide-stream. */

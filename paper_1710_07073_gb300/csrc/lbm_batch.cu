@@ -383,9 +383,10 @@ int lbm_batch_create(int ncols, const int* dims3, const double* omegas, const un
         if (nx <= 0 || ny <= 0 || nz <= 0 || (nx & 1)) return LBM_ERR_ARG;
         if (!(omegas[c] > 0.0 && omegas[c] < 2.0)) return LBM_ERR_ARG;
         const unsigned w = walls ? walls[c] : (unsigned)LBM_WALL_ALL;
-        if (w & ~0x3Fu) return LBM_ERR_ARG;
+        if (w & ~0x7Fu) return LBM_ERR_ARG;
         for (int a = 0; a < 3; ++a)
             if (!(w & (1u << (2 * a))) != !(w & (1u << (2 * a + 1)))) return LBM_ERR_ARG;
+        if ((w & WALL_TOP_FREE) && !(w & 0x20u)) return LBM_ERR_ARG;
         const unsigned long long S = (unsigned long long)nx * ny * nz;
         if (S * Q >= (1ULL << 32)) return LBM_ERR_ARG;
         elems += S * Q;

@@ -1598,12 +1598,14 @@ __global__ void k_get_pop(const typename Store<ST>::T* __restrict__ f, Geo g, Co
 }
 
 // Where the stored (post-collision) value of direction j at node y comes
-// from: the population j of node y + c_j, or -- if that link crosses a
-// wall -- the population opp(j) of node y itself (inverse of the pull).
+// from: the population j of node y + c_j; if that link crosses a no-slip
+// wall, the population opp(j) of node y itself; if it crosses only a
+// free-slip top, the population mirz(j) of the top-layer node one
+// tangential step along (inverse of the pull).
 __device__ __forceinline__ void push_target(const Geo& g, int j, int x, int y, int z, int& dir,
                                             long long& node) {
     int tx = x + cx(j), ty = y + cy(j), tz = z + cz(j);
-    bool bounce = false;
+    bool bounce = false, specular = false;
     if (cx(j) != 0 && (tx < 0 || tx >= g.nx)) {
         if (g.walls & 0x01) bounce = true;
         else tx = tx < 0 ? tx + g.nx : tx - g.nx;
@@ -1613,12 +1615,16 @@ __device__ __forceinline__ void push_target(const Geo& g, int j, int x, int y, i
         else ty = ty < 0 ? ty + g.ny : ty - g.ny;
     }
     if (cz(j) != 0 && (tz < 0 || tz >= g.nz)) {
-        if (g.walls & 0x10) bounce = true;
+        if (tz >= g.nz && (g.walls & WALL_TOP_FREE)) specular = true;
+        else if (g.walls & 0x10) bounce = true;
         else tz = tz < 0 ? tz + g.nz : tz - g.nz;
     }
     if (bounce) {
         dir = opp(j);
         node = site_index(g, x, y, z);
+    } else if (specular) {
+        dir = mirz(j);
+        node = site_index(g, tx, ty, z);
     } else {
         dir = j;
         node = site_index(g, tx, ty, tz);

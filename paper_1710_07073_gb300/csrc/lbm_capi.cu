@@ -143,11 +143,12 @@ int ensure_device(lbm_ctx* c) {
 namespace {
 
 int check_walls(unsigned walls) {
-    if (walls & ~0x3Fu) return 0;
+    if (walls & ~0x7Fu) return 0;
     for (int a = 0; a < 3; ++a) {
         bool lo = walls & (1u << (2 * a)), hi = walls & (1u << (2 * a + 1));
         if (lo != hi) return 0;
     }
+    if ((walls & WALL_TOP_FREE) && !(walls & 0x20)) return 0;   // a free-slip top bounds z
     return 1;
 }
 

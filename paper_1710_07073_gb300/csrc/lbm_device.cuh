@@ -111,14 +111,16 @@ __device__ __forceinline__ int site_index(const Geo& g, int x, int y, int z) {
 }
 
 // Source of population j arriving at node (x,y,z) under streaming (Eq. 16):
-// the node x - c_j, wrapped on periodic axes.  If the link crosses a wall the
-// population is the opposite one leaving the same node (half-way
-// bounce-back); `plane` and `idx` say where to read it.
+// the node x - c_j, wrapped on periodic axes.  If the link crosses a no-slip
+// wall the population is the opposite one leaving the same node (half-way
+// bounce-back).  If it crosses only a free-slip top (Sec. 3.3), it is the
+// z-mirrored population leaving the top layer one tangential step back
+// (specular reflection).  `plane` and `idx` say where to read it.
 template <int J>
 __device__ __forceinline__ void pull_source(const Geo& g, int x, int y, int z, int& plane,
                                             int& idx) {
     int sx = x - cx(J), sy = y - cy(J), sz = z - cz(J);
-    bool bounce = false;
+    bool bounce = false, specular = false;
     if (cx(J) != 0 && (sx < 0 || sx >= g.nx)) {
         if (g.walls & 0x01) bounce = true;
         else sx = sx < 0 ? sx + g.nx : sx - g.nx;
@@ -128,12 +130,16 @@ __device__ __forceinline__ void pull_source(const Geo& g, int x, int y, int z, i
         else sy = sy < 0 ? sy + g.ny : sy - g.ny;
     }
     if (cz(J) != 0 && (sz < 0 || sz >= g.nz)) {
-        if (g.walls & 0x10) bounce = true;
+        if (sz >= g.nz && (g.walls & WALL_TOP_FREE)) specular = true;
+        else if (g.walls & 0x10) bounce = true;
         else sz = sz < 0 ? sz + g.nz : sz - g.nz;
     }
     if (bounce) {
         plane = opp(J);
         idx = site_index(g, x, y, z);
+    } else if (specular) {
+        plane = mirz(J);
+        idx = site_index(g, sx, sy, z);
     } else {
         plane = J;
         idx = site_index(g, sx, sy, sz);
@@ -147,7 +153,7 @@ __device__ __forceinline__ void pull_source(const Geo& g, int x, int y, int z, i
 template <int J>
 __device__ __forceinline__ unsigned pull_offset(const Geo& g, int x, int y, int z) {
     int sx = x - cx(J), sy = y - cy(J), sz = z - cz(J);
-    bool bounce = false;
+    bool bounce = false, specular = false;
     if (cx(J) != 0) {
         const bool out = (unsigned)sx >= (unsigned)g.nx;
         bounce = bounce || (out && (g.walls & 0x01));
@@ -160,15 +166,18 @@ __device__ __forceinline__ unsigned pull_offset(const Geo& g, int x, int y, int 
     }
     if (cz(J) != 0) {
         const bool out = (unsigned)sz >= (unsigned)g.nz;
-        bounce = bounce || (out && (g.walls & 0x10));
-        sz = out ? (sz < 0 ? sz + g.nz : sz - g.nz) : sz;
+        specular = cz(J) < 0 && out && (g.walls & WALL_TOP_FREE);
+        bounce = bounce || (out && !specular && (g.walls & 0x10));
+        sz = out ? (specular ? z : (sz < 0 ? sz + g.nz : sz - g.nz)) : sz;
     }
     const unsigned S = (unsigned)g.S;
     const unsigned own = (unsigned)site_index(g, x, y, z);
     const unsigned src = (unsigned)site_index(g, sx, sy, sz);
-    // The stored scale of a bounced population is that of its own plane; the
-    // 16-bit formats share w_j between opposite directions, so J's scale holds.
-    return bounce ? (unsigned)opp(J) * S + own : (unsigned)J * S + src;
+    // The stored scale of a bounced or mirrored population is that of its own
+    // plane; the 16-bit formats share w_j between opposite and mirrored
+    // directions, so J's scale holds.
+    return bounce ? (unsigned)opp(J) * S + own
+                  : (specular ? (unsigned)mirz(J) * S + src : (unsigned)J * S + src);
 }
 
 // Stored pre-collision values at one node: the 19 loads, issued together.

@@ -49,6 +49,15 @@ __host__ __device__ __forceinline__ constexpr int cz(int j) {
 __host__ __device__ __forceinline__ constexpr int opp(int j) {
     return j == 0 ? 0 : ((j & 1) ? j + 1 : j - 1);
 }
+// The direction with the same tangential components and c_z reversed
+// (specular reflection at a z face).
+__host__ __device__ __forceinline__ constexpr int mirz(int j) {
+    return j == 5 ? 6 : j == 6 ? 5 : j == 11 ? 13 : j == 13 ? 11 : j == 12 ? 14 : j == 14 ? 12
+         : j == 15 ? 17 : j == 17 ? 15 : j == 16 ? 18 : j == 18 ? 16 : j;
+}
+// walls bit: the +z face (bounded, bit 0x20 set too) is a free-slip plane
+// (specular reflection) instead of a no-slip wall (LBM_TOP_FREE_SLIP).
+constexpr unsigned WALL_TOP_FREE = 0x40;
 // Eq. 8 weights and their reciprocals.
 __host__ __device__ __forceinline__ constexpr float wf(int j) {
     return j == 0 ? (1.0f / 3.0f) : (j <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));

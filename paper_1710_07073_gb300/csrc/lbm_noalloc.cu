@@ -61,9 +61,10 @@ extern "C" int lbm_bin_bubbles_noalloc(int nx, int ny, int nz, unsigned walls, i
                                        int cap_items, int* status, void* stream) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || n < 0 || cap_items < 0) return LBM_ERR_ARG;
     if ((long long)nx * ny * nz * 19 >= (1LL << 32)) return LBM_ERR_ARG;
-    if (walls & ~0x3Fu) return LBM_ERR_ARG;
+    if (walls & ~0x7Fu) return LBM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (!(walls & (1u << (2 * a))) != !(walls & (1u << (2 * a + 1)))) return LBM_ERR_ARG;
+    if ((walls & WALL_TOP_FREE) && !(walls & 0x20u)) return LBM_ERR_ARG;
     Geo g;
     g.nx = nx;
     g.ny = ny;

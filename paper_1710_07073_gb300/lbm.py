@@ -28,6 +28,8 @@ LBM_ERR_STATE = -6
 
 LBM_WALL_XM, LBM_WALL_XP, LBM_WALL_YM, LBM_WALL_YP, LBM_WALL_ZM, LBM_WALL_ZP = (1 << k for k in range(6))
 LBM_WALL_ALL = 0x3F
+LBM_TOP_FREE_SLIP = 0x40
+LBM_WALL_ALL_FREE_TOP = 0x7F
 
 LBM_STORE_F32 = 0
 LBM_STORE_F16 = 1

@@ -62,7 +62,8 @@ def test_host_only_calls_without_gpu(libpath):
 
 @pytest.mark.parametrize("args", [
     (0, 8, 8, 1.6, 0x3F), (8, 8, 8, 0.0, 0x3F), (8, 8, 8, 2.0, 0x3F),
-    (8, 8, 8, 1.6, 0x01), (8, 8, 8, 1.6, 0x40), (2048, 2048, 1024, 1.6, 0x3F)])
+    (8, 8, 8, 1.6, 0x01), (8, 8, 8, 1.6, 0x40), (8, 8, 8, 1.6, 0x0F | 0x40),
+    (8, 8, 8, 1.6, 0x80 | 0x3F), (2048, 2048, 1024, 1.6, 0x3F)])
 def test_create_rejects_bad_arguments(libpath, args):
     from paper_1710_07073_gb300 import lbm
     with pytest.raises(lbm.LbmError) as e:
@@ -89,3 +90,11 @@ def test_bubble_arguments_checked_before_device_use(libpath):
             lbm.lbm_set_bubbles(h, [8, 8, 4], [0, 0, 0], [2.5])
     finally:
         lbm.lbm_destroy(h)
+
+
+@pytest.mark.parametrize("walls", [0x7F, 0x30 | 0x40, 0x33 | 0x40])
+def test_create_accepts_free_slip_top_with_bounded_z(libpath, walls):
+    # The free-slip top (0x40) is valid whenever the z faces are bounded.
+    from paper_1710_07073_gb300 import lbm
+    h = lbm.lbm_create(8, 8, 8, 1.6, walls)
+    lbm.lbm_destroy(h)

@@ -42,7 +42,9 @@ def _random_pops(dims, seed, amp=1e-2):
     return f * (1.0 + 0.1 * amp * rng.standard_normal(f.shape))
 
 
-WALL_CASES = [olat.ALL_WALLS, 0, olat.WALL_ZM | olat.WALL_ZP, olat.WALL_XM | olat.WALL_XP]
+WALL_CASES = [olat.ALL_WALLS, 0, olat.WALL_ZM | olat.WALL_ZP, olat.WALL_XM | olat.WALL_XP,
+              olat.ALL_WALLS | olat.TOP_FREE_SLIP,
+              olat.WALL_ZM | olat.WALL_ZP | olat.TOP_FREE_SLIP]
 
 
 @pytest.mark.parametrize("dims", [(37, 9, 11), (1, 1, 12), (64, 4, 4)])
