@@ -23,6 +23,14 @@ Readings of the paper where it is garbled or silent:
 * A bubble stays inside a wall-bounded axis: its centre is held in
   [r_b, L - r_b] and the velocity component into the wall is zeroed.  On a
   periodic axis the centre wraps.
+* Table 1's lift coefficient prints f(Eo_d) = 0.00105 Eo_d^3 - 0.0159 Eo_d^2
+  - 0.0204 Eo_d without a constant term; the published correlation it cites
+  has + 0.474, restored here (it makes C_L continuous at Eo_d = 4 for large
+  Re and near-continuous at Eo_d = 10, and positive for small bubbles).  The
+  exponent printed as E^{2\3} is 2/3: Eo_d = Eo / E^(2/3), E = 1/(1 + 0.163
+  Eo^0.757).  Lift and the stress-gradient force are off unless asked for.
+* The stress-gradient force F_S = rho_l V_b D_t u_l uses the same D_t u_l as
+  the virtual-mass force.
 """
 import math
 
@@ -36,7 +44,7 @@ class BubbleParams:
 
     def __init__(self, omega, g=1e-5, rho_l=1.0, rho_ratio=1e-3, sigma=5.84e-6,
                  c_added_mass=0.5, drag_scale=1.0, sn_coeff=0.15, sn_exp=0.687,
-                 width_factor=1.5, substeps=10, dt_l=1.0):
+                 width_factor=1.5, substeps=10, dt_l=1.0, lift=False, stress_gradient=False):
         self.omega = omega
         self.nu = viscosity(omega)
         self.g = g
@@ -51,6 +59,8 @@ class BubbleParams:
         self.substeps = substeps
         self.dt_l = dt_l
         self.dt_b = dt_l / substeps   # Table 2: dt_b = dt_l / 10
+        self.lift = lift                          # F_L of Table 1
+        self.stress_gradient = stress_gradient    # F_S of Table 1
 
 
 def volume(d):
@@ -95,18 +105,50 @@ def buoyancy_force(d, p):
     return np.array([0.0, 0.0, (p.rho_l - p.rho_b) * volume(d) * p.g])
 
 
+def lift_f(eo_d):
+    """Table 1's f(Eo_d), with the published constant 0.474 restored."""
+    return 0.00105 * eo_d ** 3 - 0.0159 * eo_d ** 2 - 0.0204 * eo_d + 0.474
+
+
+def eotvos_deformed(eo):
+    """Table 1: Eo_d = Eo / E^(2/3), E = 1 / (1 + 0.163 Eo^0.757)."""
+    e = 1.0 / (1.0 + 0.163 * eo ** 0.757)
+    return eo / e ** (2.0 / 3.0)
+
+
+def lift_coefficient(re, eo):
+    """Table 1: C_L = min[0.288 tanh(0.121 Re), f(Eo_d)] for Eo_d < 4,
+    f(Eo_d) for 4 <= Eo_d <= 10, -0.29 above."""
+    eo_d = eotvos_deformed(eo)
+    if eo_d < 4.0:
+        return min(0.288 * math.tanh(0.121 * re), lift_f(eo_d))
+    if eo_d <= 10.0:
+        return lift_f(eo_d)
+    return -0.29
+
+
+def lift_force(vrel, omega_l, d, p):
+    """Table 1: F_L = -C_L rho_l V_b (u_b - u_l) x (curl u_l)."""
+    vrel = np.asarray(vrel, dtype=np.float64)
+    re = reynolds(vrel, d, p)
+    cl = lift_coefficient(re, eotvos(d, p))
+    return -cl * p.rho_l * volume(d) * np.cross(vrel, np.asarray(omega_l, dtype=np.float64))
+
+
 def effective_mass(d, p):
     """m_b + C_A rho_l V_b: bubble mass plus the added mass moved to the left of Eq. 4."""
     return (p.rho_b + p.c_added_mass * p.rho_l) * volume(d)
 
 
-def advance(x, u, d, ul, dul, dims, walls, p):
+def advance(x, u, d, ul, dul, dims, walls, p, omega_l=None):
     """Algorithm 1 steps 4-6 for one bubble over one liquid step.
 
     x, u: position and velocity at the start of the liquid step; ul: liquid
-    velocity interpolated at x (Eq. 20); dul: D_t u_l.  Runs ``p.substeps``
-    explicit updates of Eq. 4 with dt_b, each followed by the position step.
-    Returns (x_new, u_new, psi) with psi = -(mean F_D) the reaction (step 6).
+    velocity interpolated at x (Eq. 20); dul: D_t u_l; omega_l: the liquid
+    vorticity interpolated at x (Eq. 20; needed with lift on).  Runs
+    ``p.substeps`` explicit updates of Eq. 4 with dt_b, each followed by the
+    position step.  Returns (x_new, u_new, psi) with psi = -(mean of F_D + F_L)
+    the reaction (step 6).
     """
     x = np.array(x, dtype=np.float64)
     u = np.array(u, dtype=np.float64)
@@ -114,12 +156,16 @@ def advance(x, u, d, ul, dul, dims, walls, p):
     r = 0.5 * d
     meff = effective_mass(d, p)
     fb = buoyancy_force(d, p)
-    fvm_liquid = p.c_added_mass * p.rho_l * volume(d) * np.asarray(dul, dtype=np.float64)
+    dul = np.asarray(dul, dtype=np.float64)
+    fvm_liquid = p.c_added_mass * p.rho_l * volume(d) * dul
+    fs = p.rho_l * volume(d) * dul if p.stress_gradient else np.zeros(3)   # F_S
     fd_sum = np.zeros(3)
     for _ in range(p.substeps):
         fd = drag_force(u - ul, d, p)
+        if p.lift:
+            fd = fd + lift_force(u - ul, omega_l, d, p)      # F_D + F_L
         fd_sum += fd
-        u = u + (fb + fd + fvm_liquid) / meff * p.dt_b      # Eq. 4 with m_eff
+        u = u + (fb + fd + fvm_liquid + fs) / meff * p.dt_b   # Eq. 4 with m_eff
         x = x + u * p.dt_b                                  # S = u^{k+1} dt_b
         for a in range(3):
             length = dims[a]

@@ -196,3 +196,37 @@ def _check_walls(walls):
 def lb_step(f, omega, walls, force=None):
     """Collide (Eq. 13-15) then stream (Eq. 16) once."""
     return stream(collide(f, omega, force), walls)
+
+
+def vorticity(u, walls):
+    """curl u at the nodes by central differences, [3, nz, ny, nx].
+
+    The paper interpolates the liquid vorticity to the bubble (Sec. 3.2,
+    Algorithm 1 step 3) without saying how it is formed; it is read as the
+    central difference (u(i+1) - u(i-1)) / 2 of the bare Eq. 10 velocity.  A
+    neighbour beyond a face is a ghost node: periodic faces wrap; the no-slip
+    wall half-way beyond the boundary node gives the ghost -u (velocity zero
+    at the wall); the free-slip top gives the tangential components +u (zero
+    shear at the plane).  Only tangential components are differentiated
+    across a face in the curl.
+    """
+    u = np.asarray(u, dtype=np.float64)
+    free_top = bool(walls & TOP_FREE_SLIP)
+
+    def diff(comp, d):
+        # d/dx_d of u[comp]; array axis of x_d is 2 - d
+        f = u[comp]
+        ax = 2 - d
+        if not (walls & (1 << (2 * d))):
+            return 0.5 * (np.roll(f, -1, axis=ax) - np.roll(f, 1, axis=ax))
+        lo = np.take(f, [0], axis=ax)
+        hi = np.take(f, [f.shape[ax] - 1], axis=ax)
+        s_hi = 1.0 if (d == 2 and free_top) else -1.0
+        padded = np.concatenate([-lo, f, s_hi * hi], axis=ax)
+        n = f.shape[ax]
+        return 0.5 * (np.take(padded, np.arange(2, n + 2), axis=ax)
+                      - np.take(padded, np.arange(0, n), axis=ax))
+
+    return np.stack([diff(2, 1) - diff(1, 2),     # d u_z/dy - d u_y/dz
+                     diff(0, 2) - diff(2, 0),     # d u_x/dz - d u_z/dx
+                     diff(1, 0) - diff(0, 1)])    # d u_y/dx - d u_x/dy

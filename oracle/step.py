@@ -4,7 +4,8 @@ One call of ``OracleSim.step`` is one pass of Algorithm 1's loop body:
 
   step 2   locate the active bubbles (the binning itself is in ``binning``);
   step 3   forward coupling: the bare Eq. 10 velocity of the current
-           populations, interpolated to each bubble centre (Eq. 19-20);
+           populations, interpolated to each bubble centre (Eq. 19-20), and
+           with lift on its vorticity (central differences, the same map);
   step 4-5 forces (Table 1) and the explicit Newton update with sub-steps
            (Eq. 4, Table 2);
   step 6   backward coupling: psi_b = -F_D spread with Eq. 21 at the updated
@@ -66,14 +67,17 @@ class OracleSim:
         if nb and self.active.any():
             rho = lat.density(self.f)
             u_nodes = lat.momentum(self.f) / rho                 # Eq. 10, bare moment
+            w_nodes = lat.vorticity(u_nodes, self.walls) if p.lift else None
             xs_new, psis, ns = [], [], []
             for b in range(nb):
                 if not self.active[b]:
                     continue
                 ul = mapping.interpolate(u_nodes, self.x[b], self.n[b], self.walls)   # Eq. 20
+                wl = (mapping.interpolate(w_nodes, self.x[b], self.n[b], self.walls)
+                      if p.lift else None)
                 dul = (ul - self.ul_prev[b]) / p.dt_l if self.has_prev[b] else np.zeros(3)
                 x_new, u_new, psi = bub.advance(self.x[b], self.u[b], self.d[b], ul, dul,
-                                                self.dims, self.walls, p)
+                                                self.dims, self.walls, p, omega_l=wl)
                 self.ul[b] = ul
                 self.ul_prev[b] = ul
                 self.has_prev[b] = True

@@ -160,3 +160,90 @@ def test_added_mass_liquid_acceleration_closed_form():
         start = [vinf * (1.0 - q ** i) for i in range(k0, k)]   # velocity at each sub-step's start
         psi_exp = kdrag / p.substeps * sum(s - ul for s in start)
         np.testing.assert_allclose(psi, psi_exp, rtol=1e-10, atol=0)
+
+
+# ---- lift and stress-gradient forces (Table 1) --------------------------------
+
+def test_deformed_eotvos_number():
+    # Eo_d = Eo / E^(2/3), E = 1 / (1 + 0.163 Eo^0.757): E -> 1 for a small
+    # bubble; Eo = 1 by hand: E = 1/1.163, Eo_d = 1.163^(2/3).
+    assert bub.eotvos_deformed(1e-12) == pytest.approx(1e-12, rel=1e-6)
+    assert bub.eotvos_deformed(1.0) == pytest.approx(1.163 ** (2.0 / 3.0), rel=1e-14)
+
+
+def test_lift_coefficient_branches_join():
+    # With the published constant 0.474 in f(Eo_d), the three branches of
+    # Table 1 join: at Eo_d = 4 the min() branch equals f (large Re), and at
+    # Eo_d = 10 f(10) = -0.27 meets the -0.29 plateau within 0.02.  Small,
+    # nearly round bubbles take the tanh branch: C_L -> 0.288 at large Re,
+    # 0.288 * 0.121 Re at small Re.  As printed (no constant) f(10) = -0.744:
+    # a jump of 0.45 to -0.29.
+    f4, f10 = bub.lift_f(4.0), bub.lift_f(10.0)
+    assert f4 == pytest.approx(0.2052, abs=1e-4)
+    assert f10 == pytest.approx(-0.270, abs=1e-3)
+    assert abs(f10 - (-0.29)) < 0.025
+    printed = lambda e: 0.00105 * e ** 3 - 0.0159 * e ** 2 - 0.0204 * e
+    assert abs(printed(10.0) - (-0.29)) > 0.4
+    # Eo chosen so that Eo_d sits just below / above 4 and 10.
+    def eo_for(eo_d):
+        lo, hi = 1e-9, 1e3
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            lo, hi = (mid, hi) if bub.eotvos_deformed(mid) < eo_d else (lo, mid)
+        return 0.5 * (lo + hi)
+    assert bub.lift_coefficient(1e4, eo_for(4.0 - 1e-9)) == pytest.approx(f4, abs=1e-6)
+    assert bub.lift_coefficient(1e4, eo_for(4.0 + 1e-9)) == pytest.approx(f4, abs=1e-6)
+    assert bub.lift_coefficient(1e4, eo_for(10.0 + 1e-6)) == -0.29
+    assert bub.lift_coefficient(1e4, 1e-6) == pytest.approx(0.288, rel=1e-12)
+    assert bub.lift_coefficient(1e-3, 1e-6) == pytest.approx(0.288 * 0.121e-3, rel=1e-6)
+
+
+def test_lift_rotates_the_slip_velocity():
+    # Lift without drag in a uniform vorticity Omega z: with the horizontal
+    # slip w = u_b - u_l = (w_x, w_y) as z = w_x + i w_y, F_L = -C_L rho_l V_b
+    # (w x Omega z) = i C_L rho_l V_b Omega z, so each explicit sub-step of
+    # Eq. 4 multiplies z by (1 + i c), c = C_L rho_l V_b Omega dt_b / m_eff,
+    # while buoyancy alone accelerates u_z.  A large Eo puts C_L on its -0.29
+    # plateau.  This fixes the order of the cross product, the sign and the
+    # coefficient of Table 1's lift.
+    p = bub.BubbleParams(1.6, sigma=1e-9, drag_scale=0.0, lift=True)
+    d = 2.0
+    omega_l = np.array([0.0, 0.0, 3e-3])
+    assert bub.lift_coefficient(1.0, bub.eotvos(d, p)) == -0.29
+    c = -0.29 * p.rho_l * bub.volume(d) * omega_l[2] * p.dt_b / bub.effective_mass(d, p)
+    x, u = np.array([32.0, 32.0, 32.0]), np.array([1e-3, 0.0, 0.0])
+    z = complex(u[0], u[1])
+    xs = x.copy()
+    for step in range(1, 6):
+        zs = [z * (1 + 1j * c) ** k for k in range(p.substeps + 1)]
+        x, u, psi = bub.advance(x, u, d, np.zeros(3), np.zeros(3), (64, 64, 64),
+                                lat.ALL_WALLS, p, omega_l=omega_l)
+        assert complex(u[0], u[1]) == pytest.approx(zs[-1], rel=1e-12)
+        kb = bub.buoyancy_force(d, p)[2] * p.dt_b / bub.effective_mass(d, p)
+        assert u[2] == pytest.approx(kb * step * p.substeps, rel=1e-12)
+        xs[:2] = xs[:2] + p.dt_b * np.array([sum(zz.real for zz in zs[1:]),
+                                            sum(zz.imag for zz in zs[1:])])
+        np.testing.assert_allclose(x[:2], xs[:2], rtol=1e-15, atol=0)
+        # Reaction: minus the mean lift over the sub-steps.
+        fl = [1j * -0.29 * p.rho_l * bub.volume(d) * omega_l[2] * zz for zz in zs[:-1]]
+        mean = sum(fl) / p.substeps
+        assert complex(psi[0], psi[1]) == pytest.approx(-mean, rel=1e-12)
+        z = zs[-1]
+
+
+def test_stress_gradient_adds_rho_l_v_b_dtul():
+    # Table 1: F_S = rho_l V_b D_t u_l, on top of the virtual mass's
+    # C_A rho_l V_b D_t u_l: with Stokes drag the update tends to
+    # u_l + (F_B + (1 + C_A) rho_l V_b D_t u_l) / K.
+    p = bub.BubbleParams(1.7, sn_coeff=0.0, sigma=1e30, stress_gradient=True)
+    d = 1.8
+    ul = np.array([1e-4, -2e-4, 3e-4])
+    dul = np.array([2e-6, 1e-6, -3e-6])
+    kdrag = 3.0 * math.pi * p.rho_l * p.nu * d
+    force = bub.buoyancy_force(d, p) + (1.0 + p.c_added_mass) * p.rho_l * bub.volume(d) * dul
+    vinf = ul + force / kdrag
+    q = 1.0 - kdrag * p.dt_b / bub.effective_mass(d, p)
+    x, u = np.array([32.0, 32.0, 20.0]), np.zeros(3)
+    for step in range(1, 6):
+        x, u, _ = bub.advance(x, u, d, ul, dul, (64, 64, 64), lat.ALL_WALLS, p)
+        np.testing.assert_allclose(u, vinf * (1.0 - q ** (step * p.substeps)), rtol=1e-11, atol=0)

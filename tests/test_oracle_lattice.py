@@ -271,3 +271,53 @@ def test_free_slip_top_half_poiseuille_exact():
     z = np.arange(H) + 0.5
     exact = gx / (2.0 * lat.viscosity(omega)) * z * (2.0 * H - z)
     assert np.abs(u - exact).max() / exact.max() < 1e-9
+
+
+# ---- vorticity at the nodes (lift) ----------------------------------------------
+
+def test_vorticity_exact_for_quadratic_fields():
+    # Central differences are exact for polynomials of degree two: away from
+    # the faces the node curl equals the analytic curl of
+    # u = (a y^2 + b z, c x z, e x y + h x^2).
+    nx, ny, nz = 7, 8, 9
+    zz, yy, xx = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5,
+                             indexing="ij")
+    a, b, c, e, h = 0.3, -0.7, 1.1, 0.4, -0.2
+    u = np.stack([a * yy ** 2 + b * zz, c * xx * zz, e * xx * yy + h * xx ** 2])
+    w = lat.vorticity(u, lat.ALL_WALLS)
+    exact = np.stack([e * xx - c * xx,            # d(u_z)/dy - d(u_y)/dz
+                      b - (e * yy + 2 * h * xx),  # d(u_x)/dz - d(u_z)/dx
+                      c * zz - 2 * a * yy])       # d(u_y)/dx - d(u_x)/dy
+    inner = (slice(None), slice(1, -1), slice(1, -1), slice(1, -1))
+    assert np.abs(w[inner] - exact[inner]).max() < 1e-12
+
+
+def test_vorticity_ghost_nodes_at_faces():
+    # A single u_x = 1 on the bottom layer: the no-slip ghost below is -1, so
+    # d(u_x)/dz there is (0 - (-1))/2 = 1/2; one layer up it is (0 - 1)/2.
+    # Under a free-slip top the tangential ghost is +u: a u_x = 1 on the top
+    # layer gives d(u_x)/dz = (1 - 0)/2 there.  Periodic axes wrap.
+    nx, ny, nz = 4, 5, 6
+    u = np.zeros((3, nz, ny, nx))
+    u[0, 0, 2, 1] = 1.0
+    w = lat.vorticity(u, lat.ALL_WALLS)
+    assert w[1, 0, 2, 1] == 0.5 and w[1, 1, 2, 1] == -0.5
+    u = np.zeros((3, nz, ny, nx))
+    u[0, nz - 1, 2, 1] = 1.0
+    w = lat.vorticity(u, lat.ALL_WALLS | lat.TOP_FREE_SLIP)
+    assert w[1, nz - 1, 2, 1] == 0.5 and w[1, nz - 2, 2, 1] == 0.5
+    w = lat.vorticity(u, lat.ALL_WALLS)
+    assert w[1, nz - 1, 2, 1] == -0.5
+    w = lat.vorticity(u, lat.WALL_XM | lat.WALL_XP | lat.WALL_YM | lat.WALL_YP)
+    assert w[1, 0, 2, 1] == -0.5 and w[1, nz - 2, 2, 1] == 0.5
+
+
+def test_vorticity_of_a_gradient_field_vanishes():
+    # Central differences along different axes commute, so the node curl of
+    # a discrete gradient field vanishes on a periodic box.
+    rng = np.random.default_rng(9)
+    phi = rng.standard_normal((6, 5, 7))
+    grad = np.stack([0.5 * (np.roll(phi, -1, 2) - np.roll(phi, 1, 2)),
+                     0.5 * (np.roll(phi, -1, 1) - np.roll(phi, 1, 1)),
+                     0.5 * (np.roll(phi, -1, 0) - np.roll(phi, 1, 0))])
+    assert np.abs(lat.vorticity(grad, 0)).max() < 1e-14
