@@ -102,14 +102,32 @@ typedef struct lbm_params {
     double width_factor;  /* mapping half-width n = width_factor * d_b (1.5)*/
     int    substeps;      /* bubble sub-steps per liquid step (Table 2: 10) */
     int    two_way;       /* 1: spread the reaction onto the liquid (Eq. 21)*/
+    int    forces;        /* LBM_FORCE_* bits: the Table 1 forces beyond    */
+                          /* buoyancy, drag and virtual mass (0: none)      */
 } lbm_params;
+
+/* Optional interface forces of Table 1 (lbm_params.forces):
+ *   LBM_FORCE_LIFT    F_L = -C_L rho_l V_b (u_b - u_l) x (curl u_l) with
+ *                     Table 1's C_L(Re, Eo_d) (f(Eo_d) carries the published
+ *                     constant 0.474 that the printed table drops); the
+ *                     liquid vorticity is the central difference of the
+ *                     Eq. 10 velocity at the nodes (ghost -u beyond a no-slip
+ *                     wall, +u tangential beyond a free-slip top), interpolated
+ *                     with Eq. 19-20 like the velocity (Algorithm 1 step 3).
+ *                     The reaction is -(F_D + F_L) (Algorithm 1 step 6).  The
+ *                     windows reach one cell further, so on a periodic axis
+ *                     2n + 4 <= L.
+ *   LBM_FORCE_STRESS  F_S = rho_l V_b D_t u_l, with the virtual mass's
+ *                     D_t u_l. */
+#define LBM_FORCE_LIFT   0x1
+#define LBM_FORCE_STRESS 0x2
 
 typedef void* (*lbm_alloc_fn)(size_t bytes, void* user);
 typedef void  (*lbm_free_fn)(void* ptr, size_t bytes, void* user);
 
 /* Fill *p with the defaults: g=1e-5, rho_l=1, rho_ratio=1e-3,
  * sigma=5.84e-6, C_A=0.5, drag_scale=1, sn_coeff=0.15, sn_exp=0.687,
- * width_factor=1.5, substeps=10, two_way=1. */
+ * width_factor=1.5, substeps=10, two_way=1, forces=0. */
 void lbm_default_params(lbm_params* p);
 
 /* Velocity set and weights in the library's direction order (Eq. 7-8):
@@ -237,7 +255,8 @@ int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
  * backward the context is back at the state the forward ended in.  Any call
  * that changes the state between the two (lbm_step, lbm_set_*) discards the
  * record; lbm_adj_backward then returns LBM_ERR_STATE.  A free-slip top
- * (LBM_TOP_FREE_SLIP) is not covered: lbm_adj_forward returns LBM_ERR_STATE.
+ * (LBM_TOP_FREE_SLIP) and the optional forces (lbm_params.forces) are not
+ * covered: lbm_adj_forward returns LBM_ERR_STATE.
  * Memory: one state per
  * checkpoint plus checkpoint_every states during the backward.  With kernel
  * timing on (lbm_set_kernel_timing), lbm_adj_backward times each launch of

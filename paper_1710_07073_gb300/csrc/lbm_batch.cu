@@ -133,6 +133,8 @@ BubbleConst batch_bubble_const(const lbm_batch* b) {
     bc.dt_b = 1.0 / b->p.substeps;
     split_f2(bc.dt_b, bc.dt_bh, bc.dt_bl);
     bc.substeps = b->p.substeps;
+    bc.lift = (b->p.forces & LBM_FORCE_LIFT) ? 1 : 0;
+    bc.stress = (b->p.forces & LBM_FORCE_STRESS) ? 1 : 0;
     return bc;
 }
 
@@ -450,8 +452,11 @@ int lbm_batch_set_params(lbm_batch* b, const lbm_params* p) {
     if (!(p->g >= 0.0) || !(p->rho_l > 0.0) || !(p->rho_ratio >= 0.0 && p->rho_ratio < 1.0) ||
         !(p->sigma > 0.0) || !(p->c_added_mass >= 0.0) || !(p->drag_scale >= 0.0) ||
         !(p->sn_coeff >= 0.0) || !(p->sn_exp > 0.0) || !(p->width_factor > 0.0) ||
-        p->substeps < 1 || p->substeps > 10000 || p->rho_ratio + p->c_added_mass <= 0.0)
+        p->substeps < 1 || p->substeps > 10000 || p->rho_ratio + p->c_added_mass <= 0.0 ||
+        (p->forces & ~(LBM_FORCE_LIFT | LBM_FORCE_STRESS)))
         return bfail(b, LBM_ERR_ARG, "parameter out of range");
+    if (b->bub.nb > 0 && ((p->forces ^ b->p.forces) & LBM_FORCE_LIFT))
+        return bfail(b, LBM_ERR_STATE, "switch lift before lbm_batch_set_bubbles");
     if (b->bub.nb > 0 && p->width_factor != b->p.width_factor)
         return bfail(b, LBM_ERR_STATE, "set width_factor before lbm_batch_set_bubbles");
     if (b->dev_ready && p->rho_l != b->p.rho_l)
@@ -490,7 +495,8 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
                 if (!(x >= 0.0 && x < (double)L[a]))
                     return bfail(b, LBM_ERR_ARG, "bubble %d: centre outside its column", k);
                 const bool periodic = !(b->walls[c] & (1u << (2 * a)));
-                if (periodic && 2.0 * hw + 2.0 > (double)L[a])
+                const double halo = (b->p.forces & LBM_FORCE_LIFT) ? 2.0 : 0.0;
+                if (periodic && 2.0 * hw + 2.0 + halo > (double)L[a])
                     return bfail(b, LBM_ERR_ARG, "bubble %d: window wraps onto itself", k);
                 if (!periodic && d >= (double)L[a])
                     return bfail(b, LBM_ERR_ARG, "bubble %d: wider than its column", k);
@@ -498,8 +504,9 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
         }
     }
     const double hwmax = b->p.width_factor * dmax;
-    const long long per = (long long)axis_tile_bound(hwmax, TX) * axis_tile_bound(hwmax, TY) *
-                          axis_tile_bound(hwmax, TZ);
+    const int pad = (b->p.forces & LBM_FORCE_LIFT) ? 1 : 0;   // the lift's vorticity halo
+    const long long per = (long long)axis_tile_bound(hwmax + pad, TX) *
+                          axis_tile_bound(hwmax + pad, TY) * axis_tile_bound(hwmax + pad, TZ);
     if (per * n > SMALL_MAX_PAIRS)
         return bfail(b, LBM_ERR_ARG, "a batch bins at most %d (tile, bubble) pairs; %lld needed",
                      SMALL_MAX_PAIRS, per * n);
@@ -532,8 +539,8 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
     B.cell = (int*)balloc(b, i1);
     B.rec = (BubbleRec*)balloc(b, sizeof(BubbleRec) * (size_t)n);
     b->bubble_col_d = (int*)balloc(b, i1);
-    sb.parts = window_parts(hwmax);
-    sb.part = (float*)balloc(b, sizeof(float) * 3 * WINDOW_CHUNKS_MAX * (size_t)n);
+    sb.parts = window_parts(hwmax, pad);
+    sb.part = (float*)balloc(b, sizeof(float) * WIN_VALS_LIFT * WINDOW_CHUNKS_MAX * (size_t)n);
     sb.arrive = (int*)balloc(b, i1);
     if (!B.k || !B.xh || !B.xl || !B.u || !B.d || !B.n || !B.ulprev || !B.ul || !B.psi || !B.out64 ||
         !B.has_prev || !B.active || !B.spread || !B.cell || !B.rec || !b->bubble_col_d ||

@@ -185,7 +185,9 @@ __device__ __forceinline__ void support_cells(F2 x, float nh, float nl, int& lo,
     hi = f2_ceil_int(f2_add(x, nh, nl)) - 1;
 }
 
-__device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w) {
+// pad: cells added beyond the support on each side (the vorticity halo of
+// lift), clipped to the box on wall axes.
+__device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w, int pad = 0) {
     const F2* xb = in.x;
     const float inv_n = in.k.inv_nf;
     if (!in.active) return BUBBLE_IDLE;
@@ -197,6 +199,8 @@ __device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w) {
         const bool periodic = !(g.walls & (1u << (2 * a)));
         int l, h;
         support_cells(xb[a], in.k.nh, in.k.nl, l, h);
+        l -= pad;
+        h += pad;
         if (!periodic) {
             l = max(l, 0);
             h = min(h, L[a] - 1);
@@ -239,18 +243,68 @@ __device__ __forceinline__ float window_node(const Geo& g, const Window& w, floa
            cell_poly(((float)(k - w.anc[2]) + 0.5f - w.fr[2]) * inv_n, hh);
 }
 
+// Lift: the four weights of window node m -- W = wx wy wz (Eq. 19) and the
+// difference weights Gx = dx wy wz, Gy = wx dy wz, Gz = wx wy dz (axis_wd) --
+// and its wrapped lattice coordinates.
+__device__ __forceinline__ void window_node_lift(const Geo& g, const Window& w, float inv_n,
+                                                 int m, int& iw, int& jw, int& kw, float wt[4]) {
+    const float hh = 0.5f * inv_n;
+    const int rest = div_small(m, w.cnt[0]);
+    const int ix = m - rest * w.cnt[0];
+    const int iz = div_small(rest, w.cnt[1]);
+    const int iy = rest - iz * w.cnt[1];
+    const int c[3] = {w.lo[0] + ix, w.lo[1] + iy, w.lo[2] + iz};
+    const int L[3] = {g.nx, g.ny, g.nz};
+    float ww[3], dd[3];
+    for (int a = 0; a < 3; ++a)
+        axis_wd(c[a], w.anc[a], w.fr[a], inv_n, hh, L[a], !(g.walls & (1u << (2 * a))),
+                a == 2 && (g.walls & WALL_TOP_FREE), ww[a], dd[a]);
+    iw = wrap_axis(c[0], g.nx);
+    jw = wrap_axis(c[1], g.ny);
+    kw = wrap_axis(c[2], g.nz);
+    wt[0] = ww[0] * ww[1] * ww[2];
+    wt[1] = dd[0] * ww[1] * ww[2];
+    wt[2] = ww[0] * dd[1] * ww[2];
+    wt[3] = ww[0] * ww[1] * dd[2];
+}
+
+// Adds node velocity u with weights wt (LIFT) or weight wt[0] into acc:
+// acc[0..2] the Eq. 20 velocity sums; with lift acc[3..8] = Gx u_y, Gx u_z,
+// Gy u_x, Gy u_z, Gz u_x, Gz u_y (the interpolated central differences
+// d(u_y)/dx, d(u_z)/dx, d(u_x)/dy, d(u_z)/dy, d(u_x)/dz, d(u_y)/dz).
+template <bool LIFT>
+__device__ __forceinline__ void add_window_node(const float wt[4], const float u[3], float* acc) {
+    acc[0] = fmaf(wt[0], u[0], acc[0]);
+    acc[1] = fmaf(wt[0], u[1], acc[1]);
+    acc[2] = fmaf(wt[0], u[2], acc[2]);
+    if (LIFT) {
+        acc[3] = fmaf(wt[1], u[1], acc[3]);
+        acc[4] = fmaf(wt[1], u[2], acc[4]);
+        acc[5] = fmaf(wt[2], u[0], acc[5]);
+        acc[6] = fmaf(wt[2], u[2], acc[6]);
+        acc[7] = fmaf(wt[3], u[0], acc[7]);
+        acc[8] = fmaf(wt[3], u[1], acc[8]);
+    }
+}
+
 // Eq. 20 partial sums of one chunk: nodes m0 + tid and m0 + tid + nt (below
 // m1), both gathered before either is used so their loads overlap.
-template <int ST>
+template <int ST, bool LIFT>
 __device__ __forceinline__ void chunk_sum2(const typename Store<ST>::T* __restrict__ f,
                                            const Geo& g, const CollideParams& cp, const Window& w,
-                                           float inv_n, int m0, int m1, int tid, int nt, float& ax,
-                                           float& ay, float& az) {
+                                           float inv_n, int m0, int m1, int tid, int nt,
+                                           float* acc) {
     const int ma = m0 + tid, mb = ma + nt;
     const bool ha = ma < m1, hb = mb < m1;
     int ia, ja, ka, ib, jb, kb;
-    const float wa = window_node(g, w, inv_n, ha ? ma : m0, ia, ja, ka);
-    const float wb = window_node(g, w, inv_n, hb ? mb : m0, ib, jb, kb);
+    float wa[4], wb[4];
+    if (LIFT) {
+        window_node_lift(g, w, inv_n, ha ? ma : m0, ia, ja, ka, wa);
+        window_node_lift(g, w, inv_n, hb ? mb : m0, ib, jb, kb, wb);
+    } else {
+        wa[0] = window_node(g, w, inv_n, ha ? ma : m0, ia, ja, ka);
+        wb[0] = window_node(g, w, inv_n, hb ? mb : m0, ib, jb, kb);
+    }
     typename Store<ST>::T ra[Q], rb[Q];
     gather_issue<ST>(f, g, ia, ja, ka, ra);
     gather_issue<ST>(f, g, ib, jb, kb, rb);
@@ -260,16 +314,8 @@ __device__ __forceinline__ void chunk_sum2(const typename Store<ST>::T* __restri
     float ua[3], ub[3];
     node_velocity(ga, cp, ua);
     node_velocity(gb, cp, ub);
-    if (ha) {
-        ax = fmaf(wa, ua[0], ax);
-        ay = fmaf(wa, ua[1], ay);
-        az = fmaf(wa, ua[2], az);
-    }
-    if (hb) {
-        ax = fmaf(wb, ub[0], ax);
-        ay = fmaf(wb, ub[1], ay);
-        az = fmaf(wb, ub[2], az);
-    }
+    if (ha) add_window_node<LIFT>(wa, ua, acc);
+    if (hb) add_window_node<LIFT>(wb, ub, acc);
 }
 
 __device__ __forceinline__ void warp_sum3(float& ax, float& ay, float& az) {
@@ -281,24 +327,24 @@ __device__ __forceinline__ void warp_sum3(float& ax, float& ay, float& az) {
     }
 }
 
-// Sum of (ax, ay, az) over the CTA's BUBBLE_THREADS threads, in thread 0
-// (fixed order: warp shuffles, then warps in order).
-__device__ __forceinline__ void block_sum3(float& ax, float& ay, float& az,
-                                           float (*red)[BUBBLE_THREADS / 32]) {
-    warp_sum3(ax, ay, az);
+// Sum of v[0..N) over the CTA's BUBBLE_THREADS threads, in thread 0 (fixed
+// order: warp shuffles, then warps in order).
+template <int N>
+__device__ __forceinline__ void block_sum_n(float* v, float (*red)[BUBBLE_THREADS / 32]) {
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     const int tid = threadIdx.x;
-    if ((tid & 31) == 0) {
-        red[0][tid >> 5] = ax;
-        red[1][tid >> 5] = ay;
-        red[2][tid >> 5] = az;
-    }
+    if ((tid & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < N; ++q) red[q][tid >> 5] = v[q];
     __syncthreads();
     if (tid == 0) {
-        ax = ay = az = 0.0f;
-        for (int k = 0; k < BUBBLE_THREADS / 32; ++k) {
-            ax += red[0][k];
-            ay += red[1][k];
-            az += red[2][k];
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            v[q] = 0.0f;
+            for (int k = 0; k < BUBBLE_THREADS / 32; ++k) v[q] += red[q][k];
         }
     }
 }
@@ -308,9 +354,11 @@ __device__ __forceinline__ void block_sum3(float& ax, float& ay, float& az,
 // flags the instability; a live one takes the Table 1 forces and the Newton
 // update of Eq. 4 with the added mass on the left (m_eff), sub-stepped with
 // dt_b (Table 2), then its reaction psi (Algorithm 1) and spreading record.
+// acc: the window sums, acc[0..2] the Eq. 20 velocity and, with lift,
+// acc[3..8] the vorticity sums (add_window_node).
 __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst& bc,
-                            int* __restrict__ flag, int b, int state, const Window& w, float ax,
-                            float ay, float az, const BubbleIn& in) {
+                            int* __restrict__ flag, int b, int state, const Window& w,
+                            const float* acc, const BubbleIn& in) {
     if (state != BUBBLE_LIVE) {
         if (state == BUBBLE_NONFINITE) {
             B.active[b] = 0;
@@ -324,10 +372,20 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
     F2 xb[3] = {in.x[0], in.x[1], in.x[2]};
     const BubbleK& K = in.k;
     const float inv_norm = 1.0f / w.norm;
-    const float ul[3] = {ax * inv_norm, ay * inv_norm, az * inv_norm};
-    float fvm[3] = {0.0f, 0.0f, 0.0f};   // C_A rho_l V_b D_t u_l
+    const float ul[3] = {acc[0] * inv_norm, acc[1] * inv_norm, acc[2] * inv_norm};
+    // Interpolated vorticity (lift): curl from the difference sums.
+    float om[3] = {0.0f, 0.0f, 0.0f};
+    if (bc.lift) {
+        om[0] = (acc[6] - acc[8]) * inv_norm;   // d(u_z)/dy - d(u_y)/dz
+        om[1] = (acc[7] - acc[4]) * inv_norm;   // d(u_x)/dz - d(u_z)/dx
+        om[2] = (acc[3] - acc[5]) * inv_norm;   // d(u_y)/dx - d(u_x)/dy
+    }
+    // C_A rho_l V_b D_t u_l (virtual mass, liquid part) plus, with the
+    // stress-gradient force, rho_l V_b D_t u_l (F_S).
+    float fvm[3] = {0.0f, 0.0f, 0.0f};
     if (in.has_prev) {
-        for (int a = 0; a < 3; ++a) fvm[a] = K.fvm_coef_dt * (ul[a] - in.ulprev[a]);
+        for (int a = 0; a < 3; ++a)
+            fvm[a] = (K.fvm_coef_dt + K.fs_coef_dt) * (ul[a] - in.ulprev[a]);
     }
     const F2 dt_b{bc.dt_bh, bc.dt_bl};
     const F2 r{K.rh, K.rl};
@@ -345,7 +403,16 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
         const float visc_a = K.visc_a0 * (1.0f + sn_coeff * __powf(re, sn_exp));
         const float cdv = fmaxf(fminf(visc_a, K.visc_b), K.eo_term * speed);   // C_D |v|
         const float kd = -K.drag_pref * cdv;
-        const float fd[3] = {kd * v0, kd * v1, kd * v2};
+        float fd[3] = {kd * v0, kd * v1, kd * v2};
+        if (bc.lift) {
+            // F_L = -C_L rho_l V_b v x omega (Table 1), with the drag in the
+            // reaction (Algorithm 1 step 6).
+            const float cl = K.cl_tanh ? fminf(0.288f * tanhf(0.121f * re), K.cl_f) : K.cl_f;
+            const float kl = -cl * K.lift_pref;
+            fd[0] = fmaf(kl, v1 * om[2] - v2 * om[1], fd[0]);
+            fd[1] = fmaf(kl, v2 * om[0] - v0 * om[2], fd[1]);
+            fd[2] = fmaf(kl, v0 * om[1] - v1 * om[0], fd[2]);
+        }
         for (int a = 0; a < 3; ++a) {
             fd_sum[a] += fd[a];
             u[a] = fmaf(fb[a] + fd[a] + fvm[a], K.kdt, u[a]);
@@ -425,19 +492,17 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
     if ((g.walls & 0x20) && !f2_lt(xb[2], top[2])) B.active[b] = 0;
 }
 
-// Table 1 / Eq. 3 constants of each bubble (FP64).
-__global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_factor) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B.nb) return;
-    const double d = B.d[b];
+// Table 1 / Eq. 3 constants of a bubble of diameter d and window half-width n
+// (FP64), with the closure parameters bc (nu: the bubble's column).
+__device__ BubbleK bubble_constants(double d, double n, const BubbleConst& bc) {
     const double r = 0.5 * d;
     const double vol = M_PI * d * d * d / 6.0;
     const double eo = (bc.rho_l - bc.rho_b) * bc.g * d * d / bc.sigma;   // Eq. 3 with d^2
     BubbleK K;
-    K.inv_nf = (float)(1.0 / B.n[b]);
+    K.inv_nf = (float)(1.0 / n);
     K.r = r;
     split_f2(r, K.rh, K.rl);
-    split_f2(B.n[b], K.nh, K.nl);
+    split_f2(n, K.nh, K.nl);
     K.kdt = (float)(bc.dt_b / ((bc.rho_b + bc.c_am * bc.rho_l) * vol));
     K.fb = (float)((bc.rho_l - bc.rho_b) * vol * bc.g);
     K.drag_pref = (float)(0.5 * bc.rho_l * M_PI * r * r * bc.drag_scale);
@@ -446,13 +511,27 @@ __global__ void k_bubble_constants(BubbleDev B, BubbleConst bc, double width_fac
     K.visc_b = (float)(48.0 * bc.nu / d);
     K.re_per_speed = (float)(d / bc.nu);
     K.eo_term = (float)(8.0 / 3.0 * eo / (eo + 4.0));
-    B.k[b] = K;
-    (void)width_factor;
+    // Lift coefficient (Table 1): Eo_d = Eo / E^(2/3), E = 1 / (1 + 0.163
+    // Eo^0.757); f(Eo_d) with the published constant 0.474.
+    const double e = 1.0 / (1.0 + 0.163 * pow(eo, 0.757));
+    const double eo_d = eo / pow(e, 2.0 / 3.0);
+    const double fl = 0.00105 * eo_d * eo_d * eo_d - 0.0159 * eo_d * eo_d - 0.0204 * eo_d + 0.474;
+    K.cl_tanh = eo_d < 4.0 ? 1 : 0;
+    K.cl_f = (float)(eo_d <= 10.0 ? fl : -0.29);
+    K.lift_pref = bc.lift ? (float)(bc.rho_l * vol) : 0.0f;
+    K.fs_coef_dt = bc.stress ? (float)(bc.rho_l * vol / bc.dt_l) : 0.0f;
+    return K;
+}
+
+__global__ void k_bubble_constants(BubbleDev B, BubbleConst bc) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nb) return;
+    B.k[b] = bubble_constants(B.d[b], B.n[b], bc);
 }
 
 cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st) {
     if (b.nb == 0) return cudaSuccess;
-    k_bubble_constants<<<(b.nb + 127) / 128, 128, 0, st>>>(b, bc, 0.0);
+    k_bubble_constants<<<(b.nb + 127) / 128, 128, 0, st>>>(b, bc);
     return cudaGetLastError();
 }
 
@@ -669,7 +748,7 @@ __device__ void clear_prev_tiles(const SmallBins& sb) {
 // With `cols` set (a batch), bubble b lives in column bubble_col[b], whose
 // tiles are numbered from cols[c].tile_base in the shared tile space.
 __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBins& sb,
-                                unsigned long long* keys, int* s_n,
+                                unsigned long long* keys, int* s_n, int pad,
                                 const BatchColumn* cols = nullptr,
                                 const int* bubble_col = nullptr) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -687,7 +766,8 @@ __device__ void bin_small_block(const Geo& g, const BubbleDev& B, const SmallBin
         for (int a = 0; a < 3; ++a) {
             int lo, hi;
             support_cells(F2{__ldcg(B.xh + 3 * b + a), __ldcg(B.xl + 3 * b + a)}, nh, nl, lo, hi);
-            ntl[a] = axis_tiles(lo, hi, L[a], !(gb.walls & (1u << (2 * a))), T[a], tl[a]);
+            ntl[a] = axis_tiles(lo - pad, hi + pad, L[a], !(gb.walls & (1u << (2 * a))), T[a],
+                                tl[a]);
         }
         // One reservation per bubble; its pairs come out in ascending tile
         // order (each axis list is ascending).
@@ -840,12 +920,14 @@ __device__ void write_safe_layers(const Geo& g, const BubbleDev& B, const SmallB
 // that sweep (whose populations it reads and whose tile lists it rewrites),
 // then lets the next sweep start: that sweep runs alongside the rest of the
 // update and waits for it only in the z layers the guard does not clear.
-template <int ST>
+// LIFT: the window carries the vorticity halo and nine sums (add_window_node).
+template <int ST, bool LIFT>
 __global__ void __launch_bounds__(BUBBLE_THREADS, 1)
 k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
                  BubbleDev B, BubbleConst bc, int* __restrict__ flag, SmallBins sb,
                  const BatchColumn* __restrict__ cols, const int* __restrict__ bubble_col) {
-    __shared__ float red[3][BUBBLE_THREADS / 32];
+    constexpr int NV = win_vals(LIFT);
+    __shared__ float red[NV][BUBBLE_THREADS / 32];
     __shared__ unsigned long long keys[SMALL_MAX_PAIRS];
     __shared__ int s_n, s_last;
     const int parts = sb.parts;
@@ -866,26 +948,28 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
         cp = col.cp;
     }
     Window w;
-    const int state = bubble_window(g, in, w);
+    const int state = bubble_window(g, in, w, LIFT ? 1 : 0);
     const int nchunks = state == BUBBLE_LIVE ? (w.M + WINDOW_CHUNK - 1) / WINDOW_CHUNK : 0;
     const float inv_n = in.k.inv_nf;
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;   // thread 0: running sum over this CTA's chunks
+    float sum[NV];   // thread 0: running sum over this CTA's chunks
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sum[q] = 0.0f;
     for (int k = p; k < nchunks; k += parts) {
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+        float acc[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] = 0.0f;
         const int m0 = k * WINDOW_CHUNK;
-        chunk_sum2<ST>(f, g, cp, w, inv_n, m0, min(m0 + WINDOW_CHUNK, w.M), threadIdx.x,
-                       BUBBLE_THREADS, ax, ay, az);
-        block_sum3(ax, ay, az, red);
+        chunk_sum2<ST, LIFT>(f, g, cp, w, inv_n, m0, min(m0 + WINDOW_CHUNK, w.M), threadIdx.x,
+                             BUBBLE_THREADS, acc);
+        block_sum_n<NV>(acc, red);
         if (threadIdx.x == 0) {
             if (parts == 1) {
-                sx += ax;
-                sy += ay;
-                sz += az;
+#pragma unroll
+                for (int q = 0; q < NV; ++q) sum[q] += acc[q];
             } else {
-                float* slot = sb.part + 3 * ((size_t)b * WINDOW_CHUNKS_MAX + k);
-                slot[0] = ax;
-                slot[1] = ay;
-                slot[2] = az;
+                float* slot = sb.part + WIN_VALS_LIFT * ((size_t)b * WINDOW_CHUNKS_MAX + k);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) slot[q] = acc[q];
             }
         }
         __syncthreads();   // `red` is reused by the next chunk
@@ -898,18 +982,16 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
             mine = atomicAdd(sb.arrive + b, 1) == parts - 1;
             if (mine) {
                 __threadfence();
-                const float* q = sb.part + 3 * (size_t)b * WINDOW_CHUNKS_MAX;
-                for (int k = 0; k < nchunks; ++k) {
-                    sx += __ldcg(q + 3 * k);
-                    sy += __ldcg(q + 3 * k + 1);
-                    sz += __ldcg(q + 3 * k + 2);
-                }
+                const float* q = sb.part + WIN_VALS_LIFT * (size_t)b * WINDOW_CHUNKS_MAX;
+                for (int k = 0; k < nchunks; ++k)
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) sum[v] += __ldcg(q + WIN_VALS_LIFT * k + v);
                 sb.arrive[b] = 0;                            // ready for the next launch
             }
         }
         s_last = 0;
         if (mine) {
-            bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz, in);
+            bubble_tail(g, B, bc, flag, b, state, w, sum, in);
             if (alone) {
                 s_last = 1;
             } else {
@@ -921,13 +1003,14 @@ k_bubbles_binned(const typename Store<ST>::T* __restrict__ f, Geo g, CollidePara
     __syncthreads();
     if (!s_last) return;
     if (!alone) __threadfence();
-    bin_small_block(g, B, sb, keys, &s_n, cols, bubble_col);
+    bin_small_block(g, B, sb, keys, &s_n, LIFT ? 1 : 0, cols, bubble_col);
     if (sb.safe != nullptr && cols == nullptr) write_safe_layers(g, B, sb);
     if (threadIdx.x == 0 && !alone) *sb.done = 0;        // ready for the next launch
 }
 
-int window_parts(double max_half_width) {
-    const int cells = std::min((int)std::ceil(2.0 * max_half_width) + 1, WINDOW_CELLS_MAX);
+int window_parts(double max_half_width, int pad) {
+    const int cells =
+        std::min((int)std::ceil(2.0 * max_half_width) + 1 + 2 * pad, WINDOW_CELLS_MAX);
     const int nodes = cells * cells * cells;
     return std::max(1, std::min((nodes + WINDOW_CHUNK - 1) / WINDOW_CHUNK, WINDOW_CHUNKS_MAX));
 }
@@ -948,8 +1031,11 @@ cudaError_t launch_binned(const void* f, const Geo& g, const CollideParams& cp,
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = overlap ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_bubbles_binned<ST>, (const T*)f, g, cp, b, bc, flag, sb,
-                              cols, bubble_col);
+    if (bc.lift)
+        return cudaLaunchKernelEx(&cfg, k_bubbles_binned<ST, true>, (const T*)f, g, cp, b, bc,
+                                  flag, sb, cols, bubble_col);
+    return cudaLaunchKernelEx(&cfg, k_bubbles_binned<ST, false>, (const T*)f, g, cp, b, bc, flag,
+                              sb, cols, bubble_col);
 }
 }  // namespace
 
@@ -1003,7 +1089,7 @@ static_assert(INTERP_THREADS % INTERP_ROWS == 0 && TZ == 4, "tile shape of the i
 // One covered tile t: the Eq. 10 velocity of its nodes, then for each listed
 // bubble the part of its Eq. 20 sum over the tile, written at the bubble's
 // list position.  Every thread of the CTA calls it.
-template <int ST, bool PAIR>
+template <int ST, bool PAIR, bool LIFT>
 __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restrict__ f,
                                             const Geo& g, const CollideParams& cp, int t,
                                             const int* __restrict__ cnt,
@@ -1016,6 +1102,7 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
     __shared__ float s_w[INTERP_CHUNK][NAX];         // per-axis cell integrals per bubble
     __shared__ BubbleRec s_rec[INTERP_CHUNK];
     __shared__ int s_xlo[INTERP_CHUNK], s_xhi[INTERP_CHUNK];   // non-zero x weights
+    __shared__ float s_d[LIFT ? INTERP_CHUNK : 1][NAX];          // lift: difference weights
     const int tid = threadIdx.x;
     const int bx = t % g.ntx, by = (t / g.ntx) % g.nty, bz = t / (g.ntx * g.nty);
     const int xb0 = bx * TX, yb0 = by * TY, zb0 = bz * TZ;
@@ -1088,7 +1175,22 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
         for (int e = tid; e < cntc * NAX; e += INTERP_THREADS) {
             const int k = e / NAX, q = e - k * NAX;
             const BubbleRec& r = s_rec[k];
-            if (q < TX) {
+            if (LIFT) {
+                float w, dw;
+                if (q < TX)
+                    axis_wd(xb0 + q, r.ax, r.fx, r.inv_n, r.h, g.nx, px, false, w, dw);
+                else if (q < TX + TY)
+                    axis_wd(yb0 + q - TX, r.ay, r.fy, r.inv_n, r.h, g.ny, py, false, w, dw);
+                else
+                    axis_wd(zb0 + q - TX - TY, r.az, r.fz, r.inv_n, r.h, g.nz, pz,
+                            (g.walls & WALL_TOP_FREE) != 0, w, dw);
+                s_w[k][q] = w;
+                s_d[k][q] = dw;
+                if (q < TX && (w != 0.0f || dw != 0.0f)) {
+                    atomicMin(&s_xlo[k], q);
+                    atomicMax(&s_xhi[k], q);
+                }
+            } else if (q < TX) {
                 const float w = axis_weight(r, xb0 + q, r.ax, r.fx, g.nx, px);
                 s_w[k][q] = w;
                 if (w != 0.0f) {
@@ -1106,43 +1208,62 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
         // are added over the rows by shuffles (fixed order).
         for (int k0 = 0; k0 < cntc; k0 += INTERP_THREADS / INTERP_ROWS) {
             const int k = k0 + tid / INTERP_ROWS, row = tid % INTERP_ROWS;
-            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            constexpr int NV = win_vals(LIFT);
+            float v[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) v[q] = 0.0f;
             if (k < cntc) {
-                const float wyz = s_w[k][TX + row % TY] * s_w[k][TX + TY + row / TY];
-                if (wyz != 0.0f) {
+                const float wy = s_w[k][TX + row % TY], wz = s_w[k][TX + TY + row / TY];
+                const float dy = LIFT ? s_d[k][TX + row % TY] : 0.0f;
+                const float dz = LIFT ? s_d[k][TX + TY + row / TY] : 0.0f;
+                const float wyz = wy * wz;
+                if (wyz != 0.0f || (LIFT && (dy * wz != 0.0f || wy * dz != 0.0f))) {
                     // Only the x columns with a non-zero weight: zero terms
-                    // add nothing.
-                    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+                    // add nothing.  Row sums sum_x w_x u (and, with lift,
+                    // sum_x d_x u_y and sum_x d_x u_z).
+                    float ax = 0.0f, ay = 0.0f, az = 0.0f, bxy = 0.0f, bxz = 0.0f;
                     const int xe = s_xhi[k];
                     for (int x = s_xlo[k]; x <= xe; ++x) {
                         const float wx = s_w[k][x];
                         ax = fmaf(wx, s_u[0][row][x], ax);
                         ay = fmaf(wx, s_u[1][row][x], ay);
                         az = fmaf(wx, s_u[2][row][x], az);
+                        if (LIFT) {
+                            const float dx = s_d[k][x];
+                            bxy = fmaf(dx, s_u[1][row][x], bxy);
+                            bxz = fmaf(dx, s_u[2][row][x], bxz);
+                        }
                     }
-                    sx = ax * wyz;
-                    sy = ay * wyz;
-                    sz = az * wyz;
+                    v[0] = ax * wyz;
+                    v[1] = ay * wyz;
+                    v[2] = az * wyz;
+                    if (LIFT) {
+                        // Gx u_y, Gx u_z, Gy u_x, Gy u_z, Gz u_x, Gz u_y
+                        v[3] = bxy * wyz;
+                        v[4] = bxz * wyz;
+                        v[5] = ax * (dy * wz);
+                        v[6] = az * (dy * wz);
+                        v[7] = ax * (wy * dz);
+                        v[8] = ay * (wy * dz);
+                    }
                 }
             }
 #pragma unroll
-            for (int o = INTERP_ROWS / 2; o > 0; o >>= 1) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                sz += __shfl_xor_sync(0xffffffffu, sz, o);
-            }
+            for (int q = 0; q < NV; ++q)
+#pragma unroll
+                for (int o = INTERP_ROWS / 2; o > 0; o >>= 1)
+                    v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
             if (row == 0 && k < cntc) {
-                float* q = partial + 3 * (size_t)(c0 + k);
-                q[0] = sx;
-                q[1] = sy;
-                q[2] = sz;
+                float* q = partial + WIN_VALS_LIFT * (size_t)(c0 + k);
+#pragma unroll
+                for (int i = 0; i < NV; ++i) q[i] = v[i];
             }
         }
     }
 }
 
 // Persistent over the list of covered tiles, a tile per CTA in turn.
-template <int ST, bool PAIR>
+template <int ST, bool PAIR, bool LIFT>
 __global__ void __launch_bounds__(INTERP_THREADS, 4)
 k_tile_interp(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
               const int* __restrict__ cnt, const int* __restrict__ off,
@@ -1152,8 +1273,8 @@ k_tile_interp(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams 
     const int ntiles = __ldcg(ncover);
     for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
         __syncthreads();   // the shared tables of the previous tile are done with
-        tile_interp<ST, PAIR>(f, g, cp, __ldcg(cover + i), cnt, off, items, cap, recs, nb,
-                              partial);
+        tile_interp<ST, PAIR, LIFT>(f, g, cp, __ldcg(cover + i), cnt, off, items, cap, recs,
+                                    nb, partial);
     }
 }
 
@@ -1175,20 +1296,20 @@ k_swarm_tail(Geo g, BubbleDev B, BubbleConst bc, int* __restrict__ flag, Bins bi
         load_bubble(B, b, true, in);
         Window w;
         const int state = bubble_window(g, in, w);
-        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        const int nv = win_vals(bc.lift != 0);
+        float acc[WIN_VALS_LIFT];
+        for (int q = 0; q < WIN_VALS_LIFT; ++q) acc[q] = 0.0f;
         if (state == BUBBLE_LIVE) {
             const int n = min(__ldcg(sw.ntile + b), sw.per);
             const int* sl = sw.slots + (size_t)b * sw.per;
             for (int k = 0; k < n; ++k) {
                 const int p = __ldcg(sl + k);
                 if (p < 0 || p >= bins.cap) continue;
-                const float* q = sw.partial + 3 * (size_t)p;
-                sx += __ldcg(q);
-                sy += __ldcg(q + 1);
-                sz += __ldcg(q + 2);
+                const float* q = sw.partial + WIN_VALS_LIFT * (size_t)p;
+                for (int v = 0; v < nv; ++v) acc[v] += __ldcg(q + v);
             }
         }
-        bubble_tail(g, B, bc, flag, b, state, w, sx, sy, sz, in);
+        bubble_tail(g, B, bc, flag, b, state, w, acc, in);
     }
 }
 
@@ -1268,7 +1389,8 @@ __device__ __forceinline__ int block_sum_int(int v, int* red) {
 // The tiles bubble b's window touches, per axis (ascending), as k_bin finds
 // them; returns false for a bubble that is not selected.
 __device__ __forceinline__ bool bubble_tiles(const Geo& g, const BubbleDev& B, const int* select,
-                                             int b, int tl[3][MAX_AXIS_TILES], int nt[3]) {
+                                             int pad, int b, int tl[3][MAX_AXIS_TILES],
+                                             int nt[3]) {
     if (!__ldcg(select + b)) return false;
     const int L[3] = {g.nx, g.ny, g.nz};
     const int T[3] = {TX, TY, TZ};
@@ -1276,7 +1398,7 @@ __device__ __forceinline__ bool bubble_tiles(const Geo& g, const BubbleDev& B, c
     for (int a = 0; a < 3; ++a) {
         int lo, hi;
         support_cells(F2{__ldcg(B.xh + 3 * b + a), __ldcg(B.xl + 3 * b + a)}, nh, nl, lo, hi);
-        nt[a] = axis_tiles(lo, hi, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
+        nt[a] = axis_tiles(lo - pad, hi + pad, L[a], !(g.walls & (1u << (2 * a))), T[a], tl[a]);
     }
     return true;
 }
@@ -1296,7 +1418,7 @@ k_swarm_bin(Geo g, BubbleDev B, Bins bins, SwarmBins sw, const int* __restrict__
     for (int b = gtid; b < B.nb; b += nthreads) {
         int tl[3][MAX_AXIS_TILES], nt[3];
         int n = 0;
-        if (bubble_tiles(g, B, select, b, tl, nt)) {
+        if (bubble_tiles(g, B, select, sw.pad, b, tl, nt)) {
             for (int iz = 0; iz < nt[2]; ++iz)
                 for (int iy = 0; iy < nt[1]; ++iy)
                     for (int ix = 0; ix < nt[0]; ++ix)
@@ -1349,7 +1471,7 @@ k_swarm_bin(Geo g, BubbleDev B, Bins bins, SwarmBins sw, const int* __restrict__
     // 3. Fill.
     for (int b = gtid; b < B.nb; b += nthreads) {
         int tl[3][MAX_AXIS_TILES], nt[3];
-        if (!bubble_tiles(g, B, select, b, tl, nt)) continue;
+        if (!bubble_tiles(g, B, select, sw.pad, b, tl, nt)) continue;
         int k = 0;
         for (int iz = 0; iz < nt[2]; ++iz)
             for (int iy = 0; iy < nt[1]; ++iy)
@@ -1446,32 +1568,36 @@ int interp_grid(int storage) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     cudaError_t e;
     switch (storage) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<0, true>, INTERP_THREADS, 0); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<1, true>, INTERP_THREADS, 0); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<2, true>, INTERP_THREADS, 0); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<0, true, true>, INTERP_THREADS, 0); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<1, true, true>, INTERP_THREADS, 0); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_tile_interp<2, true, true>, INTERP_THREADS, 0); break;
     }
     if (e != cudaSuccess || per < 1) return 0;
     return sms * per;
 }
 
 namespace {
-template <int ST, bool PAIR>
+template <int ST, bool PAIR, bool LIFT>
 cudaError_t launch_interp_as(const void* f, const Geo& g, const CollideParams& cp,
                              const Bins& bins, const BubbleDev& b, const SwarmBins& sw,
                              cudaStream_t st) {
     using T = typename Store<ST>::T;
-    k_tile_interp<ST, PAIR><<<sw.interp_grid, INTERP_THREADS, 0, st>>>(
+    k_tile_interp<ST, PAIR, LIFT><<<sw.interp_grid, INTERP_THREADS, 0, st>>>(
         (const T*)f, g, cp, bins.cnt, bins.off, bins.items, bins.cap, b.rec, b.nb, sw.cover,
         sw.ncover, sw.partial);
     return cudaGetLastError();
 }
 
-// Two-node gathers with aligned row loads on even rows.
+// Two-node gathers with aligned row loads on even rows; the vorticity sums
+// with lift.
 template <int ST>
 cudaError_t launch_interp(const void* f, const Geo& g, const CollideParams& cp, const Bins& bins,
-                          const BubbleDev& b, const SwarmBins& sw, cudaStream_t st) {
-    return (g.nx & 1) == 0 ? launch_interp_as<ST, true>(f, g, cp, bins, b, sw, st)
-                           : launch_interp_as<ST, false>(f, g, cp, bins, b, sw, st);
+                          const BubbleDev& b, const SwarmBins& sw, bool lift, cudaStream_t st) {
+    if (lift)
+        return (g.nx & 1) == 0 ? launch_interp_as<ST, true, true>(f, g, cp, bins, b, sw, st)
+                               : launch_interp_as<ST, false, true>(f, g, cp, bins, b, sw, st);
+    return (g.nx & 1) == 0 ? launch_interp_as<ST, true, false>(f, g, cp, bins, b, sw, st)
+                           : launch_interp_as<ST, false, false>(f, g, cp, bins, b, sw, st);
 }
 
 bool swarm_ready(const SwarmBins& sw) {
@@ -1488,9 +1614,9 @@ cudaError_t launch_swarm_update(int storage, const void* f, const Geo& g,
     if (!swarm_ready(sw)) return cudaErrorInvalidValue;
     cudaError_t e;
     switch (storage) {
-        case 0: e = launch_interp<0>(f, g, cp, bins, b, sw, st); break;
-        case 1: e = launch_interp<1>(f, g, cp, bins, b, sw, st); break;
-        default: e = launch_interp<2>(f, g, cp, bins, b, sw, st); break;
+        case 0: e = launch_interp<0>(f, g, cp, bins, b, sw, bc.lift != 0, st); break;
+        case 1: e = launch_interp<1>(f, g, cp, bins, b, sw, bc.lift != 0, st); break;
+        default: e = launch_interp<2>(f, g, cp, bins, b, sw, bc.lift != 0, st); break;
     }
     if (e != cudaSuccess) return e;
     k_swarm_tail<<<(b.nb + TAIL_THREADS - 1) / TAIL_THREADS, TAIL_THREADS, 0, st>>>(g, b, bc, flag,
@@ -1515,24 +1641,7 @@ __global__ void k_bubble_constants_batch(BubbleDev B, BubbleConst bc, const doub
     if (b >= B.nb) return;
     BubbleConst c = bc;
     c.nu = col_nu[bubble_col[b]];
-    const double d = B.d[b];
-    const double r = 0.5 * d;
-    const double vol = M_PI * d * d * d / 6.0;
-    const double eo = (c.rho_l - c.rho_b) * c.g * d * d / c.sigma;
-    BubbleK K;
-    K.inv_nf = (float)(1.0 / B.n[b]);
-    K.r = r;
-    split_f2(r, K.rh, K.rl);
-    split_f2(B.n[b], K.nh, K.nl);
-    K.kdt = (float)(c.dt_b / ((c.rho_b + c.c_am * c.rho_l) * vol));
-    K.fb = (float)((c.rho_l - c.rho_b) * vol * c.g);
-    K.drag_pref = (float)(0.5 * c.rho_l * M_PI * r * r * c.drag_scale);
-    K.fvm_coef_dt = (float)(c.c_am * c.rho_l * vol / c.dt_l);
-    K.visc_a0 = (float)(24.0 * c.nu / d);
-    K.visc_b = (float)(48.0 * c.nu / d);
-    K.re_per_speed = (float)(d / c.nu);
-    K.eo_term = (float)(8.0 / 3.0 * eo / (eo + 4.0));
-    B.k[b] = K;
+    B.k[b] = bubble_constants(B.d[b], B.n[b], c);
 }
 
 cudaError_t launch_bubble_constants_batch(const BubbleDev& b, const BubbleConst& bc,

@@ -97,6 +97,8 @@ BubbleConst bubble_const(const lbm_ctx* c) {
     bc.dt_b = 1.0 / c->p.substeps;            // Table 2: dt_b = dt_l / substeps
     split_f2(bc.dt_b, bc.dt_bh, bc.dt_bl);
     bc.substeps = c->p.substeps;
+    bc.lift = (c->p.forces & LBM_FORCE_LIFT) ? 1 : 0;
+    bc.stress = (c->p.forces & LBM_FORCE_STRESS) ? 1 : 0;
     return bc;
 }
 
@@ -229,9 +231,11 @@ int enqueue_one_step(lbm_ctx* c) {
     const size_t now = epoch & 1u, next = (epoch + 1u) & 1u;
     const unsigned* safe_now = safe ? safe + now * (size_t)g.ntz : nullptr;
     const int* zperm_now = zperm ? zperm + now * (size_t)nbz : nullptr;
+    const int pad = (c->p.forces & LBM_FORCE_LIFT) ? 1 : 0;   // the vorticity halo
     if (bubbles) {
         if (c->use_small) {
             SmallBins sb = c->small;
+            sb.parts = window_parts(c->hwmax, pad);
             if (sb.safe) sb.safe += next * (size_t)g.ntz;
             if (sb.zperm) sb.zperm += next * (size_t)nbz;
             sb.safe_epoch = epoch + 1;   // the update clears layers for the next step
@@ -248,12 +252,16 @@ int enqueue_one_step(lbm_ctx* c) {
                 LBM_CUDA(cudaMemsetAsync(c->bins.cnt, 0, sizeof(int) * (size_t)c->bins.T,
                                          c->stream), "cover counts");
                 LBM_CUDA(cudaMemsetAsync(c->swarm.ncover, 0, sizeof(int), c->stream), "cover list");
-                LBM_CUDA(launch_swarm_binning(g, c->bub, c->bins, c->swarm, c->bub.active,
-                                              c->flag_d, c->stream), "cover");
+                SwarmBins sw = c->swarm;
+                sw.pad = pad;
+                LBM_CUDA(launch_swarm_binning(g, c->bub, c->bins, sw, c->bub.active, c->flag_d,
+                                              c->stream), "cover");
                 c->launches += 2;
             }
+            SwarmBins sw = c->swarm;
+            sw.pad = pad;
             LBM_CUDA(launch_swarm_update(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
-                                         c->flag_d, c->bins, c->swarm, c->stream),
+                                         c->flag_d, c->bins, sw, c->stream),
                      "bubble update");
             c->launches += SWARM_LAUNCHES;   // interpolation by tiles; update; binning
             c->cover_valid = true;
@@ -332,6 +340,7 @@ void lbm_default_params(lbm_params* p) {
     p->width_factor = 1.5;
     p->substeps = 10;
     p->two_way = 1;
+    p->forces = 0;
 }
 
 void lbm_velocity_set(int* c57, double* w19) {
@@ -407,7 +416,8 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
     if (!(p->g >= 0.0) || !(p->rho_l > 0.0) || !(p->rho_ratio >= 0.0 && p->rho_ratio < 1.0) ||
         !(p->sigma > 0.0) || !(p->c_added_mass >= 0.0) || !(p->drag_scale >= 0.0) ||
         !(p->sn_coeff >= 0.0) || !(p->sn_exp > 0.0) || !(p->width_factor > 0.0) ||
-        p->substeps < 1 || p->substeps > 10000)
+        p->substeps < 1 || p->substeps > 10000 ||
+        (p->forces & ~(LBM_FORCE_LIFT | LBM_FORCE_STRESS)))
         return fail(c, LBM_ERR_ARG, "parameter out of range");
     if (p->rho_ratio + p->c_added_mass <= 0.0)
         return fail(c, LBM_ERR_ARG, "effective bubble mass must be positive");
@@ -415,13 +425,22 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
         std::vector<double> d(c->bub.nb);
         LBM_CUDA(cudaMemcpy(d.data(), c->bub.d, sizeof(double) * d.size(), cudaMemcpyDeviceToHost),
                  "read diameters");
-        for (double v : d)
+        const int pad = (p->forces & LBM_FORCE_LIFT) ? 1 : 0;
+        const int L[3] = {c->nx, c->ny, c->nz};
+        for (double v : d) {
             if (p->width_factor * v > MAX_HALF_WIDTH)
                 return fail(c, LBM_ERR_ARG, "width_factor too large for the current bubbles");
+            for (int a = 0; a < 3; ++a)
+                if (!(c->walls & (1u << (2 * a))) &&
+                    2.0 * p->width_factor * v + 2.0 + 2.0 * pad > (double)L[a])
+                    return fail(c, LBM_ERR_ARG, "a window with the lift's halo wraps onto itself "
+                                "on axis %d", a);
+        }
         if (p->width_factor != c->p.width_factor)
             return fail(c, LBM_ERR_STATE, "set width_factor before lbm_set_bubbles");
     }
     adjoint_free(c);
+    if ((p->forces ^ c->p.forces) & LBM_FORCE_LIFT) c->cover_valid = false;   // lists change reach
     c->p = *p;
     guard_invalidate(c);
     if (c->bub.nb > 0)
@@ -523,12 +542,13 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         if (hw > MAX_HALF_WIDTH)
             return fail(c, LBM_ERR_ARG, "bubble %d: window half-width %g exceeds %g", b, hw,
                         MAX_HALF_WIDTH);
+        const double halo = (c->p.forces & LBM_FORCE_LIFT) ? 2.0 : 0.0;
         for (int a = 0; a < 3; ++a) {
             const double x = pos3[3 * b + a];
             if (!(x >= 0.0 && x < (double)L[a]))
                 return fail(c, LBM_ERR_ARG, "bubble %d: centre outside the box", b);
             const bool periodic = !(c->walls & (1u << (2 * a)));
-            if (periodic && 2.0 * hw + 2.0 > (double)L[a])
+            if (periodic && 2.0 * hw + 2.0 + halo > (double)L[a])
                 return fail(c, LBM_ERR_ARG, "bubble %d: window wraps onto itself on axis %d", b, a);
             if (!periodic && d >= (double)L[a])
                 return fail(c, LBM_ERR_ARG, "bubble %d: wider than the box on axis %d", b, a);
@@ -562,12 +582,13 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     B.cell = (int*)dalloc(c, i1);
     B.rec = (BubbleRec*)dalloc(c, sizeof(BubbleRec) * (size_t)n);
     B.k = (BubbleK*)dalloc(c, sizeof(BubbleK) * (size_t)n);
-    // Upper bound of (tile, bubble) pairs from the largest window.
+    // Upper bound of (tile, bubble) pairs from the largest window, with the
+    // one-cell halo lift may add.
     double dmax = 0.0;
     for (int b = 0; b < n; ++b) dmax = std::fmax(dmax, diam[b]);
     const double hwmax = c->p.width_factor * dmax;
-    const long long per = (long long)axis_tile_bound(hwmax, TX) * axis_tile_bound(hwmax, TY) *
-                          axis_tile_bound(hwmax, TZ);
+    const long long per = (long long)axis_tile_bound(hwmax + 1.0, TX) *
+                          axis_tile_bound(hwmax + 1.0, TY) * axis_tile_bound(hwmax + 1.0, TZ);
     const long long cap = per * n;
     if (cap >= (1LL << 31)) {
         free_bubbles(c);
@@ -585,8 +606,8 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sb.prev_n = (int*)dalloc(c, sizeof(int));
         sb.overflow = (int*)dalloc(c, sizeof(int));
         sb.done = (int*)dalloc(c, sizeof(int));
-        sb.parts = window_parts(hwmax);
-        sb.part = (float*)dalloc(c, sizeof(float) * 3 * WINDOW_CHUNKS_MAX * (size_t)n);
+        sb.parts = window_parts(hwmax, 0);   // set per step (the lift's halo)
+        sb.part = (float*)dalloc(c, sizeof(float) * WIN_VALS_LIFT * WINDOW_CHUNKS_MAX * (size_t)n);
         sb.arrive = (int*)dalloc(c, sizeof(int) * (size_t)n);
         lists_ok = sb.start && sb.count && sb.items && sb.prev_tiles && sb.prev_n && sb.overflow &&
                    sb.done && sb.part && sb.arrive;
@@ -619,7 +640,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sw.kidx = (int*)dalloc(c, sizeof(int) * (size_t)cap);
         sw.slots = (int*)dalloc(c, sizeof(int) * (size_t)cap);   // n * per
         sw.ntile = (int*)dalloc(c, sizeof(int) * (size_t)n);
-        sw.partial = (float*)dalloc(c, 3 * sizeof(float) * (size_t)cap);
+        sw.partial = (float*)dalloc(c, WIN_VALS_LIFT * sizeof(float) * (size_t)cap);
         sw.cover = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.T);
         sw.ncover = (int*)dalloc(c, sizeof(int));
         sw.chunk_sums = (int*)dalloc(c, sizeof(int) * (size_t)sw.grid);
@@ -657,6 +678,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
     LBM_CUDA(launch_bubble_constants(B, bubble_const(c), s), "bubble constants");
     LBM_CUDA(cudaStreamSynchronize(s), "bubble upload");
     c->nb_cap = n;
+    c->hwmax = hwmax;
     return LBM_OK;
 }
 

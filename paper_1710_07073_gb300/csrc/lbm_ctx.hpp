@@ -39,6 +39,7 @@ struct lbm_ctx {
     // bubbles
     BubbleDev bub{};
     int nb_cap = 0;
+    double hwmax = 0.0;          // largest window half-width of the bubbles
     // bins: the large path (count, scan, fill, sort) or, for few pairs, the
     // single-launch small path
     Bins bins{};

@@ -256,6 +256,33 @@ __device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc,
     return cell_poly(rc * r.inv_n, r.h);
 }
 
+// Per-axis factors for the interpolated vorticity (lift), by summation by
+// parts.  The central difference of the node velocity, (u(c+1) - u(c-1))/2,
+// interpolated with the Eq. 19 weights w, is a sum of the velocities u(c)
+// times d(c) = (w(c-1) - w(c+1))/2 (w zero beyond a wall face), plus the
+// ghost terms of the face nodes: the ghost beyond a no-slip wall is -u (+w/2
+// at the low face, -w/2 at the high face), beyond the free-slip top +u for
+// the tangential components the curl differentiates (+w/2).  Periodic axes
+// wrap the distance to the nearer image.  Returns w(c) and d(c) for the
+// cell c, anchor cell anc and offset fr of the centre.
+__device__ __forceinline__ void axis_wd(int c, int anc, float fr, float inv_n, float hh, int L,
+                                        bool periodic, bool free_hi, float& w, float& d) {
+    float rc = (float)(c - anc) + 0.5f - fr;
+    if (periodic) {
+        if (rc > 0.5f * L) rc -= (float)L;
+        else if (rc < -0.5f * L) rc += (float)L;
+    }
+    const float s = rc * inv_n;
+    w = cell_poly(s, hh);
+    const float wm = (!periodic && c - 1 < 0) ? 0.0f : cell_poly(s - inv_n, hh);
+    const float wp = (!periodic && c + 1 > L - 1) ? 0.0f : cell_poly(s + inv_n, hh);
+    d = 0.5f * (wm - wp);
+    if (!periodic) {
+        if (c == 0) d += 0.5f * w;
+        if (c == L - 1) d += free_hi ? 0.5f * w : -0.5f * w;
+    }
+}
+
 // The tile lists and records are read through L2 (ld.global.cg): with the
 // sweep overlapping the bubble update, they are written while the sweep runs,
 // so the read-only cache path is not used for them.

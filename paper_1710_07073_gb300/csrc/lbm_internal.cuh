@@ -110,6 +110,13 @@ struct BubbleK {
     float visc_b;       // 48 nu / d
     float re_per_speed; // d / nu
     float eo_term;      // 8/3 Eo / (Eo + 4)
+    // Lift (Table 1): C_L = cl_tanh ? min(0.288 tanh(0.121 Re), cl_f) : cl_f,
+    // F_L = -C_L lift_pref (u_b - u_l) x (curl u_l); lift_pref = rho_l V_b,
+    // 0 with lift off.
+    float lift_pref;
+    float cl_f;
+    int cl_tanh;
+    float fs_coef_dt;   // rho_l V_b / dt_l for F_S = rho_l V_b D_t u_l (0: off)
 };
 
 // Bubble state on the device.  A context keeps the centres as two floats
@@ -142,7 +149,16 @@ struct BubbleConst {
     double g, rho_l, rho_b, sigma, c_am, drag_scale, sn_coeff, sn_exp, nu, dt_b, dt_l;
     float dt_bh, dt_bl;   // dt_b as two floats
     int substeps;
+    int lift;             // F_L of Table 1 on (the windows then carry the vorticity halo)
+    int stress;           // F_S of Table 1 on
 };
+
+// Values a window sum carries per bubble: the Eq. 20 velocity (3) and, with
+// lift, six sums that give the interpolated vorticity (by summation by parts:
+// the central differences of Eq. 10 velocities, interpolated with Eq. 19
+// weights, are sums of the velocities times per-axis difference weights).
+constexpr int WIN_VALS_LIFT = 9;
+__host__ __device__ constexpr int win_vals(bool lift) { return lift ? WIN_VALS_LIFT : 3; }
 
 // A double as two floats (h = v rounded, l = the rest rounded) and back.
 __host__ __device__ inline void split_f2(double v, float& h, float& l) {
@@ -178,7 +194,7 @@ constexpr int SMALL_MAX_PAIRS = 4096;
 // A bubble window is reduced in chunks of WINDOW_CHUNK nodes (two per thread
 // of a 256-thread bubble CTA): at most (2 MAX_HALF_WIDTH + 2)^3 / WINDOW_CHUNK
 // rounded up.
-constexpr int WINDOW_CELLS_MAX = 2 * (int)MAX_HALF_WIDTH + 2;
+constexpr int WINDOW_CELLS_MAX = 2 * (int)MAX_HALF_WIDTH + 4;   // + a halo cell each side (lift)
 constexpr int WINDOW_CHUNK = 512;
 constexpr int WINDOW_CHUNKS_MAX =
     (WINDOW_CELLS_MAX * WINDOW_CELLS_MAX * WINDOW_CELLS_MAX + WINDOW_CHUNK - 1) / WINDOW_CHUNK;
@@ -192,7 +208,7 @@ struct SmallBins {
     int* overflow;     // [1]
     int* done;         // [1] bubbles the update has finished (0 between launches)
     int parts;         // CTAs per bubble in the update, 1..WINDOW_CHUNKS_MAX
-    float* part;       // [nb * WINDOW_CHUNKS_MAX * 3] chunk sums (parts > 1)
+    float* part;       // [nb * WINDOW_CHUNKS_MAX * WIN_VALS_LIFT] chunk sums (parts > 1)
     int* arrive;       // [nb] CTAs of a bubble that have finished (0 between launches)
     // Overlap guard (single column): safe[l] = e states that no bubble force
     // reaches z tile layer l in the step numbered e.  The update writes
@@ -223,7 +239,8 @@ struct SwarmBins {
     int* slots;           // [nb * per] list position of bubble b's k-th tile
     int* ntile;           // [nb] tiles of bubble b in the last binning (0: not binned)
     int per;              // tiles a bubble's window can touch at most
-    float* partial;       // [3 * cap] Eq. 20 sums of each (tile, bubble) entry
+    float* partial;       // [WIN_VALS_LIFT * cap] Eq. 20 sums of each (tile, bubble) entry
+    int pad;              // cells the lists reach beyond the supports (1 with lift)
     int* cover;           // [T] the tiles with a non-empty list (any order)
     int* ncover;          // [1] their number
     int interp_grid;      // CTAs of the interpolation launch
@@ -269,9 +286,9 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
 cudaError_t launch_bubbles(int storage, const void* f, const Geo& g, const CollideParams& cp,
                            const BubbleDev& b, const BubbleConst& bc, int* flag,
                            const SmallBins& sb, bool overlap, cudaStream_t st);
-// CTAs per bubble for windows of half-width up to max_half_width: one per
-// 256-node chunk of the largest window.
-int window_parts(double max_half_width);
+// CTAs per bubble for windows of half-width up to max_half_width, widened by
+// `pad` cells each side: one per WINDOW_CHUNK nodes of the largest window.
+int window_parts(double max_half_width, int pad);
 cudaError_t launch_bubble_constants(const BubbleDev& b, const BubbleConst& bc, cudaStream_t st);
 // Host: FP64 centres and velocities of n bubbles into the device state
 // (vel3 may be null: at rest); u_l, its previous value and psi are zeroed.

@@ -31,6 +31,9 @@ LBM_WALL_ALL = 0x3F
 LBM_TOP_FREE_SLIP = 0x40
 LBM_WALL_ALL_FREE_TOP = 0x7F
 
+LBM_FORCE_LIFT = 0x1
+LBM_FORCE_STRESS = 0x2
+
 LBM_STORE_F32 = 0
 LBM_STORE_F16 = 1
 LBM_STORE_BF16 = 2
@@ -56,6 +59,7 @@ class lbm_params(ctypes.Structure):
         ("width_factor", ctypes.c_double),
         ("substeps", ctypes.c_int),
         ("two_way", ctypes.c_int),
+        ("forces", ctypes.c_int),
     ]
 
 

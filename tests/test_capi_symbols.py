@@ -98,3 +98,21 @@ def test_create_accepts_free_slip_top_with_bounded_z(libpath, walls):
     from paper_1710_07073_gb300 import lbm
     h = lbm.lbm_create(8, 8, 8, 1.6, walls)
     lbm.lbm_destroy(h)
+
+
+def test_params_forces_bits_checked(libpath):
+    # lbm_params.forces takes LBM_FORCE_LIFT and LBM_FORCE_STRESS only.
+    from paper_1710_07073_gb300 import lbm
+    h = lbm.lbm_create(16, 16, 16, 1.6, lbm.LBM_WALL_ALL)
+    try:
+        p = lbm.lbm_default_params()
+        assert p.forces == 0
+        p.forces = lbm.LBM_FORCE_LIFT | lbm.LBM_FORCE_STRESS
+        lbm.lbm_set_params(h, p)
+        assert lbm.lbm_get_params(h).forces == 3
+        p.forces = 4
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_params(h, p)
+        assert e.value.code == lbm.LBM_ERR_ARG
+    finally:
+        lbm.lbm_destroy(h)
