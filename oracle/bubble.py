@@ -31,6 +31,15 @@ Readings of the paper where it is garbled or silent:
   Eo^0.757).  Lift and the stress-gradient force are off unless asked for.
 * The stress-gradient force F_S = rho_l V_b D_t u_l uses the same D_t u_l as
   the virtual-mass force.
+* Sec. 3.2 defines the reaction as psi_b = -sum F, the reaction of the
+  momentum the liquid transfers to the bubble, while Algorithm 1 step 6
+  writes -(F_D + F_L).  The default follows Algorithm 1; ``reaction="all"``
+  takes the sum over the interphase forces of Table 1, F_D + F_L + F_S +
+  F_VM, with F_VM = C_A rho_l V_b (D_t u_l - D_t u_b) and D_t u_b the
+  sub-step's acceleration (before any wall clamp), averaged over the
+  sub-steps.  Gravity acts on the bubble from outside the liquid, and the
+  liquid's hydrostatic share of F_B is carried by the reduced pressure the
+  liquid has no gravity for, so neither is passed back.
 """
 import math
 
@@ -44,7 +53,12 @@ class BubbleParams:
 
     def __init__(self, omega, g=1e-5, rho_l=1.0, rho_ratio=1e-3, sigma=5.84e-6,
                  c_added_mass=0.5, drag_scale=1.0, sn_coeff=0.15, sn_exp=0.687,
-                 width_factor=1.5, substeps=10, dt_l=1.0, lift=False, stress_gradient=False):
+                 width_factor=1.5, substeps=10, dt_l=1.0, lift=False, stress_gradient=False,
+                 mapping="cell", reaction="drag_lift"):
+        if mapping not in ("cell", "point"):
+            raise ValueError("mapping must be 'cell' or 'point'")
+        if reaction not in ("drag_lift", "all"):
+            raise ValueError("reaction must be 'drag_lift' or 'all'")
         self.omega = omega
         self.nu = viscosity(omega)
         self.g = g
@@ -61,6 +75,8 @@ class BubbleParams:
         self.dt_b = dt_l / substeps   # Table 2: dt_b = dt_l / 10
         self.lift = lift                          # F_L of Table 1
         self.stress_gradient = stress_gradient    # F_S of Table 1
+        self.mapping = mapping                    # Eq. 19 cell integral or point sample
+        self.reaction = reaction                  # psi_b = -(F_D + F_L) or -sum F
 
 
 def volume(d):
@@ -147,8 +163,9 @@ def advance(x, u, d, ul, dul, dims, walls, p, omega_l=None):
     velocity interpolated at x (Eq. 20); dul: D_t u_l; omega_l: the liquid
     vorticity interpolated at x (Eq. 20; needed with lift on).  Runs
     ``p.substeps`` explicit updates of Eq. 4 with dt_b, each followed by the
-    position step.  Returns (x_new, u_new, psi) with psi = -(mean of F_D + F_L)
-    the reaction (step 6).
+    position step.  Returns (x_new, u_new, psi) with psi the reaction averaged
+    over the sub-steps: -(F_D + F_L) (step 6), or with ``p.reaction == "all"``
+    -(F_D + F_L + F_S + F_VM) (Sec. 3.2, psi_b = -sum F).
     """
     x = np.array(x, dtype=np.float64)
     u = np.array(u, dtype=np.float64)
@@ -159,13 +176,19 @@ def advance(x, u, d, ul, dul, dims, walls, p, omega_l=None):
     dul = np.asarray(dul, dtype=np.float64)
     fvm_liquid = p.c_added_mass * p.rho_l * volume(d) * dul
     fs = p.rho_l * volume(d) * dul if p.stress_gradient else np.zeros(3)   # F_S
+    ca_vol = p.c_added_mass * p.rho_l * volume(d)
     fd_sum = np.zeros(3)
     for _ in range(p.substeps):
         fd = drag_force(u - ul, d, p)
         if p.lift:
             fd = fd + lift_force(u - ul, omega_l, d, p)      # F_D + F_L
-        fd_sum += fd
-        u = u + (fb + fd + fvm_liquid + fs) / meff * p.dt_b   # Eq. 4 with m_eff
+        accel = (fb + fd + fvm_liquid + fs) / meff          # Eq. 4 with m_eff
+        if p.reaction == "all":
+            fvm = ca_vol * (dul - accel)                    # F_VM with this sub-step's D_t u_b
+            fd_sum += fd + fs + fvm
+        else:
+            fd_sum += fd
+        u = u + accel * p.dt_b
         x = x + u * p.dt_b                                  # S = u^{k+1} dt_b
         for a in range(3):
             length = dims[a]

@@ -8,7 +8,8 @@ One call of ``OracleSim.step`` is one pass of Algorithm 1's loop body:
            with lift on its vorticity (central differences, the same map);
   step 4-5 forces (Table 1) and the explicit Newton update with sub-steps
            (Eq. 4, Table 2);
-  step 6   backward coupling: psi_b = -F_D spread with Eq. 21 at the updated
+  step 6   backward coupling: psi_b = -(F_D + F_L) (or the sum of the
+           interphase forces, Sec. 3.2) spread with Eq. 21 at the updated
            bubble position;
   step 7-9 first forcing, collision, second forcing (Eq. 12-15) with the
            spread force, then streaming (Eq. 16) with half-way bounce-back;
@@ -64,6 +65,7 @@ class OracleSim:
         p = self.p
         nb = len(self.d)
         force = None
+        point = p.mapping == "point"
         if nb and self.active.any():
             rho = lat.density(self.f)
             u_nodes = lat.momentum(self.f) / rho                 # Eq. 10, bare moment
@@ -72,8 +74,9 @@ class OracleSim:
             for b in range(nb):
                 if not self.active[b]:
                     continue
-                ul = mapping.interpolate(u_nodes, self.x[b], self.n[b], self.walls)   # Eq. 20
-                wl = (mapping.interpolate(w_nodes, self.x[b], self.n[b], self.walls)
+                ul = mapping.interpolate(u_nodes, self.x[b], self.n[b], self.walls,
+                                         point)                                    # Eq. 20
+                wl = (mapping.interpolate(w_nodes, self.x[b], self.n[b], self.walls, point)
                       if p.lift else None)
                 dul = (ul - self.ul_prev[b]) / p.dt_l if self.has_prev[b] else np.zeros(3)
                 x_new, u_new, psi = bub.advance(self.x[b], self.u[b], self.d[b], ul, dul,
@@ -87,7 +90,7 @@ class OracleSim:
                 xs_new.append(x_new)
                 psis.append(psi)
                 ns.append(self.n[b])
-            force = mapping.spread(psis, xs_new, ns, self.dims, self.walls)   # Eq. 21
+            force = mapping.spread(psis, xs_new, ns, self.dims, self.walls, point)   # Eq. 21
             if self.walls & lat.WALL_ZP:
                 nz = self.dims[2]
                 for b in range(nb):

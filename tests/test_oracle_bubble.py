@@ -247,3 +247,49 @@ def test_stress_gradient_adds_rho_l_v_b_dtul():
     for step in range(1, 6):
         x, u, _ = bub.advance(x, u, d, ul, dul, (64, 64, 64), lat.ALL_WALLS, p)
         np.testing.assert_allclose(u, vinf * (1.0 - q ** (step * p.substeps)), rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("lift,stress", [(False, False), (True, True)])
+def test_reaction_all_interphase_forces_closed_form(lift, stress):
+    # Sec. 3.2's psi_b = -sum F over the interphase forces F_D + F_L + F_S +
+    # F_VM, with F_VM = C_A rho_l V_b (D_t u_l - a_k): since m_eff a_k =
+    # F_B + F_D + F_L + F_S + C_A rho_l V_b D_t u_l, the sum is m_b a_k - F_B,
+    # and its mean over the sub-steps is m_b (u_new - u_old)/dt_l - F_B.  So
+    # psi = F_B - m_b (u_new - u_old)/dt_l whatever the closures (no clamp).
+    rng = np.random.default_rng(41)
+    for _ in range(20):
+        p = bub.BubbleParams(1.6, g=1e-4, lift=lift, stress_gradient=stress, reaction="all",
+                             rho_ratio=rng.uniform(1e-3, 0.5))
+        d = rng.uniform(1.0, 3.0)
+        x = np.array([20.0, 20.0, 20.0])
+        u = rng.normal(scale=1e-3, size=3)
+        ul = rng.normal(scale=1e-3, size=3)
+        dul = rng.normal(scale=1e-5, size=3)
+        om = rng.normal(scale=1e-3, size=3)
+        x1, u1, psi = bub.advance(x, u, d, ul, dul, (40, 40, 40), lat.ALL_WALLS, p, omega_l=om)
+        mb = p.rho_b * bub.volume(d)
+        expect = bub.buoyancy_force(d, p) - mb * (u1 - u) / p.dt_l
+        np.testing.assert_allclose(psi, expect, rtol=1e-9, atol=1e-12 * np.abs(expect).max())
+        # and it differs from Algorithm 1's -(F_D + F_L) while the bubble accelerates
+        p0 = bub.BubbleParams(1.6, g=1e-4, lift=lift, stress_gradient=stress,
+                              rho_ratio=p.rho_b / p.rho_l)
+        _, _, psi0 = bub.advance(x, u, d, ul, dul, (40, 40, 40), lat.ALL_WALLS, p0, omega_l=om)
+        assert np.abs(psi0 - psi).max() > 1e-3 * np.abs(psi).max()
+
+
+def test_reaction_all_of_massless_bubble_is_buoyancy():
+    # m_b = 0: the liquid takes the whole buoyancy at every step, however far
+    # from terminal the bubble is.
+    p = bub.BubbleParams(1.6, rho_ratio=0.0, reaction="all")
+    x, u = np.array([8.0, 8.0, 8.0]), np.zeros(3)
+    for _ in range(3):
+        x, u, psi = bub.advance(x, u, 2.0, np.zeros(3), np.array([1e-6, 0.0, 2e-6]),
+                                (16, 16, 32), lat.ALL_WALLS, p)
+        np.testing.assert_allclose(psi, bub.buoyancy_force(2.0, p), rtol=1e-12, atol=1e-20)
+
+
+def test_mapping_and_reaction_switches_validated():
+    with pytest.raises(ValueError):
+        bub.BubbleParams(1.6, mapping="nodal")
+    with pytest.raises(ValueError):
+        bub.BubbleParams(1.6, reaction="drag")

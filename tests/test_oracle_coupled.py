@@ -60,3 +60,39 @@ def test_bubble_deactivated_at_top_wall():
     sim.run(3)
     assert np.array_equal(sim.x[0], x_stop)
     assert sim.last_force is None
+
+
+@pytest.mark.parametrize("point", [False, True])
+def test_reaction_all_conserves_mixture_momentum(point):
+    # With psi_b = -sum F (Sec. 3.2) Newton's third law holds for the mixture:
+    # on a periodic box the liquid's momentum sum c_j f_j plus the bubbles'
+    # own momentum m_b u_b grows by exactly the buoyancy sum F_B per step
+    # (liquid: + sum psi, Eq. 12-15; bubble: m_b (u_new - u_old) = F_B - psi).
+    # With Algorithm 1's -(F_D + F_L) the added-mass exchange is missing.
+    def run(reaction):
+        p = bub.BubbleParams(1.6, g=1e-4, rho_ratio=0.05, reaction=reaction,
+                             mapping="point" if point else "cell")
+        sim = OracleSim((12, 12, 16), 1.6, 0, p)
+        sim.set_bubbles([[6.0, 6.2, 5.0], [3.1, 9.0, 11.5]], [[0, 0, 0], [1e-4, 0, 0]],
+                        [2.0, 1.5])
+        mb = p.rho_b * bub.volume(sim.d)
+        fb = sum(bub.buoyancy_force(d, p) for d in sim.d)
+        gaps = []
+        for _ in range(6):
+            p0 = lat.momentum(sim.f).sum(axis=(1, 2, 3)) + (mb[:, None] * sim.u).sum(axis=0)
+            sim.step()
+            p1 = lat.momentum(sim.f).sum(axis=(1, 2, 3)) + (mb[:, None] * sim.u).sum(axis=0)
+            gaps.append(np.abs(p1 - p0 - fb).max() / np.abs(fb).max())
+        return max(gaps)
+    assert run("all") < 1e-9
+    assert run("drag_lift") > 1e-4
+
+
+def test_point_mapping_two_way_exchange_is_equal_and_opposite():
+    p = bub.BubbleParams(1.6, mapping="point")
+    sim = OracleSim((12, 12, 16), 1.6, lat.ALL_WALLS, p)
+    sim.set_bubbles([[1.3, 6.2, 5.0], [3.1, 9.0, 14.5]], [[0, 0, 0], [1e-4, 0, 0]], [2.0, 1.5])
+    for _ in range(4):
+        sim.step()
+        assert np.allclose(sim.last_force.sum(axis=(1, 2, 3)), sim.psi.sum(axis=0),
+                           rtol=1e-12, atol=1e-18)

@@ -169,3 +169,70 @@ def test_interpolation_reproduces_linear_field(n, tol):
         xb = rng.uniform(n + 1.0, 31.0 - n, 3)
         out = mapping.interpolate(sigma, xb, n, lat.ALL_WALLS)
         assert np.all(np.abs(out - (a * xb + b)) <= tol * np.abs(a)), (xb, out)
+
+
+# ---- point-sampled variant of Eq. 19 (node values of Z, renormalised) -------
+
+def test_point_sampled_weights_node_centred_by_hand():
+    # n = 3 with the centre on node 6 (x = 6.5): the node samples of
+    # (1 - (r/n)^2)^2 at r = 0, +-1, +-2 are 1, 64/81, 25/81 (r = +-3 sits on
+    # the window edge, Z = 0), so the renormalised factors are
+    # (25, 64, 81, 64, 25) / 259 on nodes 4..8.
+    cells, w = mapping.axis_window(6.5, 3.0, 16, False, point=True)
+    keep = w > 0
+    assert list(cells[keep]) == [4, 5, 6, 7, 8]
+    np.testing.assert_allclose(w[keep] / w.sum(), np.array([25, 64, 81, 64, 25]) / 259.0,
+                               rtol=1e-15, atol=0)
+    cz, cy, cx, w3 = mapping.window_weights([6.5, 6.5, 6.5], 3.0, (16, 16, 16), lat.ALL_WALLS,
+                                            point=True)
+    ax = np.array([0, 25, 64, 81, 64, 25, 0]) / 259.0
+    np.testing.assert_allclose(w3, ax[:, None, None] * ax[None, :, None] * ax[None, None, :],
+                               rtol=1e-14, atol=1e-18)
+
+
+def test_point_samples_sum_to_one_up_to_midpoint_error():
+    # The node samples of Z are a midpoint rule for its unit integral; Z and Z'
+    # vanish at +-n and Z'' jumps there by J = 15/(2 n^3), so by Poisson
+    # summation the error is at most 2 J sum_{k != 0} |2 pi k|^-3 + O(n^-4)
+    # = 2 J 2 zeta(3) / (2 pi)^3 + ... = 0.145 n^-3 + ...
+    rng = np.random.default_rng(21)
+    for _ in range(300):
+        n = rng.uniform(1.0, 12.0)
+        xb = 40.0 + rng.uniform(0.0, 1.0)
+        raw = mapping.cell_factor(np.arange(0, 80), xb, n, point=True).sum()
+        assert abs(raw - 1.0) < 0.16 / n ** 3
+
+
+def test_point_and_cell_weights_converge_second_order():
+    # The midpoint value of a cell differs from its mean by h^2 Z''/24: the
+    # two maps agree to O(n^-2) relative to the O(1/n) weights.  A sample off
+    # the node centre (x = i instead of i + 1/2) would differ at O(1/n).
+    rng = np.random.default_rng(22)
+    for n in (1.5, 3.0, 6.0, 12.0):
+        worst = 0.0
+        for _ in range(50):
+            xb = 30.0 + rng.uniform(0.0, 1.0)
+            cells = np.arange(0, 60)
+            wp = mapping.cell_factor(cells, xb, n, point=True)
+            wc = mapping.cell_factor(cells, xb, n, point=False)
+            worst = max(worst, n * np.abs(wp / wp.sum() - wc).max())
+        assert worst < 0.35 / n ** 2
+
+
+@pytest.mark.parametrize("walls", [0, lat.ALL_WALLS])
+def test_point_spreading_equal_and_opposite(walls):
+    # Eq. 21 with point-sampled weights: after renormalisation the spread
+    # force sums to psi also for windows cut by a wall or wrapping.
+    rng = np.random.default_rng(23)
+    dims = (12, 10, 14)
+    psis = [rng.normal(size=3) for _ in range(4)]
+    xs = [[rng.uniform(0.0, L) for L in dims] for _ in range(4)]
+    ns = [1.5 * rng.uniform(0.6, 2.0) for _ in range(4)]
+    phi = mapping.spread(psis, xs, ns, dims, walls, point=True)
+    np.testing.assert_allclose(phi.sum(axis=(1, 2, 3)), np.sum(psis, axis=0), rtol=1e-12,
+                               atol=1e-14)
+    for xb, n in zip(xs, ns):
+        w = mapping.node_weights(xb, n, dims, walls, point=True)
+        assert abs(w.sum() - 1.0) < 1e-13 and (w >= 0.0).all()
+        cz, cy, cx, ww = mapping.window_weights(xb, n, dims, walls, point=True)
+        np.testing.assert_allclose(w[np.ix_(cz, cy, cx)], ww, rtol=1e-12, atol=1e-16)
