@@ -104,7 +104,36 @@ typedef struct lbm_params {
     int    two_way;       /* 1: spread the reaction onto the liquid (Eq. 21)*/
     int    forces;        /* LBM_FORCE_* bits: the Table 1 forces beyond    */
                           /* buoyancy, drag and virtual mass (0: none)      */
+    int    mapping;       /* LBM_MAP_CELL (Eq. 19) or LBM_MAP_POINT         */
+    int    reaction;      /* LBM_REACTION_DRAG_LIFT or LBM_REACTION_ALL     */
 } lbm_params;
+
+/* Mapping weights (lbm_params.mapping), for interpolation (Eq. 20) and
+ * spreading (Eq. 21) alike, renormalised over the in-box nodes either way:
+ *   LBM_MAP_CELL   the cell integral of Z over the node's cell (Eq. 19);
+ *   LBM_MAP_POINT  Z sampled at the node, times the cell width.  The node
+ *                  samples sum to one only up to the midpoint rule's error
+ *                  (below 0.15 n^-3), which the renormalisation removes.
+ *                  Needs n = width_factor d_b > 1/2 for every bubble, so
+ *                  that the nearest node lies inside the window
+ *                  (lbm_set_bubbles returns LBM_ERR_ARG otherwise).
+ * The mapping can change only while the context holds no bubbles
+ * (LBM_ERR_STATE otherwise). */
+#define LBM_MAP_CELL  0
+#define LBM_MAP_POINT 1
+
+/* Reaction spread onto the liquid (lbm_params.reaction), averaged over the
+ * bubble sub-steps of a liquid step:
+ *   LBM_REACTION_DRAG_LIFT  psi_b = -(F_D + F_L) (Algorithm 1 step 6);
+ *   LBM_REACTION_ALL        psi_b = -sum F over the interphase forces of
+ *                           Table 1 (Sec. 3.2): F_D + F_L + F_S + F_VM with
+ *                           F_VM = C_A rho_l V_b (D_t u_l - D_t u_b), D_t u_b
+ *                           the sub-step's acceleration.  Gravity and the
+ *                           hydrostatic part of F_B are not passed back, so
+ *                           psi_b = F_B - m_b (u_b^{n+1} - u_b^n)/dt_l, and
+ *                           the mixture's momentum grows by sum F_B per step. */
+#define LBM_REACTION_DRAG_LIFT 0
+#define LBM_REACTION_ALL       1
 
 /* Optional interface forces of Table 1 (lbm_params.forces):
  *   LBM_FORCE_LIFT    F_L = -C_L rho_l V_b (u_b - u_l) x (curl u_l) with
@@ -127,7 +156,8 @@ typedef void  (*lbm_free_fn)(void* ptr, size_t bytes, void* user);
 
 /* Fill *p with the defaults: g=1e-5, rho_l=1, rho_ratio=1e-3,
  * sigma=5.84e-6, C_A=0.5, drag_scale=1, sn_coeff=0.15, sn_exp=0.687,
- * width_factor=1.5, substeps=10, two_way=1, forces=0. */
+ * width_factor=1.5, substeps=10, two_way=1, forces=0, mapping=LBM_MAP_CELL,
+ * reaction=LBM_REACTION_DRAG_LIFT. */
 void lbm_default_params(lbm_params* p);
 
 /* Velocity set and weights in the library's direction order (Eq. 7-8):
@@ -255,8 +285,9 @@ int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
  * backward the context is back at the state the forward ended in.  Any call
  * that changes the state between the two (lbm_step, lbm_set_*) discards the
  * record; lbm_adj_backward then returns LBM_ERR_STATE.  A free-slip top
- * (LBM_TOP_FREE_SLIP) and the optional forces (lbm_params.forces) are not
- * covered: lbm_adj_forward returns LBM_ERR_STATE.
+ * (LBM_TOP_FREE_SLIP), the optional forces (lbm_params.forces), point-sampled
+ * mapping and the -sum F reaction are not covered: lbm_adj_forward returns
+ * LBM_ERR_STATE.
  * Memory: one state per
  * checkpoint plus checkpoint_every states during the backward.  With kernel
  * timing on (lbm_set_kernel_timing), lbm_adj_backward times each launch of

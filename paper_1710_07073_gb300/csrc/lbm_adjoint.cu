@@ -756,6 +756,9 @@ extern "C" int lbm_adj_forward(lbm_ctx* c, int nsteps, int checkpoint_every, int
         return fail(c, LBM_ERR_STATE, "the adjoint covers no-slip and periodic faces only");
     if (c->p.forces != 0)
         return fail(c, LBM_ERR_STATE, "the adjoint covers buoyancy, drag and virtual mass only");
+    if (c->p.mapping != LBM_MAP_CELL || c->p.reaction != LBM_REACTION_DRAG_LIFT)
+        return fail(c, LBM_ERR_STATE, "the adjoint covers the cell-integral map and the "
+                    "-(F_D + F_L) reaction only");
     const int nb = c->bub.nb;
     if (nb < 1 || nb > ADJ_MAX_BUBBLES)
         return fail(c, LBM_ERR_STATE, "the adjoint needs 1..%d bubbles", ADJ_MAX_BUBBLES);

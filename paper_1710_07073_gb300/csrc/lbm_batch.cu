@@ -135,6 +135,8 @@ BubbleConst batch_bubble_const(const lbm_batch* b) {
     bc.substeps = b->p.substeps;
     bc.lift = (b->p.forces & LBM_FORCE_LIFT) ? 1 : 0;
     bc.stress = (b->p.forces & LBM_FORCE_STRESS) ? 1 : 0;
+    bc.point = b->p.mapping == LBM_MAP_POINT ? 1 : 0;
+    bc.reaction_all = b->p.reaction == LBM_REACTION_ALL ? 1 : 0;
     return bc;
 }
 
@@ -453,12 +455,16 @@ int lbm_batch_set_params(lbm_batch* b, const lbm_params* p) {
         !(p->sigma > 0.0) || !(p->c_added_mass >= 0.0) || !(p->drag_scale >= 0.0) ||
         !(p->sn_coeff >= 0.0) || !(p->sn_exp > 0.0) || !(p->width_factor > 0.0) ||
         p->substeps < 1 || p->substeps > 10000 || p->rho_ratio + p->c_added_mass <= 0.0 ||
-        (p->forces & ~(LBM_FORCE_LIFT | LBM_FORCE_STRESS)))
+        (p->forces & ~(LBM_FORCE_LIFT | LBM_FORCE_STRESS)) ||
+        (p->mapping != LBM_MAP_CELL && p->mapping != LBM_MAP_POINT) ||
+        (p->reaction != LBM_REACTION_DRAG_LIFT && p->reaction != LBM_REACTION_ALL))
         return bfail(b, LBM_ERR_ARG, "parameter out of range");
     if (b->bub.nb > 0 && ((p->forces ^ b->p.forces) & LBM_FORCE_LIFT))
         return bfail(b, LBM_ERR_STATE, "switch lift before lbm_batch_set_bubbles");
     if (b->bub.nb > 0 && p->width_factor != b->p.width_factor)
         return bfail(b, LBM_ERR_STATE, "set width_factor before lbm_batch_set_bubbles");
+    if (b->bub.nb > 0 && p->mapping != b->p.mapping)
+        return bfail(b, LBM_ERR_STATE, "set the mapping before lbm_batch_set_bubbles");
     if (b->dev_ready && p->rho_l != b->p.rho_l)
         return bfail(b, LBM_ERR_STATE, "rho_l is the storage reference; set it before first use");
     b->p = *p;
@@ -489,6 +495,9 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
                 return bfail(b, LBM_ERR_ARG, "bubble %d: diameter out of range", k);
             const double hw = b->p.width_factor * d;
             if (hw > MAX_HALF_WIDTH) return bfail(b, LBM_ERR_ARG, "bubble %d: window too wide", k);
+            if (b->p.mapping == LBM_MAP_POINT && !(hw > 0.5))
+                return bfail(b, LBM_ERR_ARG, "bubble %d: the point-sampled map needs a window "
+                             "half-width above 1/2", k);
             dmax = std::fmax(dmax, d);
             for (int a = 0; a < 3; ++a) {
                 const double x = pos3[3 * k + a];

@@ -80,10 +80,25 @@ __device__ __forceinline__ int f2_ceil_int(F2 a) {
     return (int)c;
 }
 
-// Window normalisation along one axis: the integral of the mapping over the
-// in-box part of [-n, n] (without 15/16), for the two-float coordinate xa; the
-// full 16/15 on a periodic axis.
-__device__ __forceinline__ float axis_norm2(F2 xa, float inv_n, int L, bool periodic) {
+// Window normalisation along one axis: the sum of the axis weights over the
+// in-box cells.  For cell integrals (h > 0) that is the integral of the
+// mapping over the in-box part of [-n, n] (without 15/16), for the two-float
+// coordinate xa, and the full 16/15 on a periodic axis.  For point samples
+// (h < 0) it is the sum of the node samples themselves, evaluated as the
+// weights are (cell_poly of the offset from the anchor cell anc, fraction fr)
+// over the cells within n + 1 of the centre.
+__device__ __forceinline__ float axis_norm(F2 xa, int anc, float fr, float inv_n, float h, int L,
+                                           bool periodic) {
+    if (h < 0.0f) {
+        const int K = (int)ceilf(1.0f / inv_n) + 1;
+        float sum = 0.0f;
+        for (int k = -K; k <= K; ++k) {
+            const int c = anc + k;
+            if (!periodic && (c < 0 || c >= L)) continue;
+            sum += cell_poly(((float)k + 0.5f - fr) * inv_n, h);
+        }
+        return sum;
+    }
     if (periodic) return 16.0f / 15.0f;
     const float lo = (-xa.h - xa.l) * inv_n, hi = (((float)L - xa.h) - xa.l) * inv_n;
     const float a = fmaxf(lo, -1.0f), b = fminf(hi, 1.0f);
@@ -93,15 +108,17 @@ __device__ __forceinline__ float axis_norm2(F2 xa, float inv_n, int L, bool peri
     return (b - a) * (p4 * 0.2f - (b2 + ab + a2) * (2.0f / 3.0f) + 1.0f);
 }
 
-__device__ __forceinline__ void make_record(const F2* xb, float inv_n, const Geo& g,
+__device__ __forceinline__ void make_record(const F2* xb, const BubbleK& K, const Geo& g,
                                             const float* psi, BubbleRec& r) {
+    const float inv_n = K.inv_nf;
     int anc[3];
     float fr[3];
     float norm = 1.0f;
     const int L[3] = {g.nx, g.ny, g.nz};
     for (int a = 0; a < 3; ++a) {
         anc[a] = f2_floor(xb[a], fr[a]);
-        norm *= axis_norm2(xb[a], inv_n, L[a], !(g.walls & (1u << (2 * a))));
+        norm *= axis_norm(xb[a], anc[a], fr[a], inv_n, K.hmap, L[a],
+                          !(g.walls & (1u << (2 * a))));
     }
     const float inv_norm = 1.0f / norm;
     r.ax = anc[0];
@@ -112,7 +129,7 @@ __device__ __forceinline__ void make_record(const F2* xb, float inv_n, const Geo
     r.fy = fr[1];
     r.fz = fr[2];
     r.inv_n = inv_n;
-    r.h = 0.5f * inv_n;
+    r.h = K.hmap;
     r.px = psi[0] * inv_norm;
     r.py = psi[1] * inv_norm;
     r.pz = psi[2] * inv_norm;
@@ -149,6 +166,7 @@ struct Window {
     int lo[3], cnt[3], anc[3];
     float fr[3];
     float norm;
+    float h;  // cell_poly's h: 1/(2n) for cell integrals, -1/(2n) for point samples
     int M;   // nodes in the window
 };
 
@@ -195,6 +213,7 @@ __device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w, int pa
     // A non-finite centre can only come from an unstable liquid.
     if (!(isfinite(xb[0].h) && isfinite(xb[1].h) && isfinite(xb[2].h))) return BUBBLE_NONFINITE;
     w.norm = 1.0f;
+    w.h = in.k.hmap;
     for (int a = 0; a < 3; ++a) {
         const bool periodic = !(g.walls & (1u << (2 * a)));
         int l, h;
@@ -208,7 +227,7 @@ __device__ int bubble_window(const Geo& g, const BubbleIn& in, Window& w, int pa
         w.lo[a] = l;
         w.cnt[a] = min(max(h - l + 1, 0), WINDOW_CELLS_MAX);
         w.anc[a] = f2_floor(xb[a], w.fr[a]);
-        w.norm *= axis_norm2(xb[a], inv_n, L[a], periodic);
+        w.norm *= axis_norm(xb[a], w.anc[a], w.fr[a], inv_n, w.h, L[a], periodic);
     }
     w.M = w.cnt[0] * w.cnt[1] * w.cnt[2];
     return BUBBLE_LIVE;
@@ -229,7 +248,7 @@ __device__ __forceinline__ int wrap_axis(int i, int L) {
 
 __device__ __forceinline__ float window_node(const Geo& g, const Window& w, float inv_n, int m,
                                              int& iw, int& jw, int& kw) {
-    const float hh = 0.5f * inv_n;
+    const float hh = w.h;
     const int rest = div_small(m, w.cnt[0]);
     const int ix = m - rest * w.cnt[0];
     const int iz = div_small(rest, w.cnt[1]);
@@ -248,7 +267,7 @@ __device__ __forceinline__ float window_node(const Geo& g, const Window& w, floa
 // and its wrapped lattice coordinates.
 __device__ __forceinline__ void window_node_lift(const Geo& g, const Window& w, float inv_n,
                                                  int m, int& iw, int& jw, int& kw, float wt[4]) {
-    const float hh = 0.5f * inv_n;
+    const float hh = w.h;
     const int rest = div_small(m, w.cnt[0]);
     const int ix = m - rest * w.cnt[0];
     const int iz = div_small(rest, w.cnt[1]);
@@ -459,10 +478,18 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
         too_fast |= !(fabsf(d) <= (float)GUARD_CELLS);
     }
     if (too_fast) atomicOr(flag, 4);
+    // Reaction: -(F_D + F_L) averaged over the sub-steps (Algorithm 1 step
+    // 6), or -sum F over the interphase forces (Sec. 3.2).  The latter adds
+    // F_S and F_VM = C_A rho_l V_b (D_t u_l - a_k); with m_eff a_k = F_B +
+    // F_D + F_L + F_S + C_A rho_l V_b D_t u_l its sub-step mean is
+    // react_mb (mean F_D + F_L + fvm) - react_ca F_B, fvm = F_S + C_A rho_l
+    // V_b D_t u_l.
     float psi[3];
     const float inv_sub = 1.0f / (float)bc.substeps;
     for (int a = 0; a < 3; ++a) {
-        psi[a] = -fd_sum[a] * inv_sub;
+        psi[a] = bc.reaction_all
+                     ? K.react_ca * fb[a] - K.react_mb * fmaf(fd_sum[a], inv_sub, fvm[a])
+                     : -fd_sum[a] * inv_sub;
         B.xh[3 * b + a] = xb[a].h;
         B.xl[3 * b + a] = xb[a].l;
         B.u[3 * b + a] = u[a];
@@ -487,7 +514,7 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
         ci[a] = min(max(f2_floor(xb[a], fr), 0), L[a] - 1);
     }
     B.cell[b] = (ci[2] * g.ny + ci[1]) * g.nx + ci[0];
-    make_record(xb, K.inv_nf, g, psi, B.rec[b]);
+    make_record(xb, K, g, psi, B.rec[b]);
     // Algorithm 1: the bubble stops once it reaches the top of the liquid.
     if ((g.walls & 0x20) && !f2_lt(xb[2], top[2])) B.active[b] = 0;
 }
@@ -520,6 +547,10 @@ __device__ BubbleK bubble_constants(double d, double n, const BubbleConst& bc) {
     K.cl_f = (float)(eo_d <= 10.0 ? fl : -0.29);
     K.lift_pref = bc.lift ? (float)(bc.rho_l * vol) : 0.0f;
     K.fs_coef_dt = bc.stress ? (float)(bc.rho_l * vol / bc.dt_l) : 0.0f;
+    K.hmap = (float)((bc.point ? -0.5 : 0.5) / n);
+    const double meff_per_vol = bc.rho_b + bc.c_am * bc.rho_l;
+    K.react_ca = (float)(bc.c_am * bc.rho_l / meff_per_vol);
+    K.react_mb = (float)(bc.rho_b / meff_per_vol);
     return K;
 }
 
@@ -1543,7 +1574,7 @@ __global__ void k_bubble_records(Geo g, BubbleDev B) {
     const F2 xb[3] = {F2{B.xh[3 * b], B.xl[3 * b]}, F2{B.xh[3 * b + 1], B.xl[3 * b + 1]},
                       F2{B.xh[3 * b + 2], B.xl[3 * b + 2]}};
     const float psi[3] = {B.psi[3 * b], B.psi[3 * b + 1], B.psi[3 * b + 2]};
-    make_record(xb, B.k[b].inv_nf, g, psi, B.rec[b]);
+    make_record(xb, B.k[b], g, psi, B.rec[b]);
 }
 
 cudaError_t launch_bubble_records(const Geo& g, const BubbleDev& b, cudaStream_t st) {

@@ -99,6 +99,8 @@ BubbleConst bubble_const(const lbm_ctx* c) {
     bc.substeps = c->p.substeps;
     bc.lift = (c->p.forces & LBM_FORCE_LIFT) ? 1 : 0;
     bc.stress = (c->p.forces & LBM_FORCE_STRESS) ? 1 : 0;
+    bc.point = c->p.mapping == LBM_MAP_POINT ? 1 : 0;
+    bc.reaction_all = c->p.reaction == LBM_REACTION_ALL ? 1 : 0;
     return bc;
 }
 
@@ -341,6 +343,8 @@ void lbm_default_params(lbm_params* p) {
     p->substeps = 10;
     p->two_way = 1;
     p->forces = 0;
+    p->mapping = LBM_MAP_CELL;
+    p->reaction = LBM_REACTION_DRAG_LIFT;
 }
 
 void lbm_velocity_set(int* c57, double* w19) {
@@ -417,7 +421,9 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
         !(p->sigma > 0.0) || !(p->c_added_mass >= 0.0) || !(p->drag_scale >= 0.0) ||
         !(p->sn_coeff >= 0.0) || !(p->sn_exp > 0.0) || !(p->width_factor > 0.0) ||
         p->substeps < 1 || p->substeps > 10000 ||
-        (p->forces & ~(LBM_FORCE_LIFT | LBM_FORCE_STRESS)))
+        (p->forces & ~(LBM_FORCE_LIFT | LBM_FORCE_STRESS)) ||
+        (p->mapping != LBM_MAP_CELL && p->mapping != LBM_MAP_POINT) ||
+        (p->reaction != LBM_REACTION_DRAG_LIFT && p->reaction != LBM_REACTION_ALL))
         return fail(c, LBM_ERR_ARG, "parameter out of range");
     if (p->rho_ratio + p->c_added_mass <= 0.0)
         return fail(c, LBM_ERR_ARG, "effective bubble mass must be positive");
@@ -438,6 +444,8 @@ int lbm_set_params(lbm_ctx* c, const lbm_params* p) {
         }
         if (p->width_factor != c->p.width_factor)
             return fail(c, LBM_ERR_STATE, "set width_factor before lbm_set_bubbles");
+        if (p->mapping != c->p.mapping)
+            return fail(c, LBM_ERR_STATE, "set the mapping before lbm_set_bubbles");
     }
     adjoint_free(c);
     if ((p->forces ^ c->p.forces) & LBM_FORCE_LIFT) c->cover_valid = false;   // lists change reach
@@ -542,6 +550,9 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         if (hw > MAX_HALF_WIDTH)
             return fail(c, LBM_ERR_ARG, "bubble %d: window half-width %g exceeds %g", b, hw,
                         MAX_HALF_WIDTH);
+        if (c->p.mapping == LBM_MAP_POINT && !(hw > 0.5))
+            return fail(c, LBM_ERR_ARG, "bubble %d: the point-sampled map needs a window "
+                        "half-width above 1/2 (got %g)", b, hw);
         const double halo = (c->p.forces & LBM_FORCE_LIFT) ? 2.0 : 0.0;
         for (int a = 0; a < 3; ++a) {
             const double x = pos3[3 * b + a];

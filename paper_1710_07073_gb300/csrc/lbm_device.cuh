@@ -222,7 +222,14 @@ __device__ __forceinline__ void gather(const typename Store<ST>::T* __restrict__
 //     = (b - a) [ (b^4 + b^3 a + b^2 a^2 + b a^3 + a^4)/5 - 2 (b^2 + a b + a^2)/3 + 1 ]
 // with a, b clipped to the window [-1, 1] (Eq. 18-19).  The factored form
 // avoids the cancellation of a difference of antiderivatives.
+// A negative h selects the point-sampled map: Z at the node times the cell
+// width, 2|h| (1 - s^2)^2, zero outside the window.
 __device__ __forceinline__ float cell_poly(float s, float h) {
+    if (h < 0.0f) {
+        const float t = fminf(fabsf(s), 1.0f);
+        const float q = fmaf(-t, t, 1.0f);
+        return -2.0f * h * q * q;
+    }
     float a = fmaxf(s - h, -1.0f);
     float b = fminf(s + h, 1.0f);
     if (!(b > a)) return 0.0f;
@@ -230,16 +237,6 @@ __device__ __forceinline__ float cell_poly(float s, float h) {
     float p4 = b2 * b2 + b2 * ab + ab * ab + ab * a2 + a2 * a2;
     float p2 = b2 + ab + a2;
     return (b - a) * (p4 * 0.2f - p2 * (2.0f / 3.0f) + 1.0f);
-}
-
-__device__ __forceinline__ double cell_poly_d(double a, double b) {
-    a = fmax(a, -1.0);
-    b = fmin(b, 1.0);
-    if (!(b > a)) return 0.0;
-    double a2 = a * a, b2 = b * b, ab = a * b;
-    double p4 = b2 * b2 + b2 * ab + ab * ab + ab * a2 + a2 * a2;
-    double p2 = b2 + ab + a2;
-    return (b - a) * (p4 * 0.2 - p2 * (2.0 / 3.0) + 1.0);
 }
 
 // Cell integral of the mapping along one axis for lattice coordinate c, with

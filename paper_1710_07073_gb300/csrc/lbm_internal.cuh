@@ -117,6 +117,13 @@ struct BubbleK {
     float cl_f;
     int cl_tanh;
     float fs_coef_dt;   // rho_l V_b / dt_l for F_S = rho_l V_b D_t u_l (0: off)
+    // Mapping weights (Eq. 19): h = 1/(2n) takes the cell integral of Z,
+    // h = -1/(2n) the point sample at the node (cell_poly).
+    float hmap;
+    // Reaction -sum F (Sec. 3.2): psi = react_ca F_B - react_mb (mean F_D +
+    // F_L + F_S + C_A rho_l V_b D_t u_l), react_ca = C_A rho_l V_b / m_eff,
+    // react_mb = m_b / m_eff.
+    float react_ca, react_mb;
 };
 
 // Bubble state on the device.  A context keeps the centres as two floats
@@ -151,6 +158,8 @@ struct BubbleConst {
     int substeps;
     int lift;             // F_L of Table 1 on (the windows then carry the vorticity halo)
     int stress;           // F_S of Table 1 on
+    int point;            // mapping by point samples of Z instead of cell integrals
+    int reaction_all;     // psi_b = -sum of the interphase forces (Sec. 3.2)
 };
 
 // Values a window sum carries per bubble: the Eq. 20 velocity (3) and, with

@@ -33,6 +33,10 @@ LBM_WALL_ALL_FREE_TOP = 0x7F
 
 LBM_FORCE_LIFT = 0x1
 LBM_FORCE_STRESS = 0x2
+LBM_MAP_CELL = 0
+LBM_MAP_POINT = 1
+LBM_REACTION_DRAG_LIFT = 0
+LBM_REACTION_ALL = 1
 
 LBM_STORE_F32 = 0
 LBM_STORE_F16 = 1
@@ -60,6 +64,8 @@ class lbm_params(ctypes.Structure):
         ("substeps", ctypes.c_int),
         ("two_way", ctypes.c_int),
         ("forces", ctypes.c_int),
+        ("mapping", ctypes.c_int),
+        ("reaction", ctypes.c_int),
     ]
 
 

@@ -38,7 +38,11 @@ def params_for_oracle(col_params, omega):
     return obub.BubbleParams(omega, g=p.g, rho_l=p.rho_l, rho_ratio=p.rho_ratio, sigma=p.sigma,
                              c_added_mass=p.c_added_mass, drag_scale=p.drag_scale,
                              sn_coeff=p.sn_coeff, sn_exp=p.sn_exp, width_factor=p.width_factor,
-                             substeps=p.substeps)
+                             substeps=p.substeps,
+                             lift=bool(p.forces & lbm.LBM_FORCE_LIFT),
+                             stress_gradient=bool(p.forces & lbm.LBM_FORCE_STRESS),
+                             mapping="point" if p.mapping == lbm.LBM_MAP_POINT else "cell",
+                             reaction="all" if p.reaction == lbm.LBM_REACTION_ALL else "drag_lift")
 
 
 def rel_linf(a, b):

@@ -116,3 +116,31 @@ def test_params_forces_bits_checked(libpath):
         assert e.value.code == lbm.LBM_ERR_ARG
     finally:
         lbm.lbm_destroy(h)
+
+
+def test_params_mapping_and_reaction_checked(libpath):
+    # lbm_params.mapping takes LBM_MAP_CELL / LBM_MAP_POINT, .reaction
+    # LBM_REACTION_DRAG_LIFT / LBM_REACTION_ALL; the point-sampled map refuses
+    # windows of half-width 1/2 or less (no node need lie inside them).
+    from paper_1710_07073_gb300 import lbm
+    h = lbm.lbm_create(16, 16, 16, 1.6, lbm.LBM_WALL_ALL)
+    try:
+        p = lbm.lbm_default_params()
+        assert p.mapping == lbm.LBM_MAP_CELL and p.reaction == lbm.LBM_REACTION_DRAG_LIFT
+        for field, bad in (("mapping", 2), ("mapping", -1), ("reaction", 2)):
+            q = lbm.lbm_default_params()
+            setattr(q, field, bad)
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_params(h, q)
+            assert e.value.code == lbm.LBM_ERR_ARG
+        p.mapping = lbm.LBM_MAP_POINT
+        p.reaction = lbm.LBM_REACTION_ALL
+        lbm.lbm_set_params(h, p)
+        got = lbm.lbm_get_params(h)
+        assert got.mapping == 1 and got.reaction == 1
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_bubbles(h, [8.0, 8.0, 8.0], [0, 0, 0], [1.0 / 3.0])   # n = 1/2
+        assert e.value.code == lbm.LBM_ERR_ARG
+        assert "point-sampled" in lbm.lbm_last_error(h)
+    finally:
+        lbm.lbm_destroy(h)
