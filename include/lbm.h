@@ -164,6 +164,41 @@ void lbm_default_params(lbm_params* p);
  * c[3*j + a] is component a of c_j, w[j] its weight.  Either may be NULL. */
 void lbm_velocity_set(int* c57, double* w19);
 
+/* ---- physical units (Appendix A) -------------------------------------------
+ * A physical set-up (SI units) and its lattice: Delta x_lu = Delta t_lu = 1,
+ * so the conversion factors lattice-per-physical are LCF = 1/dx, TCF = 1/dt
+ * and, from rho_pu = rho_lu LCF^3 / MCF, MCF = rho_lu LCF^3 / rho_pu.  A
+ * quantity of dimension m^a s^b kg^c converts as x_lu = x_pu LCF^a TCF^b
+ * MCF^c: lengths by LCF, times by TCF, velocities by LCF/TCF, g by
+ * LCF/TCF^2, kinematic viscosity by LCF^2/TCF, surface tension (kg/s^2) by
+ * MCF/TCF^2. */
+typedef struct lbm_physical {
+    double dx;        /* grid spacing Delta x, m                          */
+    double dt;        /* liquid time step Delta t_l, s                    */
+    double rho_l;     /* liquid density, kg/m^3                           */
+    double rho_b;     /* bubble density, kg/m^3                           */
+    double mu_l;      /* liquid dynamic viscosity, kg/(m s)               */
+    double sigma;     /* surface tension, N/m                             */
+    double g;         /* gravity, m/s^2                                   */
+    double rho_l_lu;  /* liquid density in lattice units (Appendix A: 1)  */
+} lbm_physical;
+
+typedef struct lbm_units {
+    double lcf, tcf, mcf;   /* lattice per physical: length, time, mass     */
+} lbm_units;
+
+/* Convert a physical set-up to lattice units (Appendix A).  Fills *u with
+ * the factors; *p (if not NULL) gets g, rho_l = rho_l_lu, rho_ratio, sigma in
+ * lattice units, the other fields untouched (call lbm_default_params first);
+ * *omega (if not NULL) gets the relaxation frequency of nu_lu = (mu_l/rho_l)
+ * LCF^2/TCF by Eq. 9, omega = 1/(3 nu_lu + 1/2).  Returns LBM_ERR_ARG for a
+ * non-positive or non-finite input or rho_b >= rho_l.  A set-up with water's
+ * viscosity at millimetre cells gives omega just below 2 (Appendix A's 4 mm
+ * case: nu_lu = 4e-6, omega = 1.99995); the conversion does not judge
+ * stability. */
+int lbm_units_from_physical(const lbm_physical* ph, lbm_units* u, lbm_params* p,
+                            double* omega);
+
 /* Create a context for an nx*ny*nz column with relaxation frequency omega
  * (Eq. 9: nu = (1/omega - 1/2)/3; omega must lie in (0, 2)) and the given
  * wall bits, FP32 storage.  The liquid starts at f = f^eq(rho_l, 0)

@@ -358,6 +358,34 @@ void lbm_velocity_set(int* c57, double* w19) {
     }
 }
 
+// Appendix A: lattice-per-physical factors from Delta x_lu = Delta t_lu = 1
+// and rho_pu = rho_lu LCF^3 / MCF; each quantity scales by its dimensions.
+int lbm_units_from_physical(const lbm_physical* ph, lbm_units* u, lbm_params* p,
+                            double* omega) {
+    if (!ph || !u) return LBM_ERR_ARG;
+    const double v[8] = {ph->dx, ph->dt, ph->rho_l, ph->rho_b, ph->mu_l, ph->sigma, ph->g,
+                         ph->rho_l_lu};
+    for (int i = 0; i < 8; ++i)
+        if (!std::isfinite(v[i]) || v[i] < 0.0) return LBM_ERR_ARG;
+    if (!(ph->dx > 0.0 && ph->dt > 0.0 && ph->rho_l > 0.0 && ph->mu_l > 0.0 &&
+          ph->sigma > 0.0 && ph->rho_l_lu > 0.0) || !(ph->rho_b < ph->rho_l))
+        return LBM_ERR_ARG;
+    const double lcf = 1.0 / ph->dx, tcf = 1.0 / ph->dt;
+    const double mcf = ph->rho_l_lu * lcf * lcf * lcf / ph->rho_l;
+    const double nu_lu = ph->mu_l / ph->rho_l * lcf * lcf / tcf;
+    u->lcf = lcf;
+    u->tcf = tcf;
+    u->mcf = mcf;
+    if (p) {
+        p->g = ph->g * lcf / (tcf * tcf);
+        p->rho_l = ph->rho_l_lu;
+        p->rho_ratio = ph->rho_b / ph->rho_l;
+        p->sigma = ph->sigma * mcf / (tcf * tcf);
+    }
+    if (omega) *omega = 1.0 / (3.0 * nu_lu + 0.5);   // Eq. 9
+    return LBM_OK;
+}
+
 int lbm_create_storage(int nx, int ny, int nz, double omega, unsigned walls, int storage,
                        double scale, lbm_ctx** out) {
     if (!out) return LBM_ERR_ARG;

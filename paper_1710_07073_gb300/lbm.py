@@ -69,6 +69,15 @@ class lbm_params(ctypes.Structure):
     ]
 
 
+class lbm_physical(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("dx", "dt", "rho_l", "rho_b", "mu_l", "sigma", "g", "rho_l_lu")]
+
+
+class lbm_units(ctypes.Structure):
+    _fields_ = [("lcf", ctypes.c_double), ("tcf", ctypes.c_double), ("mcf", ctypes.c_double)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -89,6 +98,7 @@ def lib():
     sig = {
         "lbm_default_params": (None, [P(lbm_params)]),
         "lbm_velocity_set": (None, [P(i), P(d)]),
+        "lbm_units_from_physical": (i, [P(lbm_physical), P(lbm_units), P(lbm_params), P(d)]),
         "lbm_create": (i, [i, i, i, d, u, P(vp)]),
         "lbm_create_storage": (i, [i, i, i, d, u, i, d, P(vp)]),
         "lbm_destroy": (None, [vp]),
@@ -185,6 +195,25 @@ def lbm_velocity_set():
     w = np.zeros(19, dtype=np.float64)
     lib().lbm_velocity_set(_iptr(c), _dptr(w))
     return c.reshape(19, 3), w
+
+
+def lbm_units_from_physical(dx, dt, rho_l=1000.0, rho_b=1.0, mu_l=1e-3, sigma=0.073, g=9.81,
+                            rho_l_lu=1.0, params=None):
+    """Appendix A conversion (defaults: Table 3's water and air).  Returns
+    (units, params, omega): units with lcf, tcf, mcf; ``params`` (a copy of
+    the given lbm_params, else the defaults) with g, rho_l, rho_ratio and sigma
+    in lattice units; omega from the lattice viscosity (Eq. 9)."""
+    ph = lbm_physical(dx, dt, rho_l, rho_b, mu_l, sigma, g, rho_l_lu)
+    u = lbm_units()
+    p = lbm_default_params()
+    if params is not None:
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(params), ctypes.sizeof(lbm_params))
+    om = ctypes.c_double(0.0)
+    rc = lib().lbm_units_from_physical(ctypes.byref(ph), ctypes.byref(u), ctypes.byref(p),
+                                       ctypes.byref(om))
+    if rc != LBM_OK:
+        raise LbmError(rc, "physical set-up out of range")
+    return u, p, om.value
 
 
 def lbm_create(nx, ny, nz, omega, walls=LBM_WALL_ALL):

@@ -11,3 +11,12 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def libpath():
+    """The built liblbm.so (built here if missing; loading needs no GPU)."""
+    from paper_1710_07073_gb300 import build, lbm
+    if not os.path.exists(lbm.LIB_PATH):
+        build.build()
+    return lbm.LIB_PATH

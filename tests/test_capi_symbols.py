@@ -20,14 +20,6 @@ def _declared():
     return names
 
 
-@pytest.fixture(scope="module")
-def libpath():
-    from paper_1710_07073_gb300 import build, lbm
-    if not os.path.exists(lbm.LIB_PATH):
-        build.build()
-    return lbm.LIB_PATH
-
-
 def test_header_declares_boundary():
     names = _declared()
     for required in ("lbm_create", "lbm_set_bubbles", "lbm_step", "lbm_get_fields",
