@@ -342,7 +342,8 @@ def run_batch(args, wl):
     lbm.lbm_batch_set_bubbles(b.h, [1] * len(cols), wl["pos"].reshape(-1), wl["vel"].reshape(-1),
                               wl["diam"])
     S = lbm.lbm_batch_sites(b.h)
-    depth, grid = lbm.lbm_batch_tune(b.h, 8)
+    lbm.lbm_batch_tune(b.h, 8)
+    planes, depth, grid = lbm.lbm_batch_launch_shape(b.h)
     lbm.lbm_batch_step(b.h, args.warmup)
     sampler = ClockSampler(local)
     sampler.start()
@@ -416,12 +417,12 @@ def run_batch(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": wl["name"], "columns": len(cols), "sites": S, "storage": storage,
-                   "tuned": {"depth": depth, "grid": grid},
+                   "tuned": {"cta_tile": [32, 4, planes], "depth": depth, "grid": grid},
                    "l2": "inputs larger than L2 (%.2f GB populations), no flush" % (
                        19 * S * (4 if storage == "f32" else 2) / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
-                     "kernel": "k_collide_batch<%s>" % storage,
+                     "kernel": "k_collide_batch<%d,%d>" % (STORAGES[storage], planes),
                      "algorithmic_bytes_per_launch": bytes_per_site * S,
                      "avg_launch_ms": round(avg_kernel_s * 1e3, 5), "launches": k_n,
                      "peak_kind": peak_kind, "timed": "separate per-launch pass after the graph run"},

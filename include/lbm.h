@@ -364,11 +364,22 @@ int lbm_batch_set_bubbles(lbm_batch* b, const int* counts, const double* pos3, c
                           const double* diam);
 /* Advance every column by nsteps coupled steps (graph replays). */
 int lbm_batch_step(lbm_batch* b, int nsteps);
-/* Autotuner: times each candidate launch shape -- work-item depth in
- * z-blocks {1, 2, 4, 8} x persistent CTAs per SM -- for trial_steps steps on
- * this batch, keeps the fastest, and restores the state the trials advanced.
- * Either output may be NULL. */
+/* Autotuner: times each candidate launch shape -- CTA tile 32 x 4 x P nodes
+ * with P in {1, 2, 4} z-planes, work-item depth in z-blocks {1, 2, 4, 8},
+ * and half, one or two times the resident CTAs per SM -- for trial_steps
+ * steps on this batch, keeps the fastest, and restores the state the trials
+ * advanced.  Results do not depend on the shape (bit for bit).  Either output
+ * may be NULL; lbm_batch_launch_shape reads the whole shape. */
 int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out);
+/* The batch's current launch shape: z-planes per CTA (the CTA tile is
+ * 32 x 4 x planes nodes), z-blocks per work item and persistent CTAs.  Before
+ * lbm_batch_tune: planes 2, depth 2 and a grid of the resident CTAs (set on
+ * first device use).  Any output may be NULL. */
+int lbm_batch_launch_shape(const lbm_batch* b, int* planes, int* depth, int* grid);
+/* Fix the launch shape without tuning: planes 1, 2 or 4, depth 1..64, grid
+ * the persistent CTAs (0: the resident CTAs per SM times the SM count).
+ * LBM_ERR_ARG otherwise. */
+int lbm_batch_set_launch_shape(lbm_batch* b, int planes, int depth, int grid);
 /* Fields of one column (as lbm_get_fields). */
 int lbm_batch_get_fields(lbm_batch* b, int col, double* rho, double* u3);
 /* All bubbles, column after column (as lbm_get_bubbles). */

@@ -4,8 +4,9 @@
 // bubble update of every column (with the binning fused behind it) and one
 // persistent collide-stream launch over all columns' work items.  Pairs of
 // steps are captured once into a CUDA graph and replayed.  An autotuner picks
-// the work-item depth and the persistent grid size by timing candidates on
-// the batch itself, with the state saved and restored around the trials.
+// the CTA tile shape (z-planes per CTA), the work-item depth and the
+// persistent grid size by timing candidates on the batch itself, with the
+// state saved and restored around the trials.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -53,8 +54,10 @@ struct lbm_batch {
     SmallBins small{};
 
     // launch shape (autotuned)
-    int depth = 2;      // z-blocks per work item
-    int grid = 0;       // persistent CTAs
+    int planes = SWEEP_PZ;   // z-planes per CTA: the CTA tile is 32 x 4 x planes nodes
+    int depth = 2;           // z-blocks (of `planes` planes) per work item
+    int grid = 0;            // persistent CTAs
+    bool grid_fixed = false; // grid set by lbm_batch_set_launch_shape
     bool tuned = false;
 
     cudaGraphExec_t graph = nullptr;
@@ -144,7 +147,7 @@ BubbleConst batch_bubble_const(const lbm_batch* b) {
 void layout_columns(lbm_batch* b) {
     unsigned long long off = 0;
     int tile = 0, item = 0;
-    const int pz = batch_z_block();
+    const int pz = b->planes;
     b->cols.resize(b->ncols);
     for (int c = 0; c < b->ncols; ++c) {
         BatchColumn& col = b->cols[c];
@@ -238,7 +241,7 @@ int ensure_device(lbm_batch* b) {
     int dev = 0, sms = 0;
     LBM_BCUDA(cudaGetDevice(&dev), "device");
     LBM_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    b->grid = sms * pair_min_blocks(b->storage);
+    if (!b->grid_fixed) b->grid = sms * batch_min_blocks(b->storage, b->planes);
     b->dev_ready = true;
     return LBM_OK;
 }
@@ -271,7 +274,8 @@ int enqueue_step(lbm_batch* b, bool time_it) {
     const bool two_way = bubbles && b->p.two_way;
     TileLists none{nullptr, nullptr, nullptr, 0};
     LBM_BCUDA(launch_collide_batch(b->storage, b->f[b->cur], b->f[b->cur ^ 1], b->cols_d, b->ncols,
-                                   b->total_items, b->depth, b->grid, b->work_counter,
+                                   b->total_items, b->depth, b->grid, b->planes,
+                                   b->work_counter,
                                    two_way ? tl : none, b->bub.rec, b->bub.nb, b->flag_d, s),
               "batch collide-stream");
     ++b->launches;
@@ -630,37 +634,47 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out)
     int dev = 0, sms = 0;
     LBM_BCUDA(cudaGetDevice(&dev), "device");
     LBM_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    const int maxb = pair_min_blocks(b->storage);
+    // Candidates: CTA tiles of 32 x 4 x {1, 2, 4} nodes; work items of
+    // {1, 2, 4, 8} z-blocks; half, one and two times the resident CTAs per SM
+    // the kernel is compiled for.  Work items span the same planes whatever
+    // the tile, so only the hand-out granularity and the CTA shape change.
+    const int planes_c[] = {1, 2, 4};
     const int depths[] = {1, 2, 4, 8};
-    const int per_sm[] = {maxb / 2, maxb, 2 * maxb};
     cudaEvent_t t0, t1;
     LBM_BCUDA(cudaEventCreate(&t0), "event");
     LBM_BCUDA(cudaEventCreate(&t1), "event");
     float best = 1e30f;
-    int best_depth = b->depth, best_grid = b->grid;
+    int best_planes = b->planes, best_depth = b->depth, best_grid = b->grid;
     const bool timing = b->timing;
     b->timing = false;
-    for (int d : depths) {
-        for (int k : per_sm) {
-            b->depth = d;
-            b->grid = sms * k;
-            layout_columns(b);
-            rc = upload_columns(b);
-            if (!rc) rc = build_graph(b);
-            if (!rc) rc = run_steps(b, 2);   // warm
-            if (rc) break;
-            cudaEventRecord(t0, s);
-            rc = run_steps(b, trial_steps);
-            cudaEventRecord(t1, s);
-            if (rc) break;
-            LBM_BCUDA(cudaEventSynchronize(t1), "trial");
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, t0, t1);
-            if (ms < best) {
-                best = ms;
-                best_depth = d;
-                best_grid = b->grid;
+    for (int pl : planes_c) {
+        const int maxb = batch_min_blocks(b->storage, pl);
+        const int per_sm[] = {maxb / 2, maxb, 2 * maxb};
+        for (int d : depths) {
+            for (int k : per_sm) {
+                b->planes = pl;
+                b->depth = d;
+                b->grid = sms * k;
+                layout_columns(b);
+                rc = upload_columns(b);
+                if (!rc) rc = build_graph(b);
+                if (!rc) rc = run_steps(b, 2);   // warm
+                if (rc) break;
+                cudaEventRecord(t0, s);
+                rc = run_steps(b, trial_steps);
+                cudaEventRecord(t1, s);
+                if (rc) break;
+                LBM_BCUDA(cudaEventSynchronize(t1), "trial");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (ms < best) {
+                    best = ms;
+                    best_planes = pl;
+                    best_depth = d;
+                    best_grid = b->grid;
+                }
             }
+            if (rc) break;
         }
         if (rc) break;
     }
@@ -668,6 +682,7 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out)
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     // Restore the state and keep the winner.
+    b->planes = best_planes;
     b->depth = best_depth;
     b->grid = best_grid;
     layout_columns(b);
@@ -691,6 +706,39 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, int* depth_out, int* grid_out)
     b->tuned = true;
     if (depth_out) *depth_out = best_depth;
     if (grid_out) *grid_out = best_grid;
+    return LBM_OK;
+}
+
+int lbm_batch_set_launch_shape(lbm_batch* b, int planes, int depth, int grid) {
+    if (!b) return LBM_ERR_ARG;
+    if ((planes != 1 && planes != 2 && planes != 4) || depth < 1 || depth > 64 || grid < 0 ||
+        grid > (1 << 20))
+        return bfail(b, LBM_ERR_ARG, "launch shape out of range (planes 1, 2 or 4)");
+    b->planes = planes;
+    b->depth = depth;
+    if (grid > 0) {
+        b->grid = grid;
+    } else if (b->dev_ready) {
+        int dev = 0, sms = 0;
+        LBM_BCUDA(cudaGetDevice(&dev), "device");
+        LBM_BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+        b->grid = sms * batch_min_blocks(b->storage, planes);
+    }
+    if (b->dev_ready) {
+        layout_columns(b);
+        int rc = upload_columns(b);
+        if (rc) return rc;
+    }
+    drop_graph(b);
+    b->grid_fixed = grid > 0;
+    return LBM_OK;
+}
+
+int lbm_batch_launch_shape(const lbm_batch* b, int* planes, int* depth, int* grid) {
+    if (!b) return LBM_ERR_ARG;
+    if (planes) *planes = b->planes;
+    if (depth) *depth = b->depth;
+    if (grid) *grid = b->grid;
     return LBM_OK;
 }
 

@@ -460,10 +460,10 @@ __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __re
     return Force2{Fx, Fy, Fz};
 }
 
-// One CTA's block of the sweep: x-pairs of 32 nodes, TY rows, PZ planes at
+// One CTA's block of the sweep: x-pairs of 32 nodes, TY rows, PZV planes at
 // block coordinates (bx, by, bz).  `srec` is the CTA's staging of bubble
 // records; every thread of the CTA must call this with the same block.
-template <int ST, bool TAB>
+template <int ST, bool TAB, int PZV = PZ>
 __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restrict__ fin,
                                             typename Store<ST>::T* __restrict__ fout,
                                             const Geo& g, const CollideParams& cp,
@@ -474,15 +474,16 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
                                             int* __restrict__ flag, int bx, int by, int bz,
                                             BubbleRec* srec, const unsigned* safe = nullptr,
                                             unsigned epoch = 0, bool lead = false) {
+    static_assert(TZ % PZV == 0 && (!TAB || PZV == PZ), "a block lies in one tile layer");
     const int x0 = bx * TX + 2 * threadIdx.x;
     const int y = by * TY + threadIdx.y;
-    const int z = bz * PZ + threadIdx.z;
+    const int z = bz * PZV + threadIdx.z;
     const bool active = (x0 < g.nx) && (y < g.ny) && (z < g.nz);
     // Inactive threads gather at a valid node and store nothing.
     const int xa = active ? x0 : 0;
     const int ya = min(y, g.ny - 1), za = min(z, g.nz - 1);
 
-    const int t = (((bz * PZ) / TZ) * g.nty + by) * g.ntx + bx;
+    const int t = (((bz * PZV) / TZ) * g.nty + by) * g.ntx + bx;
     // Read before the population loads: in plain stream order the tile count;
     // overlapped with the bubble update, the guard tag of this z layer (written
     // by the update before, which has completed).  The launch's first CTA
@@ -491,7 +492,7 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     bool skip = false;
     if (tile_count != nullptr) {
         if (safe == nullptr) n_t = __ldcg(tile_count + t);
-        else skip = !lead && __ldcg(safe + (bz * PZ) / TZ) == epoch;
+        else skip = !lead && __ldcg(safe + (bz * PZV) / TZ) == epoch;
     }
 
     const unsigned S = (unsigned)g.S;
@@ -570,8 +571,8 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
 // ---------------------------------------------------------------------------
 constexpr int MAX_BATCH_COLUMNS = 256;
 
-template <int ST>
-__global__ void __launch_bounds__(PX * TY * PZ, PairOccupancy<ST>::kMinBlocks)
+template <int ST, int PZV>
+__global__ void __launch_bounds__(PX * TY * PZV, PairOccupancy<ST>::kMinBlocks * PZ / PZV)
 k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
                 typename Store<ST>::T* __restrict__ fout, const BatchColumn* __restrict__ cols,
                 int ncols, int total_items, int depth, int* __restrict__ work_counter,
@@ -582,7 +583,7 @@ k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
     __shared__ int s_item_base[MAX_BATCH_COLUMNS + 1];
     __shared__ int s_item;
     const int tid = (threadIdx.z * TY + threadIdx.y) * PX + threadIdx.x;
-    for (int c = tid; c <= ncols; c += PX * TY * PZ)
+    for (int c = tid; c <= ncols; c += PX * TY * PZV)
         s_item_base[c] = c < ncols ? cols[c].item_base : total_items;
     for (;;) {
         __syncthreads();
@@ -602,9 +603,9 @@ k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
         const int rest = local / col.g.ntx;
         const int by = rest % col.g.nty;
         const int bz0 = (rest / col.g.nty) * depth;
-        const int nbz = (col.g.nz + PZ - 1) / PZ;
+        const int nbz = (col.g.nz + PZV - 1) / PZV;
         for (int bz = bz0; bz < min(bz0 + depth, nbz); ++bz)
-            sweep_block<ST, false>(fin + col.pop_offset, fout + col.pop_offset, col.g, col.cp,
+            sweep_block<ST, false, PZV>(fin + col.pop_offset, fout + col.pop_offset, col.g, col.cp,
                             tile_start + col.tile_base, tile_count + col.tile_base, items, cap,
                             recs, nb, flag, bx, by, bz, srec);
     }
@@ -612,36 +613,36 @@ k_collide_batch(const typename Store<ST>::T* __restrict__ fin,
 
 cudaError_t launch_collide_batch(int storage, const void* fin, void* fout,
                                  const BatchColumn* cols, int ncols, int total_items, int depth,
-                                 int grid, int* work_counter, const TileLists& tl,
+                                 int grid, int planes, int* work_counter, const TileLists& tl,
                                  const BubbleRec* recs, int nb, int* flag, cudaStream_t st) {
     if (ncols > MAX_BATCH_COLUMNS) return cudaErrorInvalidValue;
-    dim3 block(PX, TY, PZ);
-    switch (storage) {
-        case 0:
-            k_collide_batch<0><<<grid, block, 0, st>>>((const float*)fin, (float*)fout, cols, ncols,
-                                                       total_items, depth, work_counter, tl.start,
-                                                       tl.count, tl.items, tl.cap, recs, nb, flag);
-            break;
-        case 1:
-            k_collide_batch<1><<<grid, block, 0, st>>>((const __half*)fin, (__half*)fout, cols,
-                                                       ncols, total_items, depth, work_counter,
-                                                       tl.start, tl.count, tl.items, tl.cap, recs,
-                                                       nb, flag);
-            break;
+    switch (storage * 8 + planes) {
+#define LBM_LAUNCH_BATCH(SI, PV, T)                                                               \
+    case SI * 8 + PV:                                                                             \
+        k_collide_batch<SI, PV><<<grid, dim3(PX, TY, PV), 0, st>>>(                               \
+            (const T*)fin, (T*)fout, cols, ncols, total_items, depth, work_counter, tl.start,    \
+            tl.count, tl.items, tl.cap, recs, nb, flag);                                         \
+        break;
+        LBM_LAUNCH_BATCH(0, 1, float)
+        LBM_LAUNCH_BATCH(0, 2, float)
+        LBM_LAUNCH_BATCH(0, 4, float)
+        LBM_LAUNCH_BATCH(1, 1, __half)
+        LBM_LAUNCH_BATCH(1, 2, __half)
+        LBM_LAUNCH_BATCH(1, 4, __half)
+        LBM_LAUNCH_BATCH(2, 1, __nv_bfloat16)
+        LBM_LAUNCH_BATCH(2, 2, __nv_bfloat16)
+        LBM_LAUNCH_BATCH(2, 4, __nv_bfloat16)
+#undef LBM_LAUNCH_BATCH
         default:
-            k_collide_batch<2><<<grid, block, 0, st>>>(
-                (const __nv_bfloat16*)fin, (__nv_bfloat16*)fout, cols, ncols, total_items, depth,
-                work_counter, tl.start, tl.count, tl.items, tl.cap, recs, nb, flag);
-            break;
+            return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-int batch_block_threads() { return PX * TY * PZ; }
 int sweep_z_blocks(int nz) { return (nz + PZ - 1) / PZ; }
-int batch_z_block() { return PZ; }
-int pair_min_blocks(int storage) {
-    return storage == 0 ? PairOccupancy<0>::kMinBlocks : PairOccupancy<1>::kMinBlocks;
+int batch_min_blocks(int storage, int planes) {
+    const int k = storage == 0 ? PairOccupancy<0>::kMinBlocks : PairOccupancy<1>::kMinBlocks;
+    return k * PZ / planes;
 }
 
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,

@@ -355,7 +355,7 @@ cudaError_t launch_totals(int storage, const void* f, const Geo& g, const Collid
                           double* partials, int npartials, double* out4, cudaStream_t st);
 cudaError_t launch_collide_batch(int storage, const void* fin, void* fout,
                                  const BatchColumn* cols, int ncols, int total_items, int depth,
-                                 int grid, int* work_counter, const TileLists& tl,
+                                 int grid, int planes, int* work_counter, const TileLists& tl,
                                  const BubbleRec* recs, int nb, int* flag, cudaStream_t st);
 cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* cols,
                                  const int* bubble_col, const BubbleDev& b, const BubbleConst& bc,
@@ -363,9 +363,9 @@ cudaError_t launch_bubbles_batch(int storage, const void* f, const BatchColumn* 
 cudaError_t launch_bubble_constants_batch(const BubbleDev& b, const BubbleConst& bc,
                                           const double* col_nu, const int* bubble_col,
                                           cudaStream_t st);
-int batch_block_threads();
-int batch_z_block();
-int pair_min_blocks(int storage);
+// Resident CTAs per SM the batch sweep is compiled for, with `planes` z-planes
+// per CTA (1, 2 or 4; the same threads per SM for each).
+int batch_min_blocks(int storage, int planes);
 int totals_partials(const Geo& g);
 int scan_blocks(int T);
 

@@ -130,6 +130,8 @@ def lib():
         "lbm_batch_set_bubbles": (i, [vp, P(i), P(d), P(d), P(d)]),
         "lbm_batch_step": (i, [vp, i]),
         "lbm_batch_tune": (i, [vp, i, P(i), P(i)]),
+        "lbm_batch_launch_shape": (i, [vp, P(i), P(i), P(i)]),
+        "lbm_batch_set_launch_shape": (i, [vp, i, i, i]),
         "lbm_batch_get_fields": (i, [vp, i, P(d), P(d)]),
         "lbm_batch_get_bubbles": (i, [vp, i, P(i), P(d), P(d), P(d), P(d), P(i)]),
         "lbm_batch_sites": (ll, [vp]),
@@ -466,6 +468,18 @@ def lbm_batch_tune(b, trial_steps=10):
     grid = ctypes.c_int(0)
     _bcheck(b, lib().lbm_batch_tune(b, int(trial_steps), ctypes.byref(depth), ctypes.byref(grid)))
     return depth.value, grid.value
+
+
+def lbm_batch_set_launch_shape(b, planes, depth, grid=0):
+    _bcheck(b, lib().lbm_batch_set_launch_shape(b, int(planes), int(depth), int(grid)))
+
+
+def lbm_batch_launch_shape(b):
+    """(planes per CTA, z-blocks per work item, persistent CTAs)."""
+    planes, depth, grid = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _bcheck(b, lib().lbm_batch_launch_shape(b, ctypes.byref(planes), ctypes.byref(depth),
+                                            ctypes.byref(grid)))
+    return planes.value, depth.value, grid.value
 
 
 def lbm_batch_get_fields(b, col, sites, rho=True, u=True, out_rho=None, out_u=None):

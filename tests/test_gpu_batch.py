@@ -93,8 +93,23 @@ def test_tuning_restores_state_and_keeps_results():
     lbm.lbm_batch_step(b.h, 6)
     depth, grid = lbm.lbm_batch_tune(b.h, 4)
     assert depth in (1, 2, 4, 8) and grid > 0
+    planes, depth2, grid2 = lbm.lbm_batch_launch_shape(b.h)
+    assert planes in (1, 2, 4) and (depth2, grid2) == (depth, grid)
     lbm.lbm_batch_step(b.h, 14)
     _compare_exact(b, counts, _single_runs(20))
+
+
+@pytest.mark.parametrize("storage,scale", [(lbm.LBM_STORE_F32, 1.0), (lbm.LBM_STORE_F16, 256.0)])
+def test_every_tile_shape_equals_single_columns(storage, scale):
+    # The tuner's candidates -- 32 x 4 x {1, 2, 4} node tiles, any depth and
+    # grid -- give the same bits: the shape changes only who computes a node.
+    ref = _single_runs(12, storage, scale)
+    for planes in (1, 2, 4):
+        b, counts = _batch(storage, scale)
+        lbm.lbm_batch_set_launch_shape(b.h, planes, 3, 152 * planes)
+        assert lbm.lbm_batch_launch_shape(b.h) == (planes, 3, 152 * planes)
+        lbm.lbm_batch_step(b.h, 12)
+        _compare_exact(b, counts, ref)
 
 
 def test_batch_column_against_oracle():
