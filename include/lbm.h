@@ -316,13 +316,16 @@ int lbm_get_kernel_time(lbm_ctx* ctx, double* ms, int* launches);
  *                    initial populations f = f^eq(rho, u0) as lbm_set_fields
  *                    sets them (NULL to skip).
  * Wall contacts of the bubble (clamped centre) and the stop at the top are
- * treated as fixed switches.  Needs FP32 storage, 1..64 bubbles.  After the
+ * treated as fixed switches.  Needs FP32 storage, 1..256 bubbles.  After the
  * backward the context is back at the state the forward ended in.  Any call
  * that changes the state between the two (lbm_step, lbm_set_*) discards the
  * record; lbm_adj_backward then returns LBM_ERR_STATE.  A free-slip top
  * (LBM_TOP_FREE_SLIP), the optional forces (lbm_params.forces), point-sampled
  * mapping and the -sum F reaction are not covered: lbm_adj_forward returns
  * LBM_ERR_STATE.
+ * Each reverse step runs the bubbles' spreading adjoint and sub-step reverse
+ * (a CTA per bubble) on a second, library-owned stream alongside the per-node
+ * sweep, and joins them through events before the interpolation adjoint.
  * Memory: one state per
  * checkpoint plus checkpoint_every states during the backward.  With kernel
  * timing on (lbm_set_kernel_timing), lbm_adj_backward times each launch of

@@ -16,7 +16,12 @@
 // The reverse step (step n, newest first):
 //   k_adj_liquid    Lambda^n = C_f^T S^T Lambda^{n+1} per node (transposed
 //                   streaming with bounce-back, linearised forced BGK);
-//   k_adj_bubbles   per bubble: spreading adjoint (Lambda_psi, Lambda_x^{n+1},
+//   k_adj_bubbles_ab (a CTA per bubble, on a second stream alongside
+//                   k_adj_liquid: both read only Lambda^{n+1} and f^n)
+//                   spreading adjoint and the reverse of the sub-steps;
+//   k_adj_bubbles_c (after both, one CTA, bubbles in order)
+//                   the interpolation adjoint.
+//   In all:         per bubble: spreading adjoint (Lambda_psi, Lambda_x^{n+1},
 //                   Lambda_n from the force adjoint at the window nodes),
 //                   reverse of the sub-steps, interpolation adjoint (adds to
 //                   Lambda^n at the window nodes, Lambda_x^n, Lambda_n).
@@ -32,7 +37,7 @@ using namespace lbm;
 
 namespace {
 
-constexpr int ADJ_MAX_BUBBLES = 64;
+constexpr int ADJ_MAX_BUBBLES = 256;
 constexpr int ADJ_THREADS = 256;
 constexpr int ADJ_MAX_SUB = 64;
 
@@ -257,14 +262,18 @@ __device__ __forceinline__ void force_at(const Geo& g, const BubbleRec* recs, co
         float rr[3] = {(float)(x - r.ax) + 0.5f - r.fx, (float)(y - r.ay) + 0.5f - r.fy,
                        (float)(z - r.az) + 0.5f - r.fz};
         const int L[3] = {g.nx, g.ny, g.nz};
-        float w = 1.0f;
+        bool outside = false;
         for (int a = 0; a < 3; ++a) {
             if (!(g.walls & (1u << (2 * a)))) {
                 if (rr[a] > 0.5f * L[a]) rr[a] -= (float)L[a];
                 else if (rr[a] < -0.5f * L[a]) rr[a] += (float)L[a];
             }
-            w *= cell_poly(rr[a] * r.inv_n, r.h);
+            // cell_poly is zero once the cell [s - h, s + h] is outside [-1, 1]
+            outside = outside || fabsf(rr[a] * r.inv_n) >= 1.0f + r.h;
         }
+        if (outside) continue;
+        float w = 1.0f;
+        for (int a = 0; a < 3; ++a) w *= cell_poly(rr[a] * r.inv_n, r.h);
         F[0] = fmaf(w, r.px, F[0]);
         F[1] = fmaf(w, r.py, F[1]);
         F[2] = fmaf(w, r.pz, F[2]);
@@ -407,31 +416,33 @@ struct SubRec {
     int xclamp[3], uclamp[3];
 };
 
-// All bubbles of one reverse step, one after another in one CTA.
+// Phases A and B of one reverse step, a CTA per bubble (blockIdx.x).  They
+// read f^n, Lambda^{n+1} and the step's snapshots only, so they run alongside
+// k_adj_liquid; each CTA writes its own bubble's adjoint state, diameter
+// gradient, drag-scale gradient part and interpolation seed lul_out.
 __global__ void __launch_bounds__(ADJ_THREADS)
-k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
-              float* __restrict__ lam, Geo g, CollideParams cp, const BubbleSnap* __restrict__ pre,
-              const BubbleSnap* __restrict__ post, const double* __restrict__ diam, int nb,
-              AdjConst ac, BubbleAdj* __restrict__ adj, double* __restrict__ grad_sD,
-              double* __restrict__ grad_d, double loss_seed) {
+k_adj_bubbles_ab(const float* __restrict__ fn, const float* __restrict__ lam_next, Geo g,
+                 CollideParams cp, const BubbleSnap* __restrict__ pre,
+                 const BubbleSnap* __restrict__ post, const double* __restrict__ diam, int nb,
+                 AdjConst ac, BubbleAdj* __restrict__ adj, double* __restrict__ grad_sD,
+                 double* __restrict__ grad_d, double* __restrict__ lul_out, double loss_seed) {
     __shared__ BubbleRec srec[ADJ_MAX_BUBBLES];
     __shared__ int sspread[ADJ_MAX_BUBBLES];
     __shared__ double shn[ADJ_THREADS / 32][8];
-    __shared__ double s_lul[3];
     __shared__ SubRec sub[ADJ_MAX_SUB];
     const int tid = threadIdx.x;
-    for (int b = tid; b < nb; b += blockDim.x) {
-        srec[b] = post[b].rec;
-        sspread[b] = ac.two_way ? post[b].active : 0;
+    const int b = blockIdx.x;
+    if (!pre[b].active) {
+        // Not updated this step: its adjoint state passes through unchanged.
+        if (tid == 0 && loss_seed != 0.0) adj[b].lu[2] += loss_seed;
+        return;
+    }
+    for (int k = tid; k < nb; k += blockDim.x) {
+        srec[k] = post[k].rec;
+        sspread[k] = ac.two_way ? post[k].active : 0;
     }
     __syncthreads();
-    for (int b = 0; b < nb; ++b) {
-        if (!pre[b].active) {
-            // Not updated this step: its adjoint state passes through unchanged.
-            if (tid == 0 && loss_seed != 0.0) adj[b].lu[2] += loss_seed;
-            __syncthreads();
-            continue;
-        }
+    {
         const double d = diam[b];
         const double n = ac.width_factor * d;
 
@@ -614,20 +625,36 @@ k_adj_bubbles(const float* __restrict__ fn, const float* __restrict__ lam_next,
             const double gdd = lP * dP + lkdt * dkdt + lfb * dfb + lA0 * dA0 + lB * dBv + lE * dE +
                                ld_re + lCf * dCf + gn * ac.width_factor;
             grad_d[b] += gdd;
-            *grad_sD += lP * P / ac.drag_scale;
+            grad_sD[b] += lP * P / ac.drag_scale;   // summed over bubbles at the end
             for (int c = 0; c < 3; ++c) {
                 adj[b].lx[c] = lx[c];
                 adj[b].lu[c] = lu[c];
                 adj[b].lq[c] = lq[c];
-                s_lul[c] = lul[c];
+                lul_out[3 * b + c] = lul[c];
             }
         }
-        __syncthreads();
+    }
+}
+
+// Phase C of one reverse step, after k_adj_liquid and k_adj_bubbles_ab: the
+// interpolation adjoint of every active bubble, one bubble after another in
+// one CTA (windows may overlap, and Lambda^n is updated in place in bubble
+// order).
+__global__ void __launch_bounds__(ADJ_THREADS)
+k_adj_bubbles_c(const float* __restrict__ fn, float* __restrict__ lam, Geo g, CollideParams cp,
+                const BubbleSnap* __restrict__ pre, const double* __restrict__ diam, int nb,
+                AdjConst ac, BubbleAdj* __restrict__ adj, double* __restrict__ grad_d,
+                const double* __restrict__ lul_in) {
+    __shared__ double shn[ADJ_THREADS / 32][8];
+    const int tid = threadIdx.x;
+    for (int b = 0; b < nb; ++b) {
+        if (!pre[b].active) continue;
+        const double n = ac.width_factor * diam[b];
         // -- Phase C: interpolation adjoint at x^n --------------------------------
         {
             Window w;
             make_window(g, pre[b].x, n, w);
-            const double lul[3] = {s_lul[0], s_lul[1], s_lul[2]};
+            const double lul[3] = {lul_in[3 * b], lul_in[3 * b + 1], lul_in[3 * b + 2]};
             double gx0[3] = {0.0, 0.0, 0.0}, gn0 = 0.0;
             const int M = w.cnt[0] * w.cnt[1] * w.cnt[2];
             for (int m = tid; m < M; m += blockDim.x) {
@@ -840,7 +867,11 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     BubbleSnap* seg_post = (BubbleSnap*)dalloc(c, sizeof(BubbleSnap) * (size_t)K * nb);
     float* lam[2] = {(float*)dalloc(c, fb), (float*)dalloc(c, fb)};
     BubbleAdj* adj = (BubbleAdj*)dalloc(c, sizeof(BubbleAdj) * nb);
-    double* grads = (double*)dalloc(c, sizeof(double) * (1 + nb));
+    // grads[0, nb): dL/dd_b; grads[nb, 2 nb): each bubble's part of dL/ds_D
+    // (summed over the bubbles in order at the end); lul: the interpolation
+    // seed phase B hands to phase C.
+    double* grads = (double*)dalloc(c, sizeof(double) * 2 * (size_t)nb);
+    double* lul = (double*)dalloc(c, sizeof(double) * 3 * (size_t)nb);
     double* du0 = grad_u0 ? (double*)dalloc(c, sizeof(double) * 3 * (size_t)g.S) : nullptr;
     auto release = [&]() {
         for (void* p : seg_f) dfree(c, p);
@@ -850,9 +881,10 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
         dfree(c, lam[1]);
         dfree(c, adj);
         dfree(c, grads);
+        dfree(c, lul);
         dfree(c, du0);
     };
-    bool ok = seg_pre && seg_post && lam[0] && lam[1] && adj && grads && (!grad_u0 || du0);
+    bool ok = seg_pre && seg_post && lam[0] && lam[1] && adj && grads && lul && (!grad_u0 || du0);
     for (void* p : seg_f) ok = ok && p;
     if (!ok) {
         release();
@@ -885,7 +917,27 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     };
     step_rc(cudaMemsetAsync(lam[lc], 0, fb, s), "lambda");
     step_rc(cudaMemsetAsync(adj, 0, sizeof(BubbleAdj) * nb, s), "bubble adjoint");
-    step_rc(cudaMemsetAsync(grads, 0, sizeof(double) * (1 + nb), s), "grads");
+    step_rc(cudaMemsetAsync(grads, 0, sizeof(double) * 2 * (size_t)nb, s), "grads");
+    // Phases A and B of the bubble adjoint run on a second stream alongside
+    // the liquid adjoint; phase C joins both.
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_ab = nullptr;
+    step_rc(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "adjoint stream");
+    step_rc(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming), "event");
+    step_rc(cudaEventCreateWithFlags(&ev_ab, cudaEventDisableTiming), "event");
+    struct Side {
+        cudaStream_t& s2;
+        cudaEvent_t& a;
+        cudaEvent_t& b;
+        ~Side() {
+            if (s2) {
+                cudaStreamSynchronize(s2);
+                cudaStreamDestroy(s2);
+            }
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } side{s2, ev_in, ev_ab};
     const unsigned blocks = (unsigned)((g.S + 127) / 128);
     const int nseg = (N + K - 1) / K;
     for (int seg = nseg - 1; seg >= 0 && rc == LBM_OK; --seg) {
@@ -927,13 +979,20 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
                 e1 = c->events[c->events_used].second;
                 ++c->events_used;
             }
+            const double ls = n >= N - t->window ? seed : 0.0;
+            step_rc(cudaEventRecord(ev_in, s), "event");
+            step_rc(cudaStreamWaitEvent(s2, ev_in, 0), "event wait");
+            k_adj_bubbles_ab<<<nb, ADJ_THREADS, 0, s2>>>(fn, lam[lc], g, cp, pre, post, c->bub.d, nb,
+                                                          ac, adj, grads + nb, grads, lul, ls);
+            step_rc(cudaGetLastError(), "bubble adjoint");
+            step_rc(cudaEventRecord(ev_ab, s2), "event");
             k_adj_liquid<<<blocks, 128, 0, s>>>(fn, lam[lc], lam[lc ^ 1], g, cp, post, nb, ac.two_way);
             if (e1) step_rc(cudaEventRecord(e1, s), "event");
-            const double ls = n >= N - t->window ? seed : 0.0;
-            k_adj_bubbles<<<1, ADJ_THREADS, 0, s>>>(fn, lam[lc], lam[lc ^ 1], g, cp, pre, post, c->bub.d,
-                                                     nb, ac, adj, grads, grads + 1, ls);
+            step_rc(cudaStreamWaitEvent(s, ev_ab, 0), "event wait");
+            k_adj_bubbles_c<<<1, ADJ_THREADS, 0, s>>>(fn, lam[lc ^ 1], g, cp, pre, c->bub.d, nb, ac, adj,
+                                                       grads, lul);
             step_rc(cudaGetLastError(), "adjoint step");
-            c->launches += 2;
+            c->launches += 3;
             lc ^= 1;
         }
     }
@@ -943,9 +1002,10 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
         step_rc(cudaMemcpyAsync(grad_u0, du0, sizeof(double) * 3 * (size_t)g.S, cudaMemcpyDeviceToHost, s),
                 "du0");
     }
-    std::vector<double> hg(1 + nb, 0.0);
+    std::vector<double> hg(2 * (size_t)nb, 0.0);
     if (rc == LBM_OK)
-        step_rc(cudaMemcpyAsync(hg.data(), grads, sizeof(double) * (1 + nb), cudaMemcpyDeviceToHost, s),
+        step_rc(cudaMemcpyAsync(hg.data(), grads, sizeof(double) * 2 * (size_t)nb,
+                                cudaMemcpyDeviceToHost, s),
                 "grads");
     // Back to the state after the forward.
     c->cur = t->final_cur;
@@ -954,10 +1014,15 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     c->cover_valid = false;
     guard_invalidate(c);
     step_rc(cudaStreamSynchronize(s), "adjoint");
+    if (s2) step_rc(cudaStreamSynchronize(s2), "adjoint side stream");
     release();
     if (rc) return rc;
-    if (grad_drag_scale) *grad_drag_scale = hg[0];
+    if (grad_drag_scale) {
+        double sum = 0.0;
+        for (int b = 0; b < nb; ++b) sum += hg[nb + b];
+        *grad_drag_scale = sum;
+    }
     if (grad_diam)
-        for (int b = 0; b < nb; ++b) grad_diam[b] = hg[1 + b];
+        for (int b = 0; b < nb; ++b) grad_diam[b] = hg[b];
     return LBM_OK;
 }

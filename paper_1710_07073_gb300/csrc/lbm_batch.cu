@@ -165,6 +165,7 @@ void layout_columns(lbm_batch* b) {
         col.cp.rho0 = (float)b->p.rho_l;
         col.cp.scale = (float)b->scale;
         col.cp.inv_scale = (float)(1.0 / b->scale);
+        col.cp.point = b->p.mapping == LBM_MAP_POINT ? 1 : 0;
         col.pop_offset = off;
         col.tile_base = tile;
         col.item_base = item;
@@ -471,7 +472,13 @@ int lbm_batch_set_params(lbm_batch* b, const lbm_params* p) {
         return bfail(b, LBM_ERR_STATE, "set the mapping before lbm_batch_set_bubbles");
     if (b->dev_ready && p->rho_l != b->p.rho_l)
         return bfail(b, LBM_ERR_STATE, "rho_l is the storage reference; set it before first use");
+    const bool remap = b->dev_ready && p->mapping != b->p.mapping;
     b->p = *p;
+    if (remap) {   // the column table carries the mapping mode
+        layout_columns(b);
+        int rc = upload_columns(b);
+        if (rc) return rc;
+    }
     if (b->bub.nb > 0)
         LBM_BCUDA(launch_bubble_constants_batch(b->bub, batch_bubble_const(b), b->col_nu_d,
                                                 b->bubble_col_d, b->stream), "bubble constants");

@@ -1203,37 +1203,43 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
             s_xhi[tid] = -1;
         }
         __syncthreads();
-        for (int e = tid; e < cntc * NAX; e += INTERP_THREADS) {
-            const int k = e / NAX, q = e - k * NAX;
-            const BubbleRec& r = s_rec[k];
-            if (LIFT) {
-                float w, dw;
-                if (q < TX)
-                    axis_wd(xb0 + q, r.ax, r.fx, r.inv_n, r.h, g.nx, px, false, w, dw);
-                else if (q < TX + TY)
-                    axis_wd(yb0 + q - TX, r.ay, r.fy, r.inv_n, r.h, g.ny, py, false, w, dw);
-                else
-                    axis_wd(zb0 + q - TX - TY, r.az, r.fz, r.inv_n, r.h, g.nz, pz,
-                            (g.walls & WALL_TOP_FREE) != 0, w, dw);
-                s_w[k][q] = w;
-                s_d[k][q] = dw;
-                if (q < TX && (w != 0.0f || dw != 0.0f)) {
-                    atomicMin(&s_xlo[k], q);
-                    atomicMax(&s_xhi[k], q);
+        // The mapping mode is the same for every bubble: one loop per mode.
+        auto tabulate = [&](auto mode) {
+            constexpr int PM = decltype(mode)::value;
+            for (int e = tid; e < cntc * NAX; e += INTERP_THREADS) {
+                const int k = e / NAX, q = e - k * NAX;
+                const BubbleRec& r = s_rec[k];
+                if (LIFT) {
+                    float w, dw;
+                    if (q < TX)
+                        axis_wd<PM>(xb0 + q, r.ax, r.fx, r.inv_n, r.h, g.nx, px, false, w, dw);
+                    else if (q < TX + TY)
+                        axis_wd<PM>(yb0 + q - TX, r.ay, r.fy, r.inv_n, r.h, g.ny, py, false, w, dw);
+                    else
+                        axis_wd<PM>(zb0 + q - TX - TY, r.az, r.fz, r.inv_n, r.h, g.nz, pz,
+                                    (g.walls & WALL_TOP_FREE) != 0, w, dw);
+                    s_w[k][q] = w;
+                    s_d[k][q] = dw;
+                    if (q < TX && (w != 0.0f || dw != 0.0f)) {
+                        atomicMin(&s_xlo[k], q);
+                        atomicMax(&s_xhi[k], q);
+                    }
+                } else if (q < TX) {
+                    const float w = axis_weight<PM>(r, xb0 + q, r.ax, r.fx, g.nx, px);
+                    s_w[k][q] = w;
+                    if (w != 0.0f) {
+                        atomicMin(&s_xlo[k], q);
+                        atomicMax(&s_xhi[k], q);
+                    }
+                } else if (q < TX + TY) {
+                    s_w[k][q] = axis_weight<PM>(r, yb0 + q - TX, r.ay, r.fy, g.ny, py);
+                } else {
+                    s_w[k][q] = axis_weight<PM>(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, pz);
                 }
-            } else if (q < TX) {
-                const float w = axis_weight(r, xb0 + q, r.ax, r.fx, g.nx, px);
-                s_w[k][q] = w;
-                if (w != 0.0f) {
-                    atomicMin(&s_xlo[k], q);
-                    atomicMax(&s_xhi[k], q);
-                }
-            } else if (q < TX + TY) {
-                s_w[k][q] = axis_weight(r, yb0 + q - TX, r.ay, r.fy, g.ny, py);
-            } else {
-                s_w[k][q] = axis_weight(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, pz);
             }
-        }
+        };
+        if (cp.point) tabulate(MapMode<MAP_POINT>{});
+        else tabulate(MapMode<MAP_CELL>{});
         __syncthreads();
         // INTERP_ROWS threads per bubble, one (z, y) row each; the row sums
         // are added over the rows by shuffles (fixed order).

@@ -79,6 +79,7 @@ CollideParams collide_params(const lbm_ctx* c) {
     cp.rho0 = (float)c->p.rho_l;
     cp.scale = (float)c->scale;
     cp.inv_scale = (float)(1.0 / c->scale);
+    cp.point = c->p.mapping == LBM_MAP_POINT ? 1 : 0;
     return cp;
 }
 

@@ -409,7 +409,7 @@ __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __re
                                                  const int* __restrict__ items, int cap,
                                                  const BubbleRec* __restrict__ recs, int nb,
                                                  int n_t, int bx, int by, int bz, int x0, int y,
-                                                 int z, bool active, BubbleRec* srec) {
+                                                 int z, bool active, BubbleRec* srec, bool point) {
     float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
     // Chunks of FB bubbles: the CTA first tabulates each bubble's per-axis
     // cell integrals over the block (TX columns, TY rows, PZ planes), then
@@ -432,16 +432,23 @@ __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __re
             else srec[tid] = BubbleRec{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         }
         __syncthreads();
-        for (int e = tid; e < cnt * NAX; e += NT) {
-            const int k = e / NAX, q = e - k * NAX;
-            const BubbleRec& r = srec[k];
-            if (q < TX)
-                s_w[k][q] = axis_weight(r, xb0 + q, r.ax, r.fx, g.nx, !(g.walls & 0x01));
-            else if (q < TX + TY)
-                s_w[k][q] = axis_weight(r, yb0 + q - TX, r.ay, r.fy, g.ny, !(g.walls & 0x04));
-            else
-                s_w[k][q] = axis_weight(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, !(g.walls & 0x10));
-        }
+        // The mapping mode is the same for every bubble: one loop per mode.
+        auto tabulate = [&](auto mode) {
+            constexpr int PM = decltype(mode)::value;
+            for (int e = tid; e < cnt * NAX; e += NT) {
+                const int k = e / NAX, q = e - k * NAX;
+                const BubbleRec& r = srec[k];
+                if (q < TX)
+                    s_w[k][q] = axis_weight<PM>(r, xb0 + q, r.ax, r.fx, g.nx, !(g.walls & 0x01));
+                else if (q < TX + TY)
+                    s_w[k][q] = axis_weight<PM>(r, yb0 + q - TX, r.ay, r.fy, g.ny, !(g.walls & 0x04));
+                else
+                    s_w[k][q] =
+                        axis_weight<PM>(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, !(g.walls & 0x10));
+            }
+        };
+        if (point) tabulate(MapMode<MAP_POINT>{});
+        else tabulate(MapMode<MAP_CELL>{});
         __syncthreads();
         if (active) {
             const int xi = 2 * threadIdx.x, yi = TX + threadIdx.y, zi = TX + TY + threadIdx.z;
@@ -512,7 +519,7 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     const bool forced = n_t > 0;   // uniform over the CTA (one tile)
     if (forced && TAB) {
         const Force2 F = gather_force_tab(g, tile_start, items, cap, recs, nb, n_t, bx, by, bz,
-                                          x0, y, z, active, srec);
+                                          x0, y, z, active, srec, cp.point != 0);
         Fx = F.x;
         Fy = F.y;
         Fz = F.z;

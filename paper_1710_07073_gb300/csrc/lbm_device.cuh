@@ -223,9 +223,15 @@ __device__ __forceinline__ void gather(const typename Store<ST>::T* __restrict__
 // with a, b clipped to the window [-1, 1] (Eq. 18-19).  The factored form
 // avoids the cancellation of a difference of antiderivatives.
 // A negative h selects the point-sampled map: Z at the node times the cell
-// width, 2|h| (1 - s^2)^2, zero outside the window.
+// width, 2|h| (1 - s^2)^2, zero outside the window.  PM fixes the mode at
+// compile time (MAP_CELL, MAP_POINT) for loops whose mode is known uniform;
+// MAP_ANY reads it from the sign of h.
+constexpr int MAP_ANY = -1, MAP_CELL = 0, MAP_POINT = 1;
+template <int P> struct MapMode { static constexpr int value = P; };
+
+template <int PM = MAP_ANY>
 __device__ __forceinline__ float cell_poly(float s, float h) {
-    if (h < 0.0f) {
+    if (PM == MAP_POINT || (PM == MAP_ANY && h < 0.0f)) {
         const float t = fminf(fabsf(s), 1.0f);
         const float q = fmaf(-t, t, 1.0f);
         return -2.0f * h * q * q;
@@ -243,6 +249,7 @@ __device__ __forceinline__ float cell_poly(float s, float h) {
 // the record's anchor cell `anc` and offset `fr` (Eq. 19), wrapped on a
 // periodic axis of length L to the nearer image.  The sweep's force gather and
 // the many-bubble interpolation both take their weights from it.
+template <int PM = MAP_ANY>
 __device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc, float fr, int L,
                                              bool periodic) {
     float rc = (float)(c - anc) + 0.5f - fr;
@@ -250,7 +257,7 @@ __device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc,
         if (rc > 0.5f * L) rc -= (float)L;
         else if (rc < -0.5f * L) rc += (float)L;
     }
-    return cell_poly(rc * r.inv_n, r.h);
+    return cell_poly<PM>(rc * r.inv_n, r.h);
 }
 
 // Per-axis factors for the interpolated vorticity (lift), by summation by
@@ -262,6 +269,7 @@ __device__ __forceinline__ float axis_weight(const BubbleRec& r, int c, int anc,
 // the tangential components the curl differentiates (+w/2).  Periodic axes
 // wrap the distance to the nearer image.  Returns w(c) and d(c) for the
 // cell c, anchor cell anc and offset fr of the centre.
+template <int PM = MAP_ANY>
 __device__ __forceinline__ void axis_wd(int c, int anc, float fr, float inv_n, float hh, int L,
                                         bool periodic, bool free_hi, float& w, float& d) {
     float rc = (float)(c - anc) + 0.5f - fr;
@@ -270,9 +278,9 @@ __device__ __forceinline__ void axis_wd(int c, int anc, float fr, float inv_n, f
         else if (rc < -0.5f * L) rc += (float)L;
     }
     const float s = rc * inv_n;
-    w = cell_poly(s, hh);
-    const float wm = (!periodic && c - 1 < 0) ? 0.0f : cell_poly(s - inv_n, hh);
-    const float wp = (!periodic && c + 1 > L - 1) ? 0.0f : cell_poly(s + inv_n, hh);
+    w = cell_poly<PM>(s, hh);
+    const float wm = (!periodic && c - 1 < 0) ? 0.0f : cell_poly<PM>(s - inv_n, hh);
+    const float wp = (!periodic && c + 1 > L - 1) ? 0.0f : cell_poly<PM>(s + inv_n, hh);
     d = 0.5f * (wm - wp);
     if (!periodic) {
         if (c == 0) d += 0.5f * w;

@@ -82,6 +82,7 @@ struct CollideParams {
     float rho0;            // storage shift reference density
     float scale;           // 16-bit storage: stored = g * scale / w_j
     float inv_scale;
+    int point;             // bubble weights by point samples (lbm_params.mapping)
 };
 
 // What the collide-stream sweep needs to spread one bubble (Eq. 21): the

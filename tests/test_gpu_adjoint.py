@@ -115,3 +115,13 @@ def test_backward_needs_an_unchanged_forward_record():
     with pytest.raises(lbm.LbmError) as e:
         lbm.lbm_adj_backward(col.ctx)
     assert e.value.code == lbm.LBM_ERR_STATE
+
+
+def test_adjoint_many_bubbles_against_oracle_fd():
+    # Twelve bubbles with overlapping windows: a CTA per bubble for the
+    # spreading adjoint and the sub-step reverse, the interpolation adjoints
+    # added in bubble order, the drag-scale gradient summed in bubble order.
+    rng = np.random.default_rng(12)
+    pos = np.column_stack([rng.uniform(4.0, 12.0, 12), rng.uniform(4.0, 12.0, 12),
+                           rng.uniform(5.0, 14.0, 12)])
+    _check(_problem(positions=tuple(map(tuple, pos)), steps=40, every=10, window=10), d=2.0)
