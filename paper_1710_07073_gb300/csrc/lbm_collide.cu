@@ -405,6 +405,7 @@ struct Force2 {
     float2 x, y, z;
 };
 
+template <int ST>
 __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __restrict__ tile_start,
                                                  const int* __restrict__ items, int cap,
                                                  const BubbleRec* __restrict__ recs, int nb,
@@ -447,7 +448,10 @@ __device__ __forceinline__ Force2 gather_force_tab(const Geo& g, const int* __re
                         axis_weight<PM>(r, zb0 + q - TX - TY, r.az, r.fz, g.nz, !(g.walls & 0x10));
             }
         };
-        if (point) tabulate(MapMode<MAP_POINT>{});
+        // (FP32 keeps the one loop with the mode read per weight: its sweep
+        // has the slack, and the smaller code measured faster.)
+        if (ST == 0) tabulate(MapMode<MAP_ANY>{});
+        else if (point) tabulate(MapMode<MAP_POINT>{});
         else tabulate(MapMode<MAP_CELL>{});
         __syncthreads();
         if (active) {
@@ -518,7 +522,7 @@ __device__ __forceinline__ void sweep_block(const typename Store<ST>::T* __restr
     float2 Fx = f2(0.0f), Fy = f2(0.0f), Fz = f2(0.0f);
     const bool forced = n_t > 0;   // uniform over the CTA (one tile)
     if (forced && TAB) {
-        const Force2 F = gather_force_tab(g, tile_start, items, cap, recs, nb, n_t, bx, by, bz,
+        const Force2 F = gather_force_tab<ST>(g, tile_start, items, cap, recs, nb, n_t, bx, by, bz,
                                           x0, y, z, active, srec, cp.point != 0);
         Fx = F.x;
         Fy = F.y;
