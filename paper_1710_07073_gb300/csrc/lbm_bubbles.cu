@@ -419,7 +419,8 @@ __device__ void bubble_tail(const Geo& g, const BubbleDev& B, const BubbleConst&
         const float v0 = u[0] - ul[0], v1 = u[1] - ul[1], v2 = u[2] - ul[2];
         const float speed = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
         const float re = speed * K.re_per_speed;
-        const float visc_a = K.visc_a0 * (1.0f + sn_coeff * __powf(re, sn_exp));
+        // Re^b with the accurate powf (the adjoint replays the same value).
+        const float visc_a = K.visc_a0 * (1.0f + sn_coeff * powf(re, sn_exp));
         const float cdv = fmaxf(fminf(visc_a, K.visc_b), K.eo_term * speed);   // C_D |v|
         const float kd = -K.drag_pref * cdv;
         float fd[3] = {kd * v0, kd * v1, kd * v2};
