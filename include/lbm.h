@@ -194,7 +194,7 @@ typedef struct lbm_units {
  * LCF^2/TCF by Eq. 9, omega = 1/(3 nu_lu + 1/2).  Returns LBM_ERR_ARG for a
  * non-positive or non-finite input or rho_b >= rho_l.  A set-up with water's
  * viscosity at millimetre cells gives omega just below 2 (Appendix A's 4 mm
- * case: nu_lu = 4e-6, omega = 1.99995); the conversion does not judge
+ * case: nu_lu = 4e-6, omega = 1.99995); the conversion does not check
  * stability. */
 int lbm_units_from_physical(const lbm_physical* ph, lbm_units* u, lbm_params* p,
                             double* omega);
