@@ -15,6 +15,7 @@
 //                    order.
 //  field kernels     initialisation to f^eq (Eq. 6), population I/O, Eq. 10
 //                    moments and FP64 totals.
+#include <climits>
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -1327,7 +1328,13 @@ k_swarm_tail(Geo g, BubbleDev B, BubbleConst bc, int* __restrict__ flag, Bins bi
     const int tid = threadIdx.x;
     const int gtid = blockIdx.x * TAIL_THREADS + tid, nthreads = gridDim.x * TAIL_THREADS;
     for (int t = gtid; t < bins.T; t += nthreads) bins.cnt[t] = 0;
-    if (gtid == 0) *sw.ncover = 0;
+    if (gtid == 0) {
+        *sw.ncover = 0;
+        if (sw.zrange) {
+            sw.zrange[0] = INT_MAX;
+            sw.zrange[1] = -1;
+        }
+    }
     const int b = gtid;
     if (b < B.nb) {
         BubbleIn in;
@@ -1452,18 +1459,34 @@ k_swarm_bin(Geo g, BubbleDev B, Bins bins, SwarmBins sw, const int* __restrict__
     const int gtid = blockIdx.x * SWARM_THREADS + tid;
     const int T = bins.T;
 
-    // 1. Count.
+    // 1. Count; and the z tile layers the lists reach (for the next steps'
+    // split of the sweep).
+    int zlo = INT_MAX, zhi = -1;
     for (int b = gtid; b < B.nb; b += nthreads) {
         int tl[3][MAX_AXIS_TILES], nt[3];
         int n = 0;
         if (bubble_tiles(g, B, select, sw.pad, b, tl, nt)) {
-            for (int iz = 0; iz < nt[2]; ++iz)
+            for (int iz = 0; iz < nt[2]; ++iz) {
+                zlo = min(zlo, tl[2][iz]);
+                zhi = max(zhi, tl[2][iz]);
                 for (int iy = 0; iy < nt[1]; ++iy)
                     for (int ix = 0; ix < nt[0]; ++ix)
                         atomicAdd(&bins.cnt[(tl[2][iz] * g.nty + tl[1][iy]) * g.ntx + tl[0][ix]], 1);
+            }
             n = nt[0] * nt[1] * nt[2];
         }
         sw.ntile[b] = n;
+    }
+    if (sw.zrange) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            zlo = min(zlo, __shfl_xor_sync(0xffffffffu, zlo, o));
+            zhi = max(zhi, __shfl_xor_sync(0xffffffffu, zhi, o));
+        }
+        if (lane == 0 && zhi >= 0) {
+            atomicMin(sw.zrange, zlo);
+            atomicMax(sw.zrange + 1, zhi);
+        }
     }
     if (!grid_barrier(sw.bar, flag)) return;
 

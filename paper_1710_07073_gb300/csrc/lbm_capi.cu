@@ -1,6 +1,8 @@
 // Host side of the C ABI declared in include/lbm.h: argument checks, device
 // state, and the order of launches of one coupled step (Algorithm 1 of
 // arXiv:1710.07073).
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -171,7 +173,7 @@ void free_bubbles(lbm_ctx* c) {
                     b.active, b.spread, b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items,
                     sb.prev_tiles, sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, sb.safe,
                     sb.zperm, sw.bar, sw.cursor, sw.kidx, sw.slots, sw.ntile, sw.partial, sw.cover,
-                    sw.ncover, sw.chunk_sums};
+                    sw.ncover, sw.chunk_sums, sw.zrange};
     for (void* p : ptrs) dfree(c, p);
     c->cover_valid = false;
     b = BubbleDev{};
@@ -186,7 +188,10 @@ void free_bubbles(lbm_ctx* c) {
 
 }  // namespace
 
-void guard_invalidate(lbm_ctx* c) { c->epoch += 1; }
+void guard_invalidate(lbm_ctx* c) {
+    c->epoch += 1;
+    c->swarm_valid_from = c->swarm_step;   // older z ranges say nothing of the new state
+}
 
 namespace {
 
@@ -204,6 +209,81 @@ int alloc_guard(lbm_ctx* c, unsigned** safe, int** zperm, int* nbz) {
     LBM_CUDA(cudaMemcpyAsync(*zperm, ident.data(), sizeof(int) * ident.size(),
                              cudaMemcpyHostToDevice, c->stream), "sweep order");
     return LBM_OK;
+}
+
+}  // namespace
+
+// Interpolation CTAs per SM while the sweep of the blocks no bubble reaches
+// runs beside it (GB300, swarm 384x384x768: 2 gives the shortest step; 4,
+// the interpolation's own occupancy, leaves the sweep no room; 1 starves it).
+#ifndef LBM_SPLIT_INTERP_PER_SM
+#define LBM_SPLIT_INTERP_PER_SM 2
+#endif
+
+
+namespace {
+
+// Streams, events and pinned slots of the split sweep, made on first use.
+int ensure_split(lbm_ctx* c) {
+    if (c->side_hi) return LBM_OK;
+    int least = 0, greatest = 0;
+    LBM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest), "stream priorities");
+    LBM_CUDA(cudaStreamCreateWithPriority(&c->side_hi, cudaStreamNonBlocking, greatest), "stream");
+    LBM_CUDA(cudaStreamCreateWithPriority(&c->side_lo, cudaStreamNonBlocking, least), "stream");
+    LBM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+    LBM_CUDA(cudaEventCreateWithFlags(&c->ev_hi, cudaEventDisableTiming), "event");
+    LBM_CUDA(cudaEventCreateWithFlags(&c->ev_lo, cudaEventDisableTiming), "event");
+    for (int k = 0; k < lbm_ctx::SPLIT_RING; ++k) {
+        LBM_CUDA(cudaEventCreateWithFlags(&c->ev_rb[k], cudaEventDisableTiming), "event");
+        c->rb_step[k] = -1;
+    }
+    LBM_CUDA(cudaHostAlloc((void**)&c->zr_host, 2 * sizeof(int) * lbm_ctx::SPLIT_RING,
+                           cudaHostAllocDefault), "pinned z range");
+    int dev = 0;
+    LBM_CUDA(cudaGetDevice(&dev), "device");
+    LBM_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    return LBM_OK;
+}
+
+void destroy_split(lbm_ctx* c) {
+    if (c->side_hi) cudaStreamSynchronize(c->side_hi);
+    if (c->side_lo) cudaStreamSynchronize(c->side_lo);
+    if (c->side_hi) cudaStreamDestroy(c->side_hi);
+    if (c->side_lo) cudaStreamDestroy(c->side_lo);
+    for (cudaEvent_t e : {c->ev_fork, c->ev_hi, c->ev_lo})
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_rb)
+        if (e) cudaEventDestroy(e);
+    if (c->zr_host) cudaFreeHost(c->zr_host);
+}
+
+// The z blocks [*b0, *b1) that bubble forces may reach in many-path step n,
+// from the binning's z range read back SPLIT_LAG steps before: a bubble moves
+// at most GUARD_CELLS = TZ cells, one tile layer, per step (else the step is
+// flagged unstable).  Returns false if no such read-back is at hand.
+bool guarded_blocks(lbm_ctx* c, const Geo& g, int* b0, int* b1, int* rc) {
+    *rc = LBM_OK;
+    const long long n = c->swarm_step, m = n - lbm_ctx::SPLIT_LAG;
+    if (!c->side_hi || m < 0 || m < c->swarm_valid_from) return false;
+    const int slot = (int)(m % lbm_ctx::SPLIT_RING);
+    if (c->rb_step[slot] != m) return false;
+    const cudaError_t e = cudaEventSynchronize(c->ev_rb[slot]);
+    if (e != cudaSuccess) {
+        *rc = cuda_fail(c, e, "z range read-back");
+        return false;
+    }
+    static_assert(GUARD_CELLS <= TZ, "a bubble crosses at most one tile layer per step");
+    const int zlo = c->zr_host[2 * slot], zhi = c->zr_host[2 * slot + 1];
+    const int nbz = sweep_z_blocks(g.nz);
+    if (zhi < zlo) {
+        *b0 = *b1 = 0;
+        return true;
+    }
+    const int widen = (int)(n - m) + 1;
+    const int l0 = std::max(0, zlo - widen), l1 = std::min(g.ntz - 1, zhi + widen);
+    *b0 = std::min(nbz, l0 * TZ / SWEEP_PZ);
+    *b1 = std::min(nbz, (l1 + 1) * TZ / SWEEP_PZ);
+    return true;
 }
 
 }  // namespace
@@ -235,6 +315,36 @@ int enqueue_one_step(lbm_ctx* c) {
     const unsigned* safe_now = safe ? safe + now * (size_t)g.ntz : nullptr;
     const int* zperm_now = zperm ? zperm + now * (size_t)nbz : nullptr;
     const int pad = (c->p.forces & LBM_FORCE_LIFT) ? 1 : 0;   // the vorticity halo
+    // Many bubbles: the update and the sweep of the z blocks bubbles can reach
+    // run on a high-priority side stream while the other blocks are swept
+    // (without forces) on a low-priority one; the step then joins on
+    // c->stream.  The per-node arithmetic is the same, so are the results.
+    const bool many = bubbles && !c->use_small;
+    const bool split_able = many && two_way && !c->timing && (g.nx & 1) == 0 &&
+                            (c->walls & 0x30) == 0x30;
+    int gb0 = 0, gb1 = 0;
+    bool split = false;
+    if (split_able) {
+        int rc = ensure_split(c);
+        if (rc) return rc;
+        split = guarded_blocks(c, g, &gb0, &gb1, &rc);
+        if (rc) return rc;
+    }
+    cudaStream_t st = c->stream;   // the update and the guarded sweep
+    if (split) {
+        const int nbz = sweep_z_blocks(g.nz);
+        LBM_CUDA(cudaEventRecord(c->ev_fork, c->stream), "fork");
+        LBM_CUDA(cudaStreamWaitEvent(c->side_hi, c->ev_fork, 0), "fork");
+        LBM_CUDA(cudaStreamWaitEvent(c->side_lo, c->ev_fork, 0), "fork");
+        const ZSpan free_span{0, nbz - (gb1 - gb0), gb0, gb1 - gb0};
+        LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp, nullptr,
+                                       c->bub.rec, c->bub.nb, c->flag_d, nullptr, epoch, false,
+                                       nullptr, c->side_lo, &free_span),
+                 "collide-stream (no bubble reaches)");
+        LBM_CUDA(cudaEventRecord(c->ev_lo, c->side_lo), "join");
+        if (free_span.count > 0) c->launches += 1;
+        st = c->side_hi;
+    }
     if (bubbles) {
         if (c->use_small) {
             SmallBins sb = c->small;
@@ -251,23 +361,36 @@ int enqueue_one_step(lbm_ctx* c) {
             // records: left by the previous step, else made here from
             // `active` (first step after the bubbles were set).
             if (!c->cover_valid) {
-                LBM_CUDA(launch_bubble_records(g, c->bub, c->stream), "records");
-                LBM_CUDA(cudaMemsetAsync(c->bins.cnt, 0, sizeof(int) * (size_t)c->bins.T,
-                                         c->stream), "cover counts");
-                LBM_CUDA(cudaMemsetAsync(c->swarm.ncover, 0, sizeof(int), c->stream), "cover list");
+                LBM_CUDA(launch_bubble_records(g, c->bub, st), "records");
+                LBM_CUDA(cudaMemsetAsync(c->bins.cnt, 0, sizeof(int) * (size_t)c->bins.T, st),
+                         "cover counts");
+                LBM_CUDA(cudaMemsetAsync(c->swarm.ncover, 0, sizeof(int), st), "cover list");
                 SwarmBins sw = c->swarm;
                 sw.pad = pad;
-                LBM_CUDA(launch_swarm_binning(g, c->bub, c->bins, sw, c->bub.active, c->flag_d,
-                                              c->stream), "cover");
+                LBM_CUDA(launch_swarm_binning(g, c->bub, c->bins, sw, c->bub.active, c->flag_d, st),
+                         "cover");
                 c->launches += 2;
             }
             SwarmBins sw = c->swarm;
             sw.pad = pad;
+            // Split: the persistent interpolation leaves room on every SM for
+            // the sweep of the blocks bubbles do not reach.
+            if (split && c->sms > 0)
+                sw.interp_grid = std::min(sw.interp_grid, c->sms * LBM_SPLIT_INTERP_PER_SM);
             LBM_CUDA(launch_swarm_update(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
-                                         c->flag_d, c->bins, sw, c->stream),
+                                         c->flag_d, c->bins, sw, st),
                      "bubble update");
             c->launches += SWARM_LAUNCHES;   // interpolation by tiles; update; binning
             c->cover_valid = true;
+            if (split_able) {
+                // This step's z range of the lists, for the split SPLIT_LAG steps on.
+                const int slot = (int)(c->swarm_step % lbm_ctx::SPLIT_RING);
+                LBM_CUDA(cudaMemcpyAsync(c->zr_host + 2 * slot, sw.zrange, 2 * sizeof(int),
+                                         cudaMemcpyDeviceToHost, st), "z range");
+                LBM_CUDA(cudaEventRecord(c->ev_rb[slot], st), "z range");
+                c->rb_step[slot] = c->swarm_step;
+            }
+            c->swarm_step += 1;
         }
         c->bins_valid = true;
     }
@@ -287,6 +410,19 @@ int enqueue_one_step(lbm_ctx* c) {
     TileLists tl{};
     if (c->use_small) tl = TileLists{c->small.start, c->small.count, c->small.items, SMALL_MAX_PAIRS};
     else tl = TileLists{c->bins.off, c->bins.cnt, c->bins.items, c->bins.cap};
+    if (split) {
+        const ZSpan guarded{gb0, gb1 - gb0, INT_MAX, 0};
+        LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp, &tl,
+                                       c->bub.rec, c->bub.nb, c->flag_d, nullptr, epoch, false,
+                                       nullptr, st, &guarded),
+                 "collide-stream (bubbles reach)");
+        LBM_CUDA(cudaEventRecord(c->ev_hi, st), "join");
+        LBM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_hi, 0), "join");
+        LBM_CUDA(cudaStreamWaitEvent(c->stream, c->ev_lo, 0), "join");
+        if (guarded.count > 0) c->launches += 1;
+        c->cur ^= 1;
+        return LBM_OK;
+    }
     LBM_CUDA(launch_collide_stream(c->storage, c->f[c->cur], c->f[c->cur ^ 1], g, cp,
                                    two_way ? &tl : nullptr, c->bub.rec, c->bub.nb, c->flag_d,
                                    overlap ? safe_now : nullptr, epoch, overlap,
@@ -417,6 +553,7 @@ int lbm_create(int nx, int ny, int nz, double omega, unsigned walls, lbm_ctx** o
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     if (c->dev_ready) cudaStreamSynchronize(c->stream);
+    destroy_split(c);
     adjoint_free(c);
     for (auto& e : c->events) {
         cudaEventDestroy(e.first);
@@ -684,8 +821,9 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
         sw.cover = (int*)dalloc(c, sizeof(int) * (size_t)c->bins.T);
         sw.ncover = (int*)dalloc(c, sizeof(int));
         sw.chunk_sums = (int*)dalloc(c, sizeof(int) * (size_t)sw.grid);
+        sw.zrange = (int*)dalloc(c, 2 * sizeof(int));
         lists_ok = c->bins.items && sw.bar && sw.cursor && sw.kidx && sw.slots && sw.ntile &&
-                   sw.partial && sw.cover && sw.ncover && sw.chunk_sums;
+                   sw.partial && sw.cover && sw.ncover && sw.chunk_sums && sw.zrange;
         if (lists_ok)
             LBM_CUDA(cudaMemsetAsync(sw.bar, 0, 2 * sizeof(unsigned), c->stream), "barrier");
     }

@@ -14,6 +14,7 @@
 // short: nodes away from the box faces address their 19 sources with one
 // 32-bit offset each, tiles without bubbles skip the forcing terms, and each
 // pair of opposite directions shares its equilibrium terms.
+#include <climits>
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -560,14 +561,16 @@ k_collide_stream_pair(const typename Store<ST>::T* __restrict__ fin,
                       typename Store<ST>::T* __restrict__ fout, Geo g, CollideParams cp,
                       const int* tile_start, const int* tile_count, const int* items, int cap,
                       const BubbleRec* recs, int nb, int* __restrict__ flag,
-                      const unsigned* safe, unsigned epoch, const int* zperm) {
+                      const unsigned* safe, unsigned epoch, const int* zperm, ZSpan zs) {
     __shared__ BubbleRec srec[FORCE_CHUNK];
     // The next bubble update may be scheduled once every CTA of the sweep has
     // started; it waits for the sweep to complete before it reads anything.
     pdl_trigger();
     // z blocks in the order the bubble update before chose (cleared layers
-    // first); the order was written by an update that has completed.
-    const int bz = zperm != nullptr ? __ldcg(zperm + blockIdx.z) : (int)blockIdx.z;
+    // first; written by an update that has completed), else the span's.
+    int bz = zs.first + (int)blockIdx.z;
+    if (bz >= zs.hole) bz += zs.skip;
+    if (zperm != nullptr) bz = __ldcg(zperm + blockIdx.z);
     const bool lead = (blockIdx.x | blockIdx.y | blockIdx.z) == 0;
     sweep_block<ST, TAB>(fin, fout, g, cp, tile_start, tile_count, items, cap, recs, nb, flag,
                          blockIdx.x, blockIdx.y, bz, srec, safe, epoch, lead);
@@ -660,20 +663,29 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, const unsigned* safe,
                                   unsigned epoch, bool overlap, const int* zperm,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const ZSpan* span) {
     const int* start = tl ? tl->start : nullptr;
     const int* count = tl ? tl->count : nullptr;
     const int* items = tl ? tl->items : nullptr;
     const int cap = tl ? tl->cap : 0;
     if (overlap && (safe == nullptr || tl == nullptr)) return cudaErrorInvalidValue;
     if (!overlap) safe = nullptr;
+    const int nbz = (g.nz + PZ - 1) / PZ;
+    ZSpan zs{0, nbz, INT_MAX, 0};
+    if (span) {
+        if ((g.nx & 1) || zperm || span->count < 0 || span->first < 0 || span->skip < 0 ||
+            span->first + span->count + span->skip > nbz)
+            return cudaErrorInvalidValue;
+        zs = *span;
+        if (zs.count == 0) return cudaSuccess;
+    }
     if ((g.nx & 1) == 0) {
         // Even rows: two nodes per thread with aligned vector accesses.  Tile
         // lists longer than the few-bubble path's (many bubbles per tile)
         // take the tabulated force gather.
         cudaLaunchConfig_t cfg = {};
         cfg.blockDim = dim3(PX, TY, PZ);
-        cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + PZ - 1) / PZ);
+        cfg.gridDim = dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (unsigned)zs.count);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -686,7 +698,7 @@ cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, cons
     case SI * 2 + TB:                                                                             \
         return cudaLaunchKernelEx(&cfg, k_collide_stream_pair<SI, TB>, (const T*)fin, (T*)fout,   \
                                   g, cp, start, count, items, cap, recs, nb, flag, safe, epoch,  \
-                                  zperm);
+                                  zperm, zs);
             LBM_LAUNCH_PAIR(0, 0, float)
             LBM_LAUNCH_PAIR(0, 1, float)
             LBM_LAUNCH_PAIR(1, 0, __half)

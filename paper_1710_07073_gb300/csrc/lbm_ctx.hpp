@@ -56,6 +56,22 @@ struct lbm_ctx {
     bool cover_valid = false;
     // Large path: interpolation parts, list positions and binning scratch.
     SwarmBins swarm{};
+    // Large path, split sweep: a step forks from `stream` into a high-priority
+    // stream for the bubble side (update, binning, the sweep of the z blocks
+    // bubbles can reach) and a low-priority one for the sweep of the others,
+    // and joins again.  The blocks bubbles can reach come from the binning's
+    // z range of SPLIT_LAG steps before (read back into pinned memory), widened
+    // by the distance a bubble may move since.
+    static constexpr int SPLIT_RING = 4;
+    static constexpr int SPLIT_LAG = 2;
+    cudaStream_t side_hi = nullptr, side_lo = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_hi = nullptr, ev_lo = nullptr;
+    cudaEvent_t ev_rb[SPLIT_RING] = {};
+    int* zr_host = nullptr;                 // pinned [2 * SPLIT_RING]
+    long long rb_step[SPLIT_RING] = {-1, -1, -1, -1};
+    long long swarm_step = 0;               // many-path steps enqueued
+    long long swarm_valid_from = 0;         // readbacks before this step are stale
+    int sms = 0;                            // SM count (the split interpolation's grid)
 
     // timing of the collide-stream launches
     bool timing = false;

@@ -253,6 +253,7 @@ struct SwarmBins {
     int pad;              // cells the lists reach beyond the supports (1 with lift)
     int* cover;           // [T] the tiles with a non-empty list (any order)
     int* ncover;          // [1] their number
+    int* zrange;          // [2] lowest and highest z tile layer of any list (empty: lo > hi)
     int interp_grid;      // CTAs of the interpolation launch
     int* chunk_sums;      // [grid] per-CTA count totals (scan)
     int grid;             // CTAs of the binning launch (all resident)
@@ -284,11 +285,18 @@ struct BatchColumn {
 // CTA 0) wait for it before reading the tile lists.
 // zperm (may be null): the order of the z blocks (PZ planes each) in which
 // the CTAs are handed out, a permutation of 0 .. ceil(nz / PZ) - 1.
+// A subset of the sweep's z blocks (PZ planes each): CTA z-index i sweeps
+// block first + i, moved past the hole [hole, hole + skip) when it reaches it;
+// `count` blocks in all.
+struct ZSpan {
+    int first, count, hole, skip;
+};
+
 cudaError_t launch_collide_stream(int storage, const void* fin, void* fout, const Geo& g,
                                   const CollideParams& cp, const TileLists* tl,
                                   const BubbleRec* recs, int nb, int* flag, const unsigned* safe,
                                   unsigned epoch, bool overlap, const int* zperm,
-                                  cudaStream_t st);
+                                  cudaStream_t st, const ZSpan* span = nullptr);
 
 // Bubble update with the few-pair binning in the same launch (sb.parts CTAs
 // per bubble).  `overlap`: launched as a programmatic dependent of the sweep
