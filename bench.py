@@ -463,14 +463,29 @@ def run_adjoint(args):
     col.close()
     col = prob.column(1.0, 2.5, P)
     torch.cuda.synchronize()
+    launches0 = lbm.lbm_launch_count(col.ctx)
     t0 = time.perf_counter()
     loss = lbm.lbm_adj_forward(col.ctx, prob.steps, prob.checkpoint_every, prob.window, prob.target)
     t1 = time.perf_counter()
     lbm.lbm_set_kernel_timing(col.ctx, True)
     g_sd, g_d, g_u0 = lbm.lbm_adj_backward(col.ctx, 1.0, want_u0=True)
     t2 = time.perf_counter()
+    launches = lbm.lbm_launch_count(col.ctx) - launches0
     k_ms, k_n = lbm.lbm_get_kernel_time(col.ctx)
     col.close()
+    # End to end through the autograd.Function, the call a user makes: the
+    # initial field goes up from host memory, its gradient comes back.
+    from paper_1710_07073_gb300.adjoint import TerminalVelocityLoss
+    sd_t = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    d_t = torch.tensor(2.5, dtype=torch.float64, requires_grad=True)
+    u0_t = torch.from_numpy(np.ascontiguousarray(P, dtype=np.float64)).requires_grad_()
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    TerminalVelocityLoss.apply(sd_t, d_t, u0_t, prob).backward()
+    e2e_s = time.perf_counter() - t3
+    nbub = len(prob.positions)
+    h2d = 3 * S * 8 + 7 * nbub * 8   # u0, and the bubbles' positions, velocities, diameters
+    d2h = 3 * S * 8 + 2 * nbub * 8 + 8   # du0, the per-bubble gradients, the loss
     g_e = float((g_u0 * P.reshape(-1)).sum())
     h, he = 1e-3, 0.05
     fd_sd = (loss_only(1.0 + h, 2.5, 1.0) - loss_only(1.0 - h, 2.5, 1.0)) / (2 * h)
@@ -478,6 +493,18 @@ def run_adjoint(args):
     fd_e = (loss_only(1.0, 2.5, 1.0 + he) - loss_only(1.0, 2.5, 1.0 - he)) / (2 * he)
     fwd_s, bwd_s = t1 - t0, t2 - t1
     value = S * prob.steps / (fwd_s + bwd_s) / 1e6
+    cpu = None
+    if not args.no_cpu_baseline:
+        # The oracle's gradient is central differences: the loss and two runs
+        # per direction (drag scale, diameter, one initial-field direction).
+        wl_adj = dict(dims=dims, omega=1.6, g=1e-5, pos=np.array([[64.0, 64.0, 32.0]]),
+                      vel=np.zeros((1, 3)), diam=np.array([2.5]))
+        vn, dtn, procs, descn = oracle_mlups_all_cores(wl_adj, 1 << 19, 6, warmup=1,
+                                                       procs=args.cpu_procs)
+        cpu = {"value": round(vn / 7, 4), "unit": "MLUPS", "cores": procs, "kind": "oracle",
+               "sample": descn + " (%.1f s, numpy float64, one process per core); forward MLUPS "
+                         "%.4f divided by 7 forward runs per gradient (the loss and central "
+                         "differences in three directions)" % (dtn, vn)}
     achieved = 3 * 19 * 4 * S / (k_ms / max(1, k_n) * 1e-3) / 1e9
     peak, peak_kind = measured_peak()
     line = {
@@ -488,6 +515,12 @@ def run_adjoint(args):
         "config": {"workload": "adjoint: 128x128x256 column, omega 1.6, d 2.5, 1000 steps, "
                                "checkpoint every 50, loss over the last 200 steps",
                    "forward_s": round(fwd_s, 4), "backward_s": round(bwd_s, 4), "loss": loss},
+        "e2e": {"value": round(S * prob.steps / e2e_s / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": round(h2d / prob.steps, 1),
+                "d2h_bytes_per_step": round(d2h / prob.steps, 1),
+                "call": "TerminalVelocityLoss.apply(...).backward() from host tensors, column "
+                        "creation included"},
+        "cpu_baseline": cpu, "gpu_launches": int(launches),
         "gradients": {"drag_scale": [g_sd, fd_sd, abs(g_sd / fd_sd - 1)],
                       "diameter": [float(g_d[0]), fd_d, abs(g_d[0] / fd_d - 1)],
                       "u0_direction": [g_e, fd_e, abs(g_e / fd_e - 1)],

@@ -828,16 +828,19 @@ extern "C" int lbm_adj_forward(lbm_ctx* c, int nsteps, int checkpoint_every, int
             LBM_CUDA(cudaMemcpyAsync(ck, c->f[c->cur], t->fbytes, cudaMemcpyDeviceToDevice, s),
                      "checkpoint");
             k_snapshot<<<sb, 128, 0, s>>>(c->bub, cb, 0);
+            c->launches += 1;
         }
         rc = enqueue_one_step(c);
         if (rc) return rc;
         k_record_uz<<<sb, 128, 0, s>>>(c->bub, t->uz + (size_t)n * nb);
+        c->launches += 1;
     }
     LBM_CUDA(cudaMemcpyAsync(t->final_f, c->f[c->cur], t->fbytes, cudaMemcpyDeviceToDevice, s),
              "final state");
     k_snapshot<<<sb, 128, 0, s>>>(c->bub, t->final_b, 0);
     t->final_cur = c->cur;
     k_adj_loss<<<1, 32, 0, s>>>(t->uz, nsteps, nb, window, target, t->lossbuf);
+    c->launches += 2;   // the final snapshot and the loss
     LBM_CUDA(cudaGetLastError(), "adjoint forward");
     rc = finish_steps(c);
     if (rc) return rc;
@@ -949,6 +952,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
         void* const f_ctx[2] = {c->f[0], c->f[1]};
         step_rc(cudaMemcpyAsync(seg_f[0], t->ck_f[seg], fb, cudaMemcpyDeviceToDevice, s), "restore");
         k_restore<<<sb, 128, 0, s>>>(c->bub, t->ck_b[seg]);
+        c->launches += 1;
         c->cover_valid = false;
         guard_invalidate(c);
         for (int n = n0; n < n1 && rc == LBM_OK; ++n) {
@@ -959,6 +963,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
             int r2 = enqueue_one_step(c);
             if (r2) rc = r2;
             k_snapshot<<<sb, 128, 0, s>>>(c->bub, seg_post + (size_t)(n - n0) * nb, 1);
+            c->launches += 2;   // the two snapshots around the recomputed step
         }
         c->f[0] = f_ctx[0];
         c->f[1] = f_ctx[1];
@@ -998,6 +1003,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     }
     if (rc == LBM_OK && du0) {
         k_adj_init<<<blocks, 128, 0, s>>>((const float*)t->ck_f[0], lam[lc], g, cp, du0);
+        c->launches += 1;
         step_rc(cudaGetLastError(), "initial-field adjoint");
         step_rc(cudaMemcpyAsync(grad_u0, du0, sizeof(double) * 3 * (size_t)g.S, cudaMemcpyDeviceToHost, s),
                 "du0");
@@ -1011,6 +1017,7 @@ extern "C" int lbm_adj_backward(lbm_ctx* c, double dloss, double* grad_drag_scal
     c->cur = t->final_cur;
     step_rc(cudaMemcpyAsync(c->f[c->cur], t->final_f, fb, cudaMemcpyDeviceToDevice, s), "final");
     k_restore<<<sb, 128, 0, s>>>(c->bub, t->final_b);
+    c->launches += 1;
     c->cover_valid = false;
     guard_invalidate(c);
     step_rc(cudaStreamSynchronize(s), "adjoint");

@@ -125,3 +125,30 @@ def test_adjoint_many_bubbles_against_oracle_fd():
     pos = np.column_stack([rng.uniform(4.0, 12.0, 12), rng.uniform(4.0, 12.0, 12),
                            rng.uniform(5.0, 14.0, 12)])
     _check(_problem(positions=tuple(map(tuple, pos)), steps=40, every=10, window=10), d=2.0)
+
+
+def test_adjoint_launch_count():
+    # Every kernel of the forward record and of the reverse sweep is counted:
+    # per step the coupled step's own launches and the rise-velocity record;
+    # per checkpoint a bubble snapshot; the final snapshot and the loss.  The
+    # reverse: per segment a restore, per recomputed step two snapshots and the
+    # step, per reverse step three adjoint kernels; the initial-field adjoint
+    # and the final restore.
+    prob = _problem(steps=25, every=10, window=10)
+    P = workloads.gaussian_velocity_perturbation(prob.dims, seed=4, amp=1e-4)
+    col = prob.column(1.0, 2.5, P)
+    n0 = lbm.lbm_launch_count(col.ctx)
+    lbm.lbm_step(col.ctx, 1)
+    per_step = lbm.lbm_launch_count(col.ctx) - n0
+    col.close()
+    assert per_step >= 1
+    col = prob.column(1.0, 2.5, P)
+    n0 = lbm.lbm_launch_count(col.ctx)
+    lbm.lbm_adj_forward(col.ctx, prob.steps, prob.checkpoint_every, prob.window, prob.target)
+    n1 = lbm.lbm_launch_count(col.ctx)
+    lbm.lbm_adj_backward(col.ctx, 1.0, want_u0=True)
+    n2 = lbm.lbm_launch_count(col.ctx)
+    col.close()
+    segments = -(-prob.steps // prob.checkpoint_every)
+    assert n1 - n0 == prob.steps * (per_step + 1) + segments + 2
+    assert n2 - n1 == segments + prob.steps * (per_step + 2) + 3 * prob.steps + 2
