@@ -1119,17 +1119,27 @@ constexpr int INTERP_CHUNK = 32;              // listed bubbles per pass
 constexpr int INTERP_ROWS = TY * TZ;          // (y, z) rows of a tile: 16
 static_assert(INTERP_THREADS % INTERP_ROWS == 0 && TZ == 4, "tile shape of the interpolation");
 
-// One covered tile t: the Eq. 10 velocity of its nodes, then for each listed
+// The list head of a covered tile: its list range [beg, end) and this
+// thread's entry of the first chunk (-1 beyond it).  The interpolation loads
+// a tile's head one tile ahead: the chain cover -> count and offset -> entry
+// is three dependent loads.
+struct TileHead {
+    int t, beg, end, id;
+};
+
+// One covered tile h.t: the Eq. 10 velocity of its nodes, then for each listed
 // bubble the part of its Eq. 20 sum over the tile, written at the bubble's
-// list position.  Every thread of the CTA calls it.
+// list position.  Every thread of the CTA calls it.  Once the first chunk's
+// tables are made, the next tile's first list entry is loaded into next.id
+// (next.beg and next.end were loaded a tile before).
 template <int ST, bool PAIR, bool LIFT>
 __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restrict__ f,
-                                            const Geo& g, const CollideParams& cp, int t,
-                                            const int* __restrict__ cnt,
-                                            const int* __restrict__ off,
-                                            const int* __restrict__ items, int cap,
+                                            const Geo& g, const CollideParams& cp,
+                                            const TileHead& h, TileHead& next,
+                                            const int* __restrict__ items,
                                             const BubbleRec* __restrict__ recs, int nb,
                                             float* __restrict__ partial) {
+    const int t = h.t;
     constexpr int NAX = TX + TY + TZ;
     __shared__ float s_u[3][INTERP_ROWS][TX + 1];   // node velocities by (z, y) row, padded
     __shared__ float s_w[INTERP_CHUNK][NAX];         // per-axis cell integrals per bubble
@@ -1159,14 +1169,9 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
         gather_issue<ST>(f, g, ina ? x : 0, ina ? y : 0, ina ? za : 0, ra);
         gather_issue<ST>(f, g, inb ? x : 0, inb ? y : 0, inb ? zb : 0, rb);
     }
-    const int n_t = __ldcg(cnt + t);
-    const int beg = __ldcg(off + t);
-    const int end = min(beg + n_t, cap);
+    const int beg = h.beg, end = h.end;
     BubbleRec rec0{0, 0, 0, 0, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (tid < min(INTERP_CHUNK, end - beg)) {
-        const int id = __ldcg(items + beg + tid);
-        if (id >= 0 && id < nb) rec0 = load_rec(recs + id);
-    }
+    if (h.id >= 0 && h.id < nb) rec0 = load_rec(recs + h.id);
     if (PAIR) {
         // Eq. 10 velocity of the pair (zero for nodes beyond the box).
         float2 drho, jx, jy, jz;
@@ -1243,6 +1248,8 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
         if (cp.point) tabulate(MapMode<MAP_POINT>{});
         else tabulate(MapMode<MAP_CELL>{});
         __syncthreads();
+        if (c0 == beg && tid < min(INTERP_CHUNK, next.end - next.beg))
+            next.id = __ldcg(items + next.beg + tid);
         // INTERP_ROWS threads per bubble, one (z, y) row each; the row sums
         // are added over the rows by shuffles (fixed order).
         for (int k0 = 0; k0 < cntc; k0 += INTERP_THREADS / INTERP_ROWS) {
@@ -1310,10 +1317,30 @@ k_tile_interp(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams 
               const int* __restrict__ cover, const int* __restrict__ ncover,
               float* __restrict__ partial) {
     const int ntiles = __ldcg(ncover);
-    for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {
+    const int step = (int)gridDim.x;
+    int i = (int)blockIdx.x;
+    if (i >= ntiles) return;
+    // The head of the CTA's first tile, and the index of the one after it.
+    auto head = [&](int t) {
+        TileHead h{t, 0, 0, -1};
+        if (t >= 0) {
+            h.beg = __ldcg(off + t);
+            h.end = min(h.beg + __ldcg(cnt + t), cap);
+        }
+        return h;
+    };
+    TileHead h = head(__ldcg(cover + i));
+    if (threadIdx.x < min(INTERP_CHUNK, h.end - h.beg)) h.id = __ldcg(items + h.beg + threadIdx.x);
+    int tn = i + step < ntiles ? __ldcg(cover + i + step) : -1;
+    for (; i < ntiles; i += step) {
+        // The next tile's count and offset go out now; its first list entry
+        // during this tile; the index of the tile after it.
+        TileHead next = head(tn);
+        const int tnn = i + 2 * step < ntiles ? __ldcg(cover + i + 2 * step) : -1;
         __syncthreads();   // the shared tables of the previous tile are done with
-        tile_interp<ST, PAIR, LIFT>(f, g, cp, __ldcg(cover + i), cnt, off, items, cap, recs,
-                                    nb, partial);
+        tile_interp<ST, PAIR, LIFT>(f, g, cp, h, next, items, recs, nb, partial);
+        h = next;
+        tn = tnn;
     }
 }
 
