@@ -90,10 +90,11 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profile_traffic(storage, dims):
+def profile_traffic(storage, dims, key=None):
     """DRAM bytes per collide-stream launch from the committed ncu summary, if it
-    was taken on the current kernel source for this storage and lattice."""
-    key = "%s_%dx%dx%d" % (storage, *dims)
+    was taken on the current kernel source for this storage and lattice (or the
+    given key)."""
+    key = key or "%s_%dx%dx%d" % (storage, *dims)
     try:
         with open(PROFILE_SUMMARY) as fh:
             for line in fh:
@@ -421,7 +422,8 @@ def run_batch(args, wl):
                    "l2": "inputs larger than L2 (%.2f GB populations), no flush" % (
                        19 * S * (4 if storage == "f32" else 2) / 1e9)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": profile_traffic(storage, None, key="%s_batch64" % storage),
                      "kernel": "k_collide_batch<%d,%d>" % (STORAGES[storage], planes),
                      "algorithmic_bytes_per_launch": bytes_per_site * S,
                      "avg_launch_ms": round(avg_kernel_s * 1e3, 5), "launches": k_n,
