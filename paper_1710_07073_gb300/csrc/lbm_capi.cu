@@ -1027,10 +1027,12 @@ const char* lbm_sweep_kernel(const lbm_ctx* c) {
         {"k_collide_stream_pair<2,0>", "k_collide_stream_pair<2,1>"}};
     static const char* const single[3] = {"k_collide_stream<0>", "k_collide_stream<1>",
                                           "k_collide_stream<2>"};
+    static const char* const free_[3] = {"k_collide_stream_free<0>", "k_collide_stream_free<1>",
+                                         "k_collide_stream_free<2>"};
     const int st = c->storage < 0 || c->storage > 2 ? 0 : c->storage;
     if (c->nx & 1) return single[st];
-    const bool tab = c->bub.nb > 0 && c->p.two_way && !c->use_small;
-    return pair[st][tab ? 1 : 0];
+    if (!(c->bub.nb > 0 && c->p.two_way)) return free_[st];   // no tile lists
+    return pair[st][c->use_small ? 0 : 1];
 }
 
 int lbm_sync(lbm_ctx* c) {
