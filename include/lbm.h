@@ -456,9 +456,12 @@ long long lbm_launch_count(const lbm_ctx* ctx);
 
 /* Name of the collide-stream kernel (step 3 of lbm_step) that the next step
  * of this context launches, for reports that pair timings with profiles:
- * the two-node sweep "k_collide_stream_pair<S,T>" (even nx; S the storage
- * code, T = 1 for the tabulated force gather of long tile lists) or
- * "k_collide_stream<S>" (odd nx).  A static string; "" for NULL. */
+ * the two-node sweep "k_collide_stream_pair<S,T>" (even nx with two-way
+ * coupled bubbles; S the storage code, T = 1 for the tabulated force gather
+ * of long tile lists), "k_collide_stream_free<S>" (even nx, no tile lists:
+ * no bubbles or no two-way coupling; the many-bubble step also launches it
+ * for the blocks no bubble force reaches) or "k_collide_stream<S>" (odd nx).
+ * A static string; "" for NULL. */
 const char* lbm_sweep_kernel(const lbm_ctx* ctx);
 
 /* Wait for all work enqueued by this context. */
