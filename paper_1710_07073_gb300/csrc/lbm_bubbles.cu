@@ -919,10 +919,22 @@ __device__ __forceinline__ void mark_guarded_layers(const Geo& g, F2 z, float nh
 // instability.  Every thread of the CTA calls it.
 __device__ void write_safe_layers(const Geo& g, const BubbleDev& B, const SmallBins& sb) {
     __shared__ unsigned s_lay[GUARD_LAYERS_MAX / 32];
+    __shared__ int s_zr[2];   // first and last guarded layer
     const int tid = threadIdx.x, nt = blockDim.x;
     const int ntz = g.ntz;
-    if (ntz > GUARD_LAYERS_MAX) return;
+    if (ntz > GUARD_LAYERS_MAX) {
+        // No tags kept: every layer counts as guarded.
+        if (sb.zrange != nullptr && tid == 0) {
+            sb.zrange[0] = 0;
+            sb.zrange[1] = ntz - 1;
+        }
+        return;
+    }
     for (int i = tid; i < GUARD_LAYERS_MAX / 32; i += nt) s_lay[i] = 0u;
+    if (tid == 0) {
+        s_zr[0] = INT_MAX;
+        s_zr[1] = -1;
+    }
     __syncthreads();
     for (int b = tid; b < B.nb; b += nt) {
         if (!__ldcg(B.active + b)) continue;
@@ -930,9 +942,20 @@ __device__ void write_safe_layers(const Geo& g, const BubbleDev& B, const SmallB
                             __ldcg(&B.k[b].nh), __ldcg(&B.k[b].nl), s_lay);
     }
     __syncthreads();
-    for (int l = tid; l < ntz; l += nt)
-        if (!((s_lay[l >> 5] >> (l & 31)) & 1u)) sb.safe[l] = sb.safe_epoch;
+    for (int l = tid; l < ntz; l += nt) {
+        if (!((s_lay[l >> 5] >> (l & 31)) & 1u)) {
+            sb.safe[l] = sb.safe_epoch;
+        } else {
+            atomicMin(&s_zr[0], l);
+            atomicMax(&s_zr[1], l);
+        }
+    }
     if (sb.zperm != nullptr) write_zperm(sb.nbz, s_lay, sb.zperm);
+    __syncthreads();
+    if (sb.zrange != nullptr && tid == 0) {
+        sb.zrange[0] = s_zr[0];
+        sb.zrange[1] = s_zr[1];
+    }
 }
 
 // Bubble update with the few-pair binning fused behind it.

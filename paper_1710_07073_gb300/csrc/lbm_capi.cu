@@ -172,7 +172,7 @@ void free_bubbles(lbm_ctx* c) {
     void* ptrs[] = {b.k, b.xh, b.xl, b.u, b.d, b.n, b.ulprev, b.ul, b.psi, b.out64, b.has_prev,
                     b.active, b.spread, b.cell, b.rec, c->bins.items, sb.start, sb.count, sb.items,
                     sb.prev_tiles, sb.prev_n, sb.overflow, sb.done, sb.part, sb.arrive, sb.safe,
-                    sb.zperm, sw.bar, sw.cursor, sw.kidx, sw.slots, sw.ntile, sw.partial, sw.cover,
+                    sb.zperm, sb.zrange, sw.bar, sw.cursor, sw.kidx, sw.slots, sw.ntile, sw.partial, sw.cover,
                     sw.ncover, sw.chunk_sums, sw.zrange};
     for (void* p : ptrs) dfree(c, p);
     c->cover_valid = false;
@@ -197,12 +197,13 @@ namespace {
 
 // Two tag sets of ntz (zero: no layer cleared) and two sweep orders of nbz z
 // blocks (identity), by step parity.
-int alloc_guard(lbm_ctx* c, unsigned** safe, int** zperm, int* nbz) {
+int alloc_guard(lbm_ctx* c, unsigned** safe, int** zperm, int* nbz, int** zrange) {
     const Geo g = geo_of(c);
     *nbz = sweep_z_blocks(g.nz);
     *safe = (unsigned*)dalloc(c, 2 * sizeof(unsigned) * (size_t)g.ntz);
     *zperm = (int*)dalloc(c, 2 * sizeof(int) * (size_t)*nbz);
-    if (!*safe || !*zperm) return LBM_ERR_ALLOC;
+    *zrange = (int*)dalloc(c, 2 * sizeof(int));
+    if (!*safe || !*zperm || !*zrange) return LBM_ERR_ALLOC;
     std::vector<int> ident(2 * (size_t)*nbz);
     for (int k = 0; k < 2 * *nbz; ++k) ident[k] = k % *nbz;
     LBM_CUDA(cudaMemsetAsync(*safe, 0, 2 * sizeof(unsigned) * (size_t)g.ntz, c->stream), "guard");
@@ -257,10 +258,12 @@ void destroy_split(lbm_ctx* c) {
     if (c->zr_host) cudaFreeHost(c->zr_host);
 }
 
-// The z blocks [*b0, *b1) that bubble forces may reach in many-path step n,
-// from the binning's z range read back SPLIT_LAG steps before: a bubble moves
-// at most GUARD_CELLS = TZ cells, one tile layer, per step (else the step is
-// flagged unstable).  Returns false if no such read-back is at hand.
+// The z blocks [*b0, *b1) that bubble forces may reach in step n, from the z
+// range read back SPLIT_LAG steps before (the many-bubble binning's lists, or
+// the few-bubble update's guarded layers, which already reach one step on): a
+// bubble moves at most GUARD_CELLS = TZ cells, one tile layer, per step (else
+// the step is flagged unstable).  Returns false if no such read-back is at
+// hand.
 bool guarded_blocks(lbm_ctx* c, const Geo& g, int* b0, int* b1, int* rc) {
     *rc = LBM_OK;
     const long long n = c->swarm_step, m = n - lbm_ctx::SPLIT_LAG;
@@ -315,13 +318,16 @@ int enqueue_one_step(lbm_ctx* c) {
     const unsigned* safe_now = safe ? safe + now * (size_t)g.ntz : nullptr;
     const int* zperm_now = zperm ? zperm + now * (size_t)nbz : nullptr;
     const int pad = (c->p.forces & LBM_FORCE_LIFT) ? 1 : 0;   // the vorticity halo
-    // Many bubbles: the update and the sweep of the z blocks bubbles can reach
-    // run on a high-priority side stream while the other blocks are swept
-    // (without forces) on a low-priority one; the step then joins on
-    // c->stream.  The per-node arithmetic is the same, so are the results.
+    // Split step (wall-bounded z, even rows): the update and the sweep of the
+    // z blocks bubble forces can reach run on a high-priority side stream
+    // while the other blocks are swept (without forces) on a low-priority
+    // one; the step then joins on c->stream.  The per-node arithmetic is the
+    // same, so are the results.  Many bubbles take the z range of the
+    // binning's lists, few bubbles that of the update's guarded layers.
     const bool many = bubbles && !c->use_small;
-    const bool split_able = many && two_way && !c->timing && (g.nx & 1) == 0 &&
-                            (c->walls & 0x30) == 0x30;
+    const int* zrange_d = many ? c->swarm.zrange : (c->use_small ? c->small.zrange : nullptr);
+    const bool split_able = bubbles && zrange_d != nullptr && two_way && !c->timing &&
+                            (g.nx & 1) == 0 && (c->walls & 0x30) == 0x30;
     int gb0 = 0, gb1 = 0;
     bool split = false;
     if (split_able) {
@@ -353,7 +359,7 @@ int enqueue_one_step(lbm_ctx* c) {
             if (sb.zperm) sb.zperm += next * (size_t)nbz;
             sb.safe_epoch = epoch + 1;   // the update clears layers for the next step
             LBM_CUDA(launch_bubbles(c->storage, c->f[c->cur], g, cp, c->bub, bubble_const(c),
-                                    c->flag_d, sb, overlap, c->stream),
+                                    c->flag_d, sb, overlap && !split, st),
                      "bubble update");
             c->launches += 1;   // binning fused into the bubble update
         } else {
@@ -382,16 +388,16 @@ int enqueue_one_step(lbm_ctx* c) {
                      "bubble update");
             c->launches += SWARM_LAUNCHES;   // interpolation by tiles; update; binning
             c->cover_valid = true;
-            if (split_able) {
-                // This step's z range of the lists, for the split SPLIT_LAG steps on.
-                const int slot = (int)(c->swarm_step % lbm_ctx::SPLIT_RING);
-                LBM_CUDA(cudaMemcpyAsync(c->zr_host + 2 * slot, sw.zrange, 2 * sizeof(int),
-                                         cudaMemcpyDeviceToHost, st), "z range");
-                LBM_CUDA(cudaEventRecord(c->ev_rb[slot], st), "z range");
-                c->rb_step[slot] = c->swarm_step;
-            }
-            c->swarm_step += 1;
         }
+        if (split_able) {
+            // This step's z range, for the split SPLIT_LAG steps on.
+            const int slot = (int)(c->swarm_step % lbm_ctx::SPLIT_RING);
+            LBM_CUDA(cudaMemcpyAsync(c->zr_host + 2 * slot, zrange_d, 2 * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st), "z range");
+            LBM_CUDA(cudaEventRecord(c->ev_rb[slot], st), "z range");
+            c->rb_step[slot] = c->swarm_step;
+        }
+        c->swarm_step += 1;
         c->bins_valid = true;
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -790,7 +796,7 @@ int lbm_set_bubbles(lbm_ctx* c, int n, const double* pos3, const double* vel3,
                    sb.done && sb.part && sb.arrive;
         // Overlap guard: tags and sweep orders, one set per step parity.
         if (c->bins.T > 0 && geo_of(c).ntz <= GUARD_LAYERS_MAX) {
-            int rc = alloc_guard(c, &sb.safe, &sb.zperm, &sb.nbz);
+            int rc = alloc_guard(c, &sb.safe, &sb.zperm, &sb.nbz, &sb.zrange);
             if (rc == LBM_ERR_CUDA) {
                 free_bubbles(c);
                 return rc;

@@ -69,7 +69,7 @@ struct lbm_ctx {
     cudaEvent_t ev_rb[SPLIT_RING] = {};
     int* zr_host = nullptr;                 // pinned [2 * SPLIT_RING]
     long long rb_step[SPLIT_RING] = {-1, -1, -1, -1};
-    long long swarm_step = 0;               // many-path steps enqueued
+    long long swarm_step = 0;               // steps with bubbles enqueued
     long long swarm_valid_from = 0;         // readbacks before this step are stale
     int sms = 0;                            // SM count (the split interpolation's grid)
 

@@ -234,6 +234,9 @@ struct SmallBins {
     // Null: not kept.
     int* zperm;        // [nbz] (the set this launch writes)
     int nbz;
+    // The first and last z tile layer the update marks as guarded (last <
+    // first: none), for the host's split of later sweeps.  Null: not kept.
+    int* zrange;       // [2]
 };
 
 // Many bubbles: the bubble side of a step in three launches

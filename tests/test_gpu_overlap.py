@@ -7,9 +7,12 @@ velocities, update and binning for many) and the collide-stream sweep
 (Eq. 12-16, 21) as overlapping launches: sweep CTAs whose z tile layer the
 previous update cleared (no bubble support, widened by 4 cells, reaches it)
 do not wait for the update, and run first.
-With kernel timing on, the library keeps plain stream order instead, so the
-two runs below differ only in that scheduling; every population and bubble
-value must agree bit for bit.  A bubble faster than 4 cells per step is
+With wall-bounded z the step is split once the z range of the bubbles'
+reach has been read back (two steps on): the update and the sweep of the z
+blocks it can reach run on one stream, the sweep of the other blocks without
+force on another.  With kernel timing on, the library keeps plain stream
+order instead, so the two runs below differ only in that scheduling; every
+population and bubble value must agree bit for bit.  A bubble faster than 4 cells per step is
 reported as an instability.
 """
 import os
@@ -171,3 +174,24 @@ def test_many_bubbles_split_sweep_runs():
     lbm.lbm_step(col.ctx, 10)
     assert lbm.lbm_launch_count(col.ctx) - n0 == 40
     col.close()
+
+
+def test_few_bubbles_split_sweep_runs():
+    # Wall-bounded z: after the first steps a single-column step is three
+    # launches -- the update, the sweep of the z blocks its bubbles can
+    # reach, and that of the others (without force) on a second stream.
+    # Periodic z keeps the overlapped update and sweep: two launches.
+    for case, per_step in (("walls, one bubble", 3), ("periodic z, wraps through the top", 2)):
+        dims, walls, pos, vel, diam = CASES[case]
+        col = lbm.Column(dims, 1.6, walls, params=lbm.lbm_default_params())
+        lbm.lbm_set_bubbles(col.ctx, np.asarray(pos, float).reshape(-1),
+                            np.asarray(vel, float).reshape(-1), np.asarray(diam, float))
+        lbm.lbm_step(col.ctx, 4)
+        n0 = lbm.lbm_launch_count(col.ctx)
+        lbm.lbm_step(col.ctx, 10)
+        assert lbm.lbm_launch_count(col.ctx) - n0 == 10 * per_step, case
+        lbm.lbm_set_kernel_timing(col.ctx, True)      # plain order: update and one sweep
+        n0 = lbm.lbm_launch_count(col.ctx)
+        lbm.lbm_step(col.ctx, 10)
+        assert lbm.lbm_launch_count(col.ctx) - n0 == 20, case
+        col.close()
