@@ -129,26 +129,31 @@ def test_adjoint_many_bubbles_against_oracle_fd():
 
 def test_adjoint_launch_count():
     # Every kernel of the forward record and of the reverse sweep is counted:
-    # per step the coupled step's own launches and the rise-velocity record;
-    # per checkpoint a bubble snapshot; the final snapshot and the loss.  The
-    # reverse: per segment a restore, per recomputed step two snapshots and the
-    # step, per reverse step three adjoint kernels; the initial-field adjoint
-    # and the final restore.
+    # per step the coupled step's own launches (as lbm_step launches them from
+    # the same state: the first steps after the bubbles are set or restored
+    # take fewer) and the rise-velocity record; per checkpoint a bubble
+    # snapshot; the final snapshot and the loss.  The reverse: per segment a
+    # restore, its recomputed steps with two snapshots each; per reverse step
+    # three adjoint kernels; the initial-field adjoint and the final restore.
     prob = _problem(steps=25, every=10, window=10)
     P = workloads.gaussian_velocity_perturbation(prob.dims, seed=4, amp=1e-4)
+
+    def step_launches(k):
+        col = prob.column(1.0, 2.5, P)
+        n0 = lbm.lbm_launch_count(col.ctx)
+        lbm.lbm_step(col.ctx, k)
+        n = lbm.lbm_launch_count(col.ctx) - n0
+        col.close()
+        return n
+
+    N, K = prob.steps, prob.checkpoint_every
+    seg_lens = [min(K, N - s0) for s0 in range(0, N, K)]
     col = prob.column(1.0, 2.5, P)
     n0 = lbm.lbm_launch_count(col.ctx)
-    lbm.lbm_step(col.ctx, 1)
-    per_step = lbm.lbm_launch_count(col.ctx) - n0
-    col.close()
-    assert per_step >= 1
-    col = prob.column(1.0, 2.5, P)
-    n0 = lbm.lbm_launch_count(col.ctx)
-    lbm.lbm_adj_forward(col.ctx, prob.steps, prob.checkpoint_every, prob.window, prob.target)
+    lbm.lbm_adj_forward(col.ctx, N, K, prob.window, prob.target)
     n1 = lbm.lbm_launch_count(col.ctx)
     lbm.lbm_adj_backward(col.ctx, 1.0, want_u0=True)
     n2 = lbm.lbm_launch_count(col.ctx)
     col.close()
-    segments = -(-prob.steps // prob.checkpoint_every)
-    assert n1 - n0 == prob.steps * (per_step + 1) + segments + 2
-    assert n2 - n1 == segments + prob.steps * (per_step + 2) + 3 * prob.steps + 2
+    assert n1 - n0 == step_launches(N) + N + len(seg_lens) + 2
+    assert n2 - n1 == sum(1 + step_launches(L) + 2 * L for L in seg_lens) + 3 * N + 2
