@@ -221,6 +221,14 @@ int alloc_guard(lbm_ctx* c, unsigned** safe, int** zperm, int* nbz, int** zrange
 #define LBM_SPLIT_INTERP_PER_SM 2
 #endif
 
+// Few bubbles: the split pays only where the sweep is long against the
+// step's extra host and stream work (fork, join, read-back, a third launch):
+// on GB300 256x256x512 gains (FP16 step 0.460 -> 0.445 ms), 128x128x256
+// loses (0.102 -> 0.120 s for 1000 forward steps).
+#ifndef LBM_FEW_SPLIT_MIN_SITES
+#define LBM_FEW_SPLIT_MIN_SITES (1LL << 24)
+#endif
+
 
 namespace {
 
@@ -325,7 +333,8 @@ int enqueue_one_step(lbm_ctx* c) {
     // same, so are the results.  Many bubbles take the z range of the
     // binning's lists, few bubbles that of the update's guarded layers.
     const bool many = bubbles && !c->use_small;
-    const int* zrange_d = many ? c->swarm.zrange : (c->use_small ? c->small.zrange : nullptr);
+    const bool few_split = c->use_small && g.S >= LBM_FEW_SPLIT_MIN_SITES;
+    const int* zrange_d = many ? c->swarm.zrange : (few_split ? c->small.zrange : nullptr);
     const bool split_able = bubbles && zrange_d != nullptr && two_way && !c->timing &&
                             (g.nx & 1) == 0 && (c->walls & 0x30) == 0x30;
     int gb0 = 0, gb1 = 0;

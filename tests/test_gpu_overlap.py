@@ -7,10 +7,10 @@ velocities, update and binning for many) and the collide-stream sweep
 (Eq. 12-16, 21) as overlapping launches: sweep CTAs whose z tile layer the
 previous update cleared (no bubble support, widened by 4 cells, reaches it)
 do not wait for the update, and run first.
-With wall-bounded z the step is split once the z range of the bubbles'
-reach has been read back (two steps on): the update and the sweep of the z
-blocks it can reach run on one stream, the sweep of the other blocks without
-force on another.  With kernel timing on, the library keeps plain stream
+With wall-bounded z (and, for few bubbles, a column of 2^24 sites or more)
+the step is split once the z range of the bubbles' reach has been read back
+(two steps on): the update and the sweep of the z blocks it can reach run on
+one stream, the sweep of the other blocks without force on another.  With kernel timing on, the library keeps plain stream
 order instead, so the two runs below differ only in that scheduling; every
 population and bubble value must agree bit for bit.  A bubble faster than 4 cells per step is
 reported as an instability.
@@ -176,21 +176,38 @@ def test_many_bubbles_split_sweep_runs():
     col.close()
 
 
-def test_few_bubbles_split_sweep_runs():
-    # Wall-bounded z: after the first steps a single-column step is three
-    # launches -- the update, the sweep of the z blocks its bubbles can
-    # reach, and that of the others (without force) on a second stream.
-    # Periodic z keeps the overlapped update and sweep: two launches.
-    for case, per_step in (("walls, one bubble", 3), ("periodic z, wraps through the top", 2)):
+def test_few_bubbles_split_sweep_matches_plain_order():
+    # A column of 2^24 sites or more with wall-bounded z: after the first
+    # steps a step is three launches -- the update, the sweep of the z blocks
+    # its bubble can reach, and that of the others (without force) on a second
+    # stream -- and gives the bits of plain stream order.  Smaller columns
+    # and periodic z keep the overlapped update and sweep: two launches.
+    dims = (256, 256, 256)
+    pos, vel, diam = [[128.0, 128.0, 60.3]], [[0.0, 0.0, 0.05]], [2.0]
+    runs = []
+    for plain in (True, False):
+        col = lbm.Column(dims, 1.6, olat.ALL_WALLS, params=lbm.lbm_default_params())
+        lbm.lbm_set_bubbles(col.ctx, np.asarray(pos, float).reshape(-1),
+                            np.asarray(vel, float).reshape(-1), np.asarray(diam, float))
+        lbm.lbm_set_kernel_timing(col.ctx, plain)
+        lbm.lbm_step(col.ctx, 4)
+        n0 = lbm.lbm_launch_count(col.ctx)
+        lbm.lbm_step(col.ctx, 10)
+        assert lbm.lbm_launch_count(col.ctx) - n0 == (20 if plain else 30)
+        rho, u = lbm.lbm_get_fields(col.ctx)
+        b = lbm.lbm_get_bubbles(col.ctx)
+        runs.append((rho, u, b))
+        col.close()
+    (r0, u0, b0), (r1, u1, b1) = runs
+    assert np.array_equal(r0, r1) and np.array_equal(u0, u1)
+    for k in ("pos", "vel", "active"):
+        assert np.array_equal(b0[k], b1[k]), k
+    for case in ("walls, one bubble", "periodic z, wraps through the top"):
         dims, walls, pos, vel, diam = CASES[case]
         col = lbm.Column(dims, 1.6, walls, params=lbm.lbm_default_params())
         lbm.lbm_set_bubbles(col.ctx, np.asarray(pos, float).reshape(-1),
                             np.asarray(vel, float).reshape(-1), np.asarray(diam, float))
         lbm.lbm_step(col.ctx, 4)
-        n0 = lbm.lbm_launch_count(col.ctx)
-        lbm.lbm_step(col.ctx, 10)
-        assert lbm.lbm_launch_count(col.ctx) - n0 == 10 * per_step, case
-        lbm.lbm_set_kernel_timing(col.ctx, True)      # plain order: update and one sweep
         n0 = lbm.lbm_launch_count(col.ctx)
         lbm.lbm_step(col.ctx, 10)
         assert lbm.lbm_launch_count(col.ctx) - n0 == 20, case
