@@ -260,15 +260,16 @@ int lbm_set_bubbles(lbm_ctx* ctx, int n, const double* pos3, const double* vel3,
  * sweep may start while its bubble update still runs: lattice z layers that
  * no bubble can reach this step (support widened by 4 cells) do not wait for
  * it.  Results are the same bits as with the two in stream order (which the
- * library keeps while kernel timing is on).  With many bubbles on even-nx
- * lattices whose z axis is wall-bounded, a step forks from the context
- * stream into two library streams: a high-priority one for the bubble
- * update, the binning and the sweep of the z blocks bubble forces can reach,
- * and a low-priority one for the sweep of the other blocks, which needs no
- * forces; the step joins the context stream again before it ends.  The
- * reachable blocks are those of the binning two steps before, widened by one
- * tile layer per step (a bubble moving farther is flagged).  Same bits as
- * stream order.  psi_b is -mean(F_D + F_L) unless lbm_params.reaction says
+ * library keeps while kernel timing is on).  With many bubbles, or few
+ * bubbles in a lattice of 2^24 sites or more, on even-nx lattices whose z
+ * axis is wall-bounded, a step forks from the context stream into two
+ * library streams: a high-priority one for the bubble update, the binning
+ * and the sweep of the z blocks bubble forces can reach, and a low-priority
+ * one for the sweep of the other blocks, which needs no forces; the step
+ * joins the context stream again before it ends.  The reachable blocks are
+ * those of the binning (many bubbles) or of the update's guard (few) two
+ * steps before, widened by one tile layer per step (a bubble moving farther
+ * is flagged).  Same bits as stream order.  psi_b is -mean(F_D + F_L) unless lbm_params.reaction says
  * otherwise.
  * Returns after the work has completed, with LBM_ERR_UNSTABLE if flagged. */
 int lbm_step(lbm_ctx* ctx, int nsteps);
