@@ -1141,6 +1141,13 @@ constexpr int INTERP_THREADS = TX * TY * 2;   // two of a tile's TZ planes per t
 constexpr int INTERP_CHUNK = 32;              // listed bubbles per pass
 constexpr int INTERP_ROWS = TY * TZ;          // (y, z) rows of a tile: 16
 static_assert(INTERP_THREADS % INTERP_ROWS == 0 && TZ == 4, "tile shape of the interpolation");
+// Resident CTAs per SM the interpolation is compiled for: 16-bit storage on
+// even rows at 5 (48 registers; its swarm step ran 1 % shorter than at 4, at
+// 6 longer); FP32 at 4 (at 5 it spills 96 bytes and its step was longer), as
+// odd rows (whose two-node gather spills 172 bytes at 48 registers).
+template <int ST, bool PAIR> struct InterpOccupancy {
+    static constexpr int kMinBlocks = (ST != 0 && PAIR) ? 5 : 4;
+};
 
 // The list head of a covered tile: its list range [beg, end) and this
 // thread's entry of the first chunk (-1 beyond it).  The interpolation loads
@@ -1333,7 +1340,7 @@ __device__ __forceinline__ void tile_interp(const typename Store<ST>::T* __restr
 
 // Persistent over the list of covered tiles, a tile per CTA in turn.
 template <int ST, bool PAIR, bool LIFT>
-__global__ void __launch_bounds__(INTERP_THREADS, 4)
+__global__ void __launch_bounds__(INTERP_THREADS, InterpOccupancy<ST, PAIR>::kMinBlocks)
 k_tile_interp(const typename Store<ST>::T* __restrict__ f, Geo g, CollideParams cp,
               const int* __restrict__ cnt, const int* __restrict__ off,
               const int* __restrict__ items, int cap, const BubbleRec* __restrict__ recs, int nb,
